@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark: FP64 Jacobi-PCG on the 32x32x32 deformed box (32768 elements, nx=10).
+
+One step is one ``nek_cg_solve`` call of 100 Jacobi-PCG iterations (tol = 0, a
+fixed iteration count), i.e. 100 passes of the whole solve path: AX, dssum,
+mask, the weighted dot products and the vector updates.  ``value`` is local
+grid points x iterations per second (GDOF/s) over all ranks.  The AX kernel is
+timed inside the same region with CUDA events on the solve's stream; it gives the
+roofline entry and the AX-only GDOF/s and %-of-HBM figures.
+
+Inputs are synthetic (seeded deformed-box mesh, f ~ U[-1,1] per global node);
+the geometric factors alone are 1.57 GB, far larger than the 129 MB L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--iters 100] [--nx 10]
+                  [--impl reference] [--sweep] [--solve]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AX GDOF/s & % HBM peak; CG s-to-1e-8 residual, FP64 vs mixed/learned"
+UNIT = "GDOF/s"
+FP64_PEAK_TFLOPS = 1.2586  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=100, help="PCG iterations per step")
+    ap.add_argument("--nx", type=int, default=10)
+    ap.add_argument("--elems", type=int, default=32, help="elements per box edge")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--sweep", action="store_true", help="also time standalone AX at nx = 8, 10, 12, 16")
+    ap.add_argument("--solve", action="store_true", help="also time one solve to 1e-8 relative residual")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def kernel_source_sha():
+    with open(os.path.join(ROOT, "paper_2011_04981_gb300", "csrc", "nek_ax.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def traffic_from_profile(nx, nelt):
+    """DRAM bytes per AX launch from the committed ncu summary, if it matches this kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ax_fp64_traffic.json")) as fh:
+            t = json.load(fh)
+        if t.get("source_sha") != kernel_source_sha() or int(t["nx"]) != nx:
+            return None
+        return float(t["dram_bytes_per_element"]) * nelt
+    except Exception:
+        return None
+
+
+def cpu_baseline(nx, iters_budget_s=15.0):
+    """Time the oracle (as it stands, single-threaded C) on a bounded sample of
+    the same workload: Jacobi-PCG iterations on a 12x12x12-element box of the
+    same family (same nx, perturbation and seed recipe)."""
+    from oracle import ref
+    from paper_2011_04981_gb300 import inputs
+
+    e = 12
+    mesh = inputs.box_mesh(e, e, e, nx, perturb=0.1, seed=1)
+    P = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=2)
+    t0 = time.perf_counter()
+    ref.pcg(P.D, P.G, P.offsets, P.idx, mesh.mask, P.minv, f, tol=0.0, max_iter=2)
+    t1 = time.perf_counter()
+    per_it = (t1 - t0) / 2
+    iters = max(2, min(200, int(iters_budget_s / max(per_it, 1e-6))))
+    t0 = time.perf_counter()
+    ref.pcg(P.D, P.G, P.offsets, P.idx, mesh.mask, P.minv, f, tol=0.0, max_iter=iters)
+    dt = time.perf_counter() - t0
+    return {"value": mesh.npts * iters / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d Jacobi-PCG iterations on a %dx%dx%d-element deformed box, nx=%d (%d points), "
+                      "single-threaded C oracle, %.1f s" % (iters, e, e, e, nx, mesh.npts, dt),
+            "seconds": dt}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cb = None
+    steps_val = []
+    budget = max(3.0, 120.0 / max(1, args.steps + args.warmup))
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(args.nx, iters_budget_s=budget)
+        if s >= args.warmup:
+            steps_val.append(r)
+        cb = r
+    tot_pts_it = sum(r["value"] * r["seconds"] for r in steps_val)
+    tot_s = sum(r["seconds"] for r in steps_val)
+    value = tot_pts_it / tot_s
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_s / len(steps_val),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Jacobi-PCG iterations, deformed box, nx=%d, FP64 (oracle sample)" % args.nx,
+                       "elements": 12 ** 3, "nx": args.nx},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ native arm
+def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10):
+    from paper_2011_04981_gb300 import inputs, nekax, perfmodel
+    from paper_2011_04981_gb300.problem import DeviceProblem
+
+    out = {}
+    hbm, _ = peaks()
+    for nx in nxs:
+        mesh = inputs.box_mesh(32, 32, 32, nx, perturb=0.1, seed=1)
+        P = DeviceProblem(mesh, "cuda", build_minv=False)
+        u = torch.rand((mesh.nelt, nx ** 3), dtype=torch.float64, device="cuda") * 2 - 1
+        w = torch.empty_like(u)
+        s = torch.cuda.current_stream()
+        for _ in range(3):
+            P.ax(u, w)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(reps):
+            P.ax(u, w)
+        e1.record(s)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps / 1e3
+        g = mesh.npts / t / 1e9
+        out[str(nx)] = {"gdofs": g, "ms": t * 1e3, "gflops": g * perfmodel.ax_flops_per_point(nx),
+                        "hbm_frac": g * 64 / hbm, "fp64_frac": g * perfmodel.ax_flops_per_point(nx) / 1e3 /
+                        FP64_PEAK_TFLOPS}
+        del P, u, w
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_native(args):
+    import torch
+
+    from paper_2011_04981_gb300 import inputs, nekax, perfmodel
+    from paper_2011_04981_gb300.problem import DeviceProblem
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    nx, e = args.nx, args.elems
+    mesh = inputs.box_mesh(e, e, e, nx, perturb=0.1, seed=1)
+    P = DeviceProblem(mesh, "cuda")
+    f_host = torch.from_numpy(inputs.random_global_field(mesh, seed=2)).pin_memory()
+    f = f_host.to("cuda")
+    x = torch.empty_like(f)
+    x_host = torch.empty_like(f_host).pin_memory()
+    ws = torch.empty(nekax.cg_workspace_bytes(mesh.nelt, nx, False) // 8 + 64, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    iters = args.iters
+
+    for _ in range(args.warmup):
+        P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ax_ms, ax_n, launches = 0.0, 0, 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        r = P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, time_ax=True)
+        ax_ms += r["ax_ms_total"]
+        ax_n += r["ax_launches"]
+        launches += r["kernel_launches"]
+        assert r["status"] == nekax.OK and r["iters"] == iters, r
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    clk = clocks.stop()
+
+    # end to end through the public call: pinned host f -> device, solve, x -> host, every step
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f.copy_(f_host, non_blocking=True)
+        P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws)
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    barrier()
+
+    if dist is not None:
+        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev, t_e2e = float(tt[0]), float(tt[1])
+
+    pts = mesh.npts
+    value = pts * iters * args.steps * world / t_dev / 1e9
+    e2e = pts * iters * args.steps * world / t_e2e / 1e9
+    ax_t = ax_ms / max(ax_n, 1) / 1e3
+    ax_gdofs = pts / ax_t / 1e9
+    flops = perfmodel.ax_flops_per_point(nx) * pts
+    hbm, hbm_kind = peaks()
+    traffic = traffic_from_profile(nx, mesh.nelt)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Jacobi-PCG, %d PCG iterations per step (AX+dssum+mask+dots+updates), "
+                               "%dx%dx%d deformed box (perturbation 0.1 h), nx=%d, FP64" % (iters, e, e, e, nx),
+                   "elements": mesh.nelt, "nx": nx, "points": pts, "iters_per_step": iters,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (G alone %.2f GB), no flush" % (pts * 48 / 1e9)},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": pts * 8, "d2h_bytes_per_step": pts * 8},
+        "gpu_launches": launches,
+        "ax": {"gdofs": ax_gdofs, "ms_per_launch": ax_t * 1e3, "gflops": flops / ax_t / 1e9,
+               "hbm_gbs": 64 * pts / ax_t / 1e9, "hbm_frac": 64 * pts / ax_t / 1e9 / hbm, "launches": ax_n,
+               "share_of_step": ax_ms / 1e3 / t_dev},
+        "roofline": {"bound": "alu", "achieved": flops / ax_t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flops / ax_t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "k_ax_fp64<%d>" % nx,
+                     "note": "FP64 DFMA-pipe bound; peak = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz; HBM %s peak %.0f GB/s"
+                             % (hbm_kind, hbm)},
+        "clocks": clk,
+    }
+    if args.sweep and rank == 0:
+        line["ax_sweep"] = ax_sweep(torch)
+    if args.solve and rank == 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = P.cg(f, x, tol=1e-8, max_iter=20000, workspace=ws, check_every=20)
+        torch.cuda.synchronize()
+        line["cg_to_1e-8"] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"],
+                              "status": nekax.status_string(r["status"]), "precision": "fp64 jacobi-pcg"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline(nx)
+        cb.pop("seconds", None)
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,51 @@
+// Internal declarations shared by the translation units of libnekax.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nekax.h"
+
+namespace nek {
+
+constexpr int kMinNx = 2;
+constexpr int kMaxNx = 16;
+
+// Record a CUDA error in the calling thread's last-error slot and map it to NEK_ERR_CUDA.
+nek_status cuda_fail(cudaError_t e);
+inline nek_status check_cuda(cudaError_t e) { return e == cudaSuccess ? NEK_OK : cuda_fail(e); }
+inline nek_status check_launch() { return check_cuda(cudaGetLastError()); }
+
+inline bool is_aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+    return x < y + nb && y < x + na;
+}
+
+// Host GLL rule: ascending nodes, weights, D[i*nx+l] = l_l'(xi_i).
+void gll_host(int nx, double* xi, double* rho, double* D);
+
+// Kernel launchers (arguments already validated).
+nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w,
+                          cudaStream_t s);
+nek_status launch_mask(int64_t n, const uint8_t* mask, double* v, cudaStream_t s);
+nek_status launch_dssum(const nek_gs* gs, double* v, cudaStream_t s);
+
+// Deterministic block-partial reductions use this fixed grid for a given length.
+int reduce_blocks(int64_t n);
+constexpr int kReduceThreads = 256;
+constexpr int kMaxReduceBlocks = 152 * 8;
+
+}  // namespace nek
+
+// Gather-scatter plan (opaque to callers).
+struct nek_gs {
+    int64_t npts;      // local points
+    int64_t ngroups;   // groups with >= 2 members
+    int64_t nshared;   // local points that belong to a group
+    int32_t* d_offsets;  // ngroups+1
+    int32_t* d_members;  // nshared
+    double* d_c;         // npts: 1/multiplicity
+    double* d_partials;  // scratch for nek_dot_c (kMaxReduceBlocks doubles), lazily allocated
+};

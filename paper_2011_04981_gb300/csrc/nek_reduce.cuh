@@ -1,0 +1,37 @@
+// Deterministic block reduction helpers: a fixed grid accumulates per-thread
+// grid-stride sums, reduces them warp-wise with shuffles in a fixed pattern and
+// writes one partial per block; a single block then sums the partials in order.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace nek {
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh /* NT/32 doubles */)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < NT / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// Sum of nparts partials (in a fixed order) by one block of NT threads.
+template <int NT>
+__device__ __forceinline__ double sum_partials(const double* parts, int nparts, double* sh)
+{
+    double v = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += NT) v += parts[q];
+    return block_sum<NT>(v, sh);
+}
+
+}  // namespace nek

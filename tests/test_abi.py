@@ -1,0 +1,107 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and rejects bad arguments on the host before any launch.
+
+Every call here fails validation (bad nx, negative size, NULL, misaligned or
+overlapping pointers), so no kernel is ever enqueued, with or without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import ref
+from paper_2011_04981_gb300 import build as nbuild
+from paper_2011_04981_gb300 import nekax
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nbuild.build()
+    return nekax.load()
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "nekax.h")).read()
+    return sorted(set(re.findall(r"^(?:const char\*|nek_status|int|size_t)\s+(nek_\w+)\s*\(", txt, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = _declared_symbols()
+    assert len(syms) >= 18
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(nekax.exported_symbols())
+
+
+def test_status_strings(lib):
+    for st, name in [(0, "NEK_OK"), (1, "NEK_ERR_INVALID_ARG"), (2, "NEK_ERR_UNSUPPORTED_NX"), (3, "NEK_ERR_CUDA"),
+                     (4, "NEK_ERR_NOT_CONVERGED"), (5, "NEK_ERR_BREAKDOWN"), (6, "NEK_ERR_TIMEOUT"),
+                     (7, "NEK_ERR_NOMEM"), (8, "NEK_ERR_TOO_LARGE"), (99, "NEK_ERR_UNKNOWN")]:
+        assert nekax.status_string(st) == name
+    assert nekax.version() >= 100
+
+
+@pytest.mark.parametrize("nx", range(2, 17))
+def test_host_gll_matches_oracle(lib, nx):
+    xi, rho, D = nekax.gll(nx)
+    xo, ro, Do = ref.gll(nx)
+    assert np.max(np.abs(xi - xo)) <= 4e-16
+    assert np.max(np.abs(rho - ro)) <= 4e-16 * nx
+    assert np.max(np.abs(D - Do)) <= 2e-15 * nx * np.abs(Do).max()
+
+
+def test_ax_rejects_bad_arguments_before_launch(lib):
+    A16 = 0x10000  # 16-byte aligned fake addresses, never dereferenced
+    L = lib
+    assert L.nek_ax(4, 1, A16, A16, A16, A16 * 2, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_ax(4, 17, A16, A16, A16, A16 * 2, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_ax(-1, 8, A16, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax(0, 8, None, None, None, None, None) == nekax.OK  # empty input is a no-op
+    assert L.nek_ax(4, 8, None, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax(4, 8, A16, None, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax(4, 8, A16, A16 + 8, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # G misaligned
+    assert L.nek_ax(4, 8, A16, A16, A16 + 8, A16 * 2, None) == nekax.ERR_INVALID_ARG  # u misaligned
+    assert L.nek_ax(4, 8, A16 + 4, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # D misaligned
+    # u and w overlap (4 elements of 512 doubles = 16 KiB each)
+    assert L.nek_ax(4, 8, A16, A16, A16, A16 + 4096, None) == nekax.ERR_INVALID_ARG
+
+
+def test_other_entry_points_reject_bad_arguments(lib):
+    L = lib
+    A16 = 0x10000
+    assert L.nek_geom(4, 1, A16, A16, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_geom(-2, 4, A16, A16, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_geom(4, 4, None, A16, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_geom(4, 4, A16, A16 + 8, None) == nekax.ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert L.nek_gs_create(1, 1, None, ctypes.byref(h)) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_gs_create(-1, 3, None, ctypes.byref(h)) == nekax.ERR_INVALID_ARG
+    assert L.nek_gs_create(1, 3, None, ctypes.byref(h)) == nekax.ERR_INVALID_ARG
+    assert L.nek_gs_create(1, 3, None, None) == nekax.ERR_INVALID_ARG
+    bad = np.full(27, -1, dtype=np.int64)
+    assert L.nek_gs_create(1, 3, bad.ctypes.data, ctypes.byref(h)) == nekax.ERR_INVALID_ARG
+    assert L.nek_gs_create(1 << 22, 16, None, ctypes.byref(h)) == nekax.ERR_TOO_LARGE
+    assert L.nek_dssum(None, A16, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_gs_destroy(None) == nekax.OK
+    assert L.nek_gs_info(None, None, None, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_mask(-1, A16, A16, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_mask(0, None, None, None) == nekax.OK
+    assert L.nek_mask(8, None, A16, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_dot_c(None, A16, A16, A16, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_jacobi_minv(None, 1, 3, A16, A16, A16, A16, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_jacobi_minv(None, 1, 1, A16, A16, A16, A16, None) == nekax.ERR_UNSUPPORTED_NX
+    it, rr = ctypes.c_int(5), ctypes.c_double(5.0)
+    assert L.nek_cg_solve(None, 1, 3, A16, A16, A16, None, A16, A16, 1e-8, 10, None, ctypes.byref(it),
+                          ctypes.byref(rr), None) == nekax.ERR_INVALID_ARG
+    assert it.value == 0 and rr.value == 0.0
+    assert L.nek_cg_solve(None, 1, 20, A16, A16, A16, None, A16, A16, 1e-8, 10, None, None, None,
+                          None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_gll(1, None, None, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_cg_workspace_bytes(-1, 8, 1) == 0
+    n = 10 * 8 ** 3
+    assert L.nek_cg_workspace_bytes(10, 8, 1) >= 5 * 8 * n
+    assert L.nek_cg_workspace_bytes(10, 8, 0) >= 4 * 8 * n

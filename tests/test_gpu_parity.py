@@ -1,0 +1,262 @@
+"""GPU parity: every step of the solve path through the C ABI against the oracle.
+
+Tolerances (FP64 throughout): AX and G within 1e-12 relative in the max norm
+(the operator's rounding is O(nx eps) relative to |D|^2|G||u|); gather-scatter
+plan and dssum bit-exact (same groups, same left-to-right order); PCG to the
+same iteration count within 2 and a solution whose residual, recomputed by the
+oracle, meets the tolerance.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import ref  # noqa: E402
+from paper_2011_04981_gb300 import inputs, nekax  # noqa: E402
+from paper_2011_04981_gb300.problem import DeviceProblem  # noqa: E402
+
+DEV = "cuda"
+TOL_AX = 1e-12
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    nekax.load()
+
+
+# ------------------------------------------------------------------ AX
+@pytest.mark.parametrize("nx", list(range(2, 17)))
+@pytest.mark.parametrize("nelt", [1, 7, 37])
+def test_ax_parity_sweep(nx, nelt):
+    """Oracle D and G fed to both sides; several CTAs and a ragged last CTA."""
+    rng = np.random.default_rng(nx * 100 + nelt)
+    xi, rho, D = ref.gll(nx)
+    mesh = inputs.box_mesh(nelt, 1, 1, nx, perturb=0.2, seed=nx)
+    G = ref.geom(mesh.corners, nx, xi, rho)
+    u = rng.uniform(-1, 1, size=(nelt, nx ** 3))
+    wd = torch.full((nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+    nekax.ax(nelt, nx, _t(D), _t(G), _t(u), wd)
+    torch.cuda.synchronize()
+    w = wd.cpu().numpy()
+    assert np.all(np.isfinite(w)), "unwritten output entries"
+    assert _rel(w, ref.ax(D, G, u)) <= TOL_AX
+
+
+def test_ax_config1_64_elements_nx8():
+    """4x4x4 unit-cube box, nx=8, perturbation 0.05 h, G from the library's own set-up."""
+    mesh = inputs.box_mesh(4, 4, 4, 8, perturb=0.05, seed=1)
+    P = DeviceProblem(mesh, DEV, build_minv=False)
+    Pr = ref.Problem(mesh)
+    u = inputs.random_local_field(mesh.nelt, 8, seed=1)
+    w = torch.empty((mesh.nelt, 512), dtype=torch.float64, device=DEV)
+    P.ax(_t(u), w)
+    torch.cuda.synchronize()
+    assert _rel(w.cpu().numpy(), ref.ax(Pr.D, Pr.G, u)) <= TOL_AX
+
+
+def test_ax_full_size_sampled():
+    """32768 elements at nx=10 (the benchmark's launch), checked on sampled elements."""
+    nx = 10
+    mesh = inputs.box_mesh(32, 32, 32, nx, perturb=0.1, seed=2)
+    P = DeviceProblem(mesh, DEV, build_minv=False)
+    u = inputs.random_local_field(mesh.nelt, nx, seed=5)
+    w = torch.empty((mesh.nelt, nx ** 3), dtype=torch.float64, device=DEV)
+    P.ax(_t(u), w)
+    torch.cuda.synchronize()
+    sample = np.random.default_rng(0).choice(mesh.nelt, size=96, replace=False)
+    sample = np.concatenate([sample, [0, 1, mesh.nelt - 1]])
+    xi, rho, D = ref.gll(nx)
+    G = ref.geom(mesh.corners[sample], nx, xi, rho)
+    assert _rel(w.cpu().numpy()[sample], ref.ax(D, G, u[sample])) <= TOL_AX
+
+
+def test_ax_on_side_stream_and_empty():
+    nx = 6
+    xi, rho, D = ref.gll(nx)
+    mesh = inputs.box_mesh(5, 3, 1, nx, perturb=0.1)
+    G = ref.geom(mesh.corners, nx, xi, rho)
+    u = inputs.random_local_field(mesh.nelt, nx)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        Dd, Gd, ud = _t(D), _t(G), _t(u)
+        wd = torch.empty_like(ud)
+        nekax.ax(mesh.nelt, nx, Dd, Gd, ud, wd, stream=s)
+    s.synchronize()
+    assert _rel(wd.cpu().numpy(), ref.ax(D, G, u)) <= TOL_AX
+    nekax.ax(0, nx, Dd, Gd, ud, wd)  # no-op
+
+
+def test_ax_constant_in_kernel_on_gpu():
+    nx = 12
+    mesh = inputs.box_mesh(3, 3, 3, nx, perturb=0.2, seed=9)
+    P = DeviceProblem(mesh, DEV, build_minv=False)
+    u = torch.full((mesh.nelt, nx ** 3), 2.0, dtype=torch.float64, device=DEV)
+    w = torch.empty_like(u)
+    P.ax(u, w)
+    Gmax = float(P.G.abs().max())
+    Dmax = float(np.abs(P.D_host).max())
+    assert float(w.abs().max()) <= 8 * nx * 2.2e-16 * Gmax * Dmax ** 2 * nx * 2.0 * 6
+
+
+# ------------------------------------------------------------------ geometry
+@pytest.mark.parametrize("nx", [2, 5, 8, 10, 16])
+def test_geom_parity(nx):
+    mesh = inputs.box_mesh(3, 2, 2, nx, perturb=0.15, seed=nx, lengths=(1.0, 2.0, 0.5))
+    G = torch.empty((mesh.nelt, nx ** 3, 6), dtype=torch.float64, device=DEV)
+    nekax.geom(mesh.nelt, nx, _t(mesh.corners), G)
+    torch.cuda.synchronize()
+    Gr = ref.geom(mesh.corners, nx)
+    assert _rel(G.cpu().numpy(), Gr) <= 1e-13
+
+
+# ------------------------------------------------------------------ gather-scatter / mask
+@pytest.mark.parametrize("dims,nx", [((1, 1, 1), 2), ((2, 3, 2), 4), ((4, 4, 4), 8), ((5, 2, 3), 5)])
+def test_gs_plan_bit_exact(dims, nx):
+    mesh = inputs.box_mesh(*dims, nx, perturb=0.0)
+    gs = nekax.GsPlan(mesh.nelt, nx, mesh.glo_num)
+    off, mem = gs.export()
+    ro, rm = ref.gs_build(mesh.glo_num)
+    assert np.array_equal(off, ro) and np.array_equal(mem, rm)
+    npts, ng, ns = gs.info()
+    assert npts == mesh.npts and ng == len(ro) - 1 and ns == len(rm)
+
+
+def test_gs_plan_non_lattice_ids():
+    """Sparse, shuffled global ids (the sort-based plan path)."""
+    rng = np.random.default_rng(4)
+    glo = rng.integers(0, 40, size=(3, 27)) * 1_000_003
+    gs = nekax.GsPlan(3, 3, glo)
+    off, mem = gs.export()
+    ro, rm = ref.gs_build(glo)
+    assert np.array_equal(off, ro) and np.array_equal(mem, rm)
+
+
+@pytest.mark.parametrize("dims,nx", [((3, 3, 3), 5), ((8, 4, 2), 10)])
+def test_dssum_bit_exact(dims, nx):
+    mesh = inputs.box_mesh(*dims, nx, perturb=0.0)
+    gs = nekax.GsPlan(mesh.nelt, nx, mesh.glo_num)
+    v = inputs.random_local_field(mesh.nelt, nx, seed=3) * 10.0 ** np.random.default_rng(1).uniform(-8, 8, (1, nx ** 3))
+    vd = _t(v)
+    gs.dssum(vd)
+    ro, rm = ref.gs_build(mesh.glo_num)
+    assert np.array_equal(vd.cpu().numpy(), ref.dssum(ro, rm, v))
+    c = torch.empty_like(vd)
+    gs.inv_multiplicity(c)
+    assert np.array_equal(c.cpu().numpy().reshape(-1), ref.inv_multiplicity(mesh.npts, ro, rm))
+
+
+def test_mask_and_dot():
+    mesh = inputs.box_mesh(4, 3, 2, 6, perturb=0.1)
+    gs = nekax.GsPlan(mesh.nelt, 6, mesh.glo_num)
+    v = inputs.random_local_field(mesh.nelt, 6, seed=8)
+    vd = _t(v)
+    nekax.mask(mesh.npts, _t(mesh.mask), vd)
+    assert np.array_equal(vd.cpu().numpy(), ref.mask_apply(mesh.mask, v))
+    a = inputs.random_global_field(mesh, seed=1)
+    b = inputs.random_global_field(mesh, seed=2)
+    out = torch.zeros(1, dtype=torch.float64, device=DEV)
+    nekax.dot_c(gs, _t(a), _t(b), out)
+    ro, rm = ref.gs_build(mesh.glo_num)
+    c = ref.inv_multiplicity(mesh.npts, ro, rm)
+    expect = float(np.sum(c * a.reshape(-1) * b.reshape(-1)))
+    assert abs(float(out.item()) - expect) <= 1e-13 * np.sum(np.abs(c * a.reshape(-1) * b.reshape(-1)))
+
+
+# ------------------------------------------------------------------ Jacobi / CG
+@pytest.mark.parametrize("dims,nx", [((2, 2, 2), 4), ((4, 3, 2), 7)])
+def test_jacobi_minv_parity(dims, nx):
+    mesh = inputs.box_mesh(*dims, nx, perturb=0.15, seed=2)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    assert _rel(P.minv.cpu().numpy(), Pr.minv) <= 1e-13
+
+
+@pytest.mark.parametrize("dims,nx", [((3, 3, 3), 6), ((4, 2, 3), 8), ((2, 2, 2), 10)])
+def test_cg_parity(dims, nx):
+    mesh = inputs.box_mesh(*dims, nx, perturb=0.1, seed=3)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=4)
+    x = torch.full((mesh.nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+    res = P.cg(_t(f), x, tol=1e-8, max_iter=2000)
+    assert res["status"] == nekax.OK, res
+    st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 1e-8, 2000)
+    assert st == ref.OK
+    assert abs(res["iters"] - itr) <= 2, (res["iters"], itr)
+    xg = x.cpu().numpy()
+    assert Pr.residual(f, xg) <= 1e-8 * (1 + 1e-3)
+    assert _rel(xg, xr) <= 1e-6
+
+
+def test_cg_check_every_does_not_change_result():
+    mesh = inputs.box_mesh(3, 3, 2, 6, perturb=0.1, seed=6)
+    P = DeviceProblem(mesh, DEV)
+    f = _t(inputs.random_global_field(mesh, seed=1))
+    x1 = torch.empty_like(f)
+    x2 = torch.empty_like(f)
+    r1 = P.cg(f, x1, tol=1e-9, max_iter=1000, check_every=1)
+    r2 = P.cg(f, x2, tol=1e-9, max_iter=1000, check_every=7)
+    assert r1["status"] == r2["status"] == nekax.OK
+    assert r1["iters"] == r2["iters"]
+    assert torch.equal(x1, x2)
+
+
+def test_cg_fixed_iterations_and_timing():
+    mesh = inputs.box_mesh(4, 4, 4, 8, perturb=0.1, seed=7)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=2)
+    x = torch.empty((mesh.nelt, 512), dtype=torch.float64, device=DEV)
+    ws = torch.empty(nekax.cg_workspace_bytes(mesh.nelt, 8, False) // 8 + 32, dtype=torch.float64, device=DEV)
+    res = P.cg(_t(f), x, tol=0.0, max_iter=25, workspace=ws, time_ax=True)
+    assert res["status"] == nekax.OK and res["iters"] == 25
+    assert res["ax_launches"] == 25 and res["ax_ms_total"] > 0
+    st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 0.0, 25)
+    assert itr == 25
+    assert _rel(x.cpu().numpy(), xr) <= 1e-9
+    assert abs(res["relres"] - rr) <= 1e-6 * rr
+
+
+def test_cg_special_cases_and_failures():
+    # no unknowns: x = 0, 0 iterations
+    m0 = inputs.box_mesh(1, 1, 1, 2, perturb=0.0)
+    P0 = DeviceProblem(m0, DEV)
+    f0 = _t(inputs.random_global_field(m0, seed=1))
+    x0 = torch.full_like(f0, 7.0)
+    r = P0.cg(f0, x0, tol=1e-8)
+    assert r["status"] == nekax.OK and r["iters"] == 0 and float(x0.abs().max()) == 0.0
+    # one unknown: one iteration, x = b / A_pp
+    m1 = inputs.box_mesh(1, 1, 1, 3, perturb=0.0)
+    P1 = DeviceProblem(m1, DEV)
+    f1 = inputs.random_global_field(m1, seed=1)
+    x1 = torch.empty((1, 27), dtype=torch.float64, device=DEV)
+    r = P1.cg(_t(f1), x1, tol=1e-12)
+    assert r["status"] == nekax.OK and r["iters"] == 1
+    Pr = ref.Problem(m1)
+    A_pp = ref.element_matrix(Pr.D, Pr.G[0])[13, 13]
+    assert abs(float(x1[0, 13]) - f1[0, 13] / A_pp) <= 1e-14 * abs(f1[0, 13] / A_pp)
+    # max_iter reached
+    m = inputs.box_mesh(3, 3, 3, 6, perturb=0.1, seed=2)
+    P = DeviceProblem(m, DEV)
+    f = _t(inputs.random_global_field(m, seed=3))
+    x = torch.empty_like(f)
+    r = P.cg(f, x, tol=1e-14, max_iter=3)
+    assert r["status"] == nekax.ERR_NOT_CONVERGED and r["iters"] == 3
+    # NaN in f -> breakdown
+    fn = f.clone()
+    fn[13, 3 + 6 * 3 + 36 * 3] = float("nan")  # node (3,3,3) of the centre element: interior
+    r = P.cg(fn, x, tol=1e-8, max_iter=50)
+    assert r["status"] == nekax.ERR_BREAKDOWN
+    # indefinite operator (negated G) -> p.Ap <= 0 -> breakdown on the first iteration
+    r = nekax.cg_solve(P.gs, m.nelt, 6, P.D, -P.G, P.mask, P.minv.abs(), f, x, 1e-8, 50)
+    assert r["status"] == nekax.ERR_BREAKDOWN and r["iters"] == 1
