@@ -140,6 +140,27 @@ nek_status nek_jacobi_minv(const nek_gs* gs, int64_t nelt, int nx, const double*
  * first call for a plan and kept with it).  Async. */
 nek_status nek_dot_c(const nek_gs* gs, const double* a, const double* b, double* result, void* stream);
 
+/* Allocation-free form of nek_dot_c for callers that must not allocate device
+ * memory, e.g. code running between the set-up and tear-down of a host
+ * framework that owns every device allocation, or a control loop that may not
+ * call cudaMalloc/cudaFree (they synchronise the device).  The paper has no
+ * counterpart; it is an interface convenience.
+ *   n: number of points, 0 <= n <= 2^31-1 (larger n returns NEK_ERR_TOO_LARGE);
+ *   c: weights (e.g. nek_gs_inv_multiplicity), a, b: inputs, result: output
+ *      (1 double) -- all device pointers owned by the caller.
+ *   result[0] = sum_p c_p a_p b_p, computed by the same kernels and grid as
+ *   nek_dot_c, so the two agree bit for bit on the same inputs.
+ * The per-block partial sums live in a fixed 9.5 KB array inside the library
+ * (held on every GPU that loads it until the process exits); nothing is
+ * allocated or freed.  The first call on a device looks the array's device
+ * address up (which can load the library's GPU module); make that first call
+ * before any stream capture.  All calls on a device share the array: calls that
+ * overlap on the GPU (different streams, no ordering) race and may return wrong
+ * sums.  Async on stream.
+ */
+nek_status nek_dot_c_noalloc(int64_t n, const double* c, const double* a, const double* b, double* result,
+                             void* stream);
+
 /* ----------------------------------------------------------------- CG ---
  * Jacobi-preconditioned conjugate gradients on the masked, assembled operator
  * (Section II-B: vector operations, AX, nearest-neighbour exchange and global

@@ -1,6 +1,7 @@
 // Status handling, GLL, mask, gather-scatter plan and dssum, weighted dot.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -92,11 +93,63 @@ __global__ void __launch_bounds__(kReduceThreads) k_sum_partials(const double* _
     if (threadIdx.x == 0) out[0] = t;
 }
 
+// Scratch of nek_dot_c_noalloc: one partial sum per reduction block.  It is part
+// of the library image, so every GPU that loads the library holds these
+// kNoAllocPartials doubles (9.5 KB) until the process exits, and all calls on a
+// device share them.
+constexpr int kNoAllocPartials = kMaxReduceBlocks;
+constexpr int64_t kNoAllocMaxPoints = (int64_t(1) << 31) - 1;
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_partials on the current device.  In host code the
+// symbol's name is only a host-side stand-in, so the address is looked up once
+// per device with cudaGetSymbolAddress (which may load the module) and cached.
+nek_status noalloc_scratch(double** out)
+{
+    int dev = 0;
+    nek_status st = check_cuda(cudaGetDevice(&dev));
+    if (st != NEK_OK) return st;
+    if (dev < 0 || dev >= kMaxDevices) return NEK_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        st = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_partials));
+        if (st != NEK_OK) return st;
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return NEK_OK;
+}
+}  // namespace
+
 }  // namespace nek
 
 using namespace nek;
 
 extern "C" {
+
+nek_status nek_dot_c_noalloc(int64_t n, const double* c, const double* a, const double* b, double* result,
+                             void* stream)
+{
+    if (n < 0 || !result) return NEK_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxPoints) return NEK_ERR_TOO_LARGE;
+    if (n > 0 && (!c || !a || !b)) return NEK_ERR_INVALID_ARG;
+    double* parts = nullptr;
+    nek_status st = noalloc_scratch(&parts);
+    if (st != NEK_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nb = reduce_blocks(n);  // <= kNoAllocPartials; every partial read below is written first
+    k_dot_c_partials<<<nb, kReduceThreads, 0, s>>>(n, c, a, b, parts);
+    st = check_launch();
+    if (st != NEK_OK) return st;
+    k_sum_partials<<<1, kReduceThreads, 0, s>>>(parts, nb, result);
+    return check_launch();
+}
 
 const char* nek_status_string(int status)
 {

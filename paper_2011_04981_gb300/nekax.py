@@ -67,6 +67,7 @@ _SIGS = {
     "nek_mask": ([_I64, _P, _P, _P], _I),
     "nek_jacobi_minv": ([_P, _I64, _I, _P, _P, _P, _P, _P], _I),
     "nek_dot_c": ([_P, _P, _P, _P, _P], _I),
+    "nek_dot_c_noalloc": ([_I64, _P, _P, _P, _P, _P], _I),
     "nek_cg_workspace_bytes": ([_I64, _I, _I], ctypes.c_size_t),
     "nek_cg_solve": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, _P], _I),
     "nek_cg_solve_ex": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, ctypes.POINTER(NekCgOpts), _P],
@@ -202,6 +203,12 @@ def jacobi_minv(gs: GsPlan, nelt, nx, D, G, m, minv, stream=None):
 
 def dot_c(gs: GsPlan, a, b, result, stream=None):
     _check("nek_dot_c", load().nek_dot_c(gs.handle, _ptr(a), _ptr(b), _ptr(result), _stream(stream)))
+
+
+def dot_c_noalloc(n, c, a, b, result, stream=None):
+    """nek_dot_c_noalloc: the weighted dot with library-resident scratch (no allocation)."""
+    _check("nek_dot_c_noalloc", load().nek_dot_c_noalloc(n, _ptr(c), _ptr(a), _ptr(b), _ptr(result),
+                                                         _stream(stream)))
 
 
 def cg_workspace_bytes(nelt, nx, need_minv=True) -> int:
