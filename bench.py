@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--sweep", action="store_true", help="also time standalone AX at nx = 8, 10, 12, 16")
     ap.add_argument("--solve", action="store_true", help="also time one solve to 1e-8 relative residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ax", default="fp64", choices=["fp64", "ff"],
+                    help="AX operator inside the solve: native FP64 or FP64-accurate float-float")
     return ap.parse_args()
 
 
@@ -197,23 +199,27 @@ def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10):
     for nx in nxs:
         mesh = inputs.box_mesh(32, 32, 32, nx, perturb=0.1, seed=1)
         P = DeviceProblem(mesh, "cuda", build_minv=False)
+        P.prepare_ff()
         u = torch.rand((mesh.nelt, nx ** 3), dtype=torch.float64, device="cuda") * 2 - 1
         w = torch.empty_like(u)
         s = torch.cuda.current_stream()
-        for _ in range(3):
-            P.ax(u, w)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(s)
-        for _ in range(reps):
-            P.ax(u, w)
-        e1.record(s)
-        e1.synchronize()
-        t = e0.elapsed_time(e1) / reps / 1e3
-        g = mesh.npts / t / 1e9
-        out[str(nx)] = {"gdofs": g, "ms": t * 1e3, "gflops": g * perfmodel.ax_flops_per_point(nx),
-                        "hbm_frac": g * 64 / hbm, "fp64_frac": g * perfmodel.ax_flops_per_point(nx) / 1e3 /
-                        FP64_PEAK_TFLOPS}
+        res = {}
+        for name, fn in (("fp64", P.ax), ("ff", P.ax_ff)):
+            for _ in range(3):
+                fn(u, w)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(s)
+            for _ in range(reps):
+                fn(u, w)
+            e1.record(s)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / reps / 1e3
+            g = mesh.npts / t / 1e9
+            res[name] = {"gdofs": g, "ms": t * 1e3, "gflops": g * perfmodel.ax_flops_per_point(nx),
+                         "hbm_frac": g * 64 / hbm,
+                         "fp64_frac": g * perfmodel.ax_flops_per_point(nx) / 1e3 / FP64_PEAK_TFLOPS}
+        out[str(nx)] = res
         del P, u, w
         torch.cuda.empty_cache()
     return out
@@ -248,8 +254,11 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     iters = args.iters
 
+    ax_impl = nekax.AX_FF if args.ax == "ff" else nekax.AX_FP64
+    if ax_impl == nekax.AX_FF:
+        P.prepare_ff()
     for _ in range(args.warmup):
-        P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws)
+        P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, ax_impl=ax_impl)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -261,7 +270,7 @@ def run_native(args):
     ax_ms, ax_n, launches = 0.0, 0, 0
     e0.record(stream)
     for _ in range(args.steps):
-        r = P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, time_ax=True)
+        r = P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, time_ax=True, ax_impl=ax_impl)
         ax_ms += r["ax_ms_total"]
         ax_n += r["ax_launches"]
         launches += r["kernel_launches"]
@@ -279,7 +288,7 @@ def run_native(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         f.copy_(f_host, non_blocking=True)
-        P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws)
+        P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, ax_impl=ax_impl)
         x_host.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
@@ -324,7 +333,7 @@ def run_native(args):
     if args.solve and rank == 0:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = P.cg(f, x, tol=1e-8, max_iter=20000, workspace=ws, check_every=20)
+        r = P.cg(f, x, tol=1e-8, max_iter=20000, workspace=ws, check_every=20, ax_impl=ax_impl)
         torch.cuda.synchronize()
         line["cg_to_1e-8"] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"],
                               "status": nekax.status_string(r["status"]), "precision": "fp64 jacobi-pcg"}

@@ -90,6 +90,28 @@ nek_status nek_geom(int64_t nelt, int nx, const double* corners, double* G, void
 nek_status nek_ax(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w,
                   void* stream);
 
+/*
+ * Geometric factors split into float pairs for nek_ax_ff (device, async):
+ * Gff[e][p][2a] + Gff[e][p][2a+1] = G[e][p][a] to ~2^-48 relative, a = 0..5,
+ * i.e. 12 floats (48 bytes) per point, the same size as the FP64 layout.
+ * G: device, 8-byte aligned; Gff: device, 16-byte aligned, must not overlap G.
+ * Values must lie in the normal FP32 range (|g| in about [1e-30, 1e30]).
+ */
+nek_status nek_geom_ff(int64_t nelt, int nx, const double* G, float* Gff, void* stream);
+
+/*
+ * w = AX(u) to FP64 accuracy computed on the FP32 pipes (the operator of
+ * Section II-B, Listing 1, in float-float arithmetic).  Same arguments and
+ * layouts as nek_ax except Gff (from nek_geom_ff); u, w 8-byte aligned, no
+ * overlap.  Every value is carried as a pair of floats (~48 significant bits)
+ * and every sum is formed with exact residual tracking; the result matches the
+ * FP64 operator to ~1e-14 relative in the max norm.  Element blocks whose
+ * largest |u| is below ~1e-30 (or contain non-finite values) are not covered by
+ * that accuracy statement.  Async on stream.
+ */
+nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+                     void* stream);
+
 /* ------------------------------------------------------- gather-scatter ---
  * Direct stiffness summation over shared face, edge and corner nodes (the
  * nearest-neighbour exchange of Section II-B).  A plan groups every local node
@@ -183,12 +205,19 @@ nek_status nek_dot_c_noalloc(int64_t n, const double* c, const double* a, const 
  */
 size_t nek_cg_workspace_bytes(int64_t nelt, int nx, int need_minv);
 
+typedef enum {
+    NEK_AX_FP64 = 0, /* nek_ax: native FP64 */
+    NEK_AX_FF = 1    /* nek_ax_ff: FP64-accurate float-float on the FP32 pipes; needs Gff */
+} nek_ax_impl;
+
 typedef struct {
     int check_every;     /* residual read-back period in iterations (>=1; default 1) */
     int time_ax;         /* nonzero: record CUDA events around every AX launch */
     double ax_ms_total;  /* out: summed AX kernel time when time_ax */
     int ax_launches;     /* out: number of AX launches */
     int kernel_launches; /* out: kernels this call enqueued */
+    int ax_impl;         /* nek_ax_impl; default NEK_AX_FP64 */
+    const float* Gff;    /* device, from nek_geom_ff, required for NEK_AX_FF */
 } nek_cg_opts;
 
 nek_status nek_cg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,

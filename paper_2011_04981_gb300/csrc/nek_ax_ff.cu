@@ -1,0 +1,450 @@
+// AX operator to FP64 accuracy on the FP32 pipes (float-float arithmetic).
+//
+// Same operator as nek_ax (Section II-B, Listing 1 of arXiv 2011.04981).  On
+// GB300 the FP64 pipe runs 2 DFMA/clk/SM against 128 FFMA/clk/SM, so native
+// FP64 AX is bound by the FP64 pipe at ~8% of the HBM roofline.  This kernel
+// keeps every value as an unevaluated pair hi + lo of floats (about 48
+// significant bits) and does all arithmetic on the FP32 pipes, two k-planes per
+// instruction with the packed f32x2 operations of sm_100+.
+//
+// Contractions use an offset accumulator.  For a sum y = sum_l a_l b_l whose
+// terms are bounded by B (sum_l |a_l||b_l| <= B), the running sum is kept as
+// S = sigma + partial with sigma = 1.5 * 2^m and 2^m > 2B, so S stays in the
+// binade [2^m, 2^(m+1)) and every rounding of S is to the same grid 2^(m-23):
+//   t = fma(ah, bh, S);  d = S - t (exact);  r = fma(ah, bh, d)
+// gives the residual of the exact product to 2^-24 of itself (|r| <= 2^(m-24)).
+// The residuals are summed the same way on a second offset S2 = sigma * 2^-18
+// (grid 2^(m-41)), whose own exact residuals and the cross products
+// ah*bl + al*bh go to a plain float c.  The result is (S - sigma) + (S2 - sigma2)
+// + c, all exact differences, with an absolute error of about n * 2^(m-48),
+// i.e. 2^-44 B.  Bounds come from the element maximum of |u| (|wr|,|ws|,|wt| in
+// the second phase) times the absolute row (column) sums of D.
+//
+// The pointwise geometric product uses Dekker products (FMA-exact) and Knuth
+// two-sums.  Inputs: u and w in FP64, D in FP64 (split on load), G pre-split by
+// nek_geom_ff into [e][p][12] floats (48 B per point, the same HBM traffic as
+// FP64 G).
+#include <type_traits>
+
+#include "nek_internal.h"
+
+namespace nek {
+
+namespace {
+
+// ---------------------------------------------------------------- f32 / f32x2 arithmetic
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+template <class T>
+__device__ __forceinline__ T splat(float x);
+template <>
+__device__ __forceinline__ float splat<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float2 splat<float2>(float x) { return make_float2(x, x); }
+
+template <class T>
+__device__ __forceinline__ T vzero() { return splat<T>(0.f); }
+
+// Knuth two-sum: s + e = a + b exactly.
+template <class T>
+__device__ __forceinline__ void two_sum(T a, T b, T& s, T& e)
+{
+    s = vadd(a, b);
+    const T bb = vsub(s, a);
+    e = vadd(vsub(a, vsub(s, bb)), vsub(b, bb));
+}
+
+// 1.5 * 2^(floor(log2 b) + 2): offset whose binade holds any partial sum bounded by b.
+__device__ __forceinline__ float offset_for(float b)
+{
+    return __fmul_rn(__int_as_float(__float_as_int(b) & 0x7F800000), 6.0f);
+}
+__device__ __forceinline__ float2 offset_for(float2 b) { return make_float2(offset_for(b.x), offset_for(b.y)); }
+
+template <class T>
+struct OffsetAcc {
+    T S, S2, c, s1, s2;
+    __device__ __forceinline__ void init(T sigma)
+    {
+        s1 = sigma;
+        s2 = vmul(sigma, splat<T>(3.814697265625e-06f));  // 2^-18
+        S = s1;
+        S2 = s2;
+        c = vzero<T>();
+    }
+    // += (ah + al) * (bh + bl)
+    __device__ __forceinline__ void add(T ah, T al, T bh, T bl)
+    {
+        const T t = vfma(ah, bh, S);
+        const T d = vsub(S, t);
+        const T r = vfma(ah, bh, d);
+        const T t2 = vadd(S2, r);
+        const T d2 = vsub(S2, t2);
+        const T r2 = vadd(r, d2);
+        c = vadd(c, r2);
+        c = vfma(ah, bl, c);
+        c = vfma(al, bh, c);
+        S = t;
+        S2 = t2;
+    }
+    __device__ __forceinline__ void finish(T& hi, T& lo) const
+    {
+        const T H1 = vsub(S, s1);
+        const T H2 = vsub(S2, s2);
+        T e;
+        two_sum(H1, H2, hi, e);
+        lo = vadd(e, c);
+    }
+};
+
+// Dekker product with FMA: p + e = (ah + al)(bh + bl) to ~2^-48.
+template <class T>
+__device__ __forceinline__ void df_mul(T ah, T al, T bh, T bl, T& p, T& e)
+{
+    p = vmul(ah, bh);
+    e = vfma(ah, bh, vneg(p));
+    e = vfma(ah, bl, e);
+    e = vfma(al, bh, e);
+}
+
+// (ah,al)(xh,xl) + (bh,bl)(yh,yl) + (ch,cl)(zh,zl) as an unevaluated pair.
+template <class T>
+__device__ __forceinline__ void df_dot3(T ah, T al, T xh, T xl, T bh, T bl, T yh, T yl, T ch, T cl, T zh, T zl,
+                                        T& h, T& l)
+{
+    T p1, e1, p2, e2, p3, e3, s, f1, f2;
+    df_mul(ah, al, xh, xl, p1, e1);
+    df_mul(bh, bl, yh, yl, p2, e2);
+    df_mul(ch, cl, zh, zl, p3, e3);
+    two_sum(p1, p2, s, f1);
+    two_sum(s, p3, h, f2);
+    l = vadd(vadd(vadd(e1, e2), vadd(e3, f1)), f2);
+}
+
+__device__ __forceinline__ float2 split_double(double x)
+{
+    const float h = __double2float_rn(x);
+    const float l = __double2float_rn(x - (double)h);
+    return make_float2(h, l);
+}
+
+__device__ __forceinline__ float absmax_bits(float a, float b) { return fmaxf(fabsf(a), b); }
+
+// Lane access for the 1- and 2-wide forms.
+template <class T>
+struct Lanes;
+template <>
+struct Lanes<float> {
+    static constexpr int W = 1;
+    __device__ static __forceinline__ float get(float v, int) { return v; }
+    __device__ static __forceinline__ void set(float& v, int, float x) { v = x; }
+};
+template <>
+struct Lanes<float2> {
+    static constexpr int W = 2;
+    __device__ static __forceinline__ float get(float2 v, int q) { return q ? v.y : v.x; }
+    __device__ static __forceinline__ void set(float2& v, int q, float x)
+    {
+        if (q)
+            v.y = x;
+        else
+            v.x = x;
+    }
+};
+
+template <int NX>
+constexpr int ff_epb()
+{
+    return NX == 2 ? 32 : NX == 3 ? 32 : NX == 4 ? 8 : NX == 5 ? 16 : NX == 6 ? 8 : NX == 7 ? 8 : NX == 8 ? 4
+         : NX == 9 ? 4 : NX == 10 ? 4 : NX == 11 ? 2 : NX == 12 ? 2 : NX == 13 ? 2 : 1;
+}
+
+template <int NX, int EPB>
+constexpr size_t ff_smem_bytes()
+{
+    // three float2 blocks [EPB][N3] (u, ws, wr), D and D^T as float2 pairs,
+    // rowabs, colabs and the per-element maxima.
+    return sizeof(float2) * (3 * EPB * NX * NX * NX + 2 * NX * NX) + sizeof(float) * (2 * NX + 4 * EPB + 4) + 16;
+}
+
+template <int NX, int EPB>
+__global__ void __launch_bounds__(NX* NX* EPB, 1) k_ax_ff(int64_t nelt, const double* __restrict__ D,
+                                                           const float4* __restrict__ Gff,
+                                                           const double* __restrict__ u, double* __restrict__ w)
+{
+    using T = typename std::conditional<(NX % 2 == 0), float2, float>::type;
+    using L = Lanes<T>;
+    constexpr int W = L::W;
+    constexpr int N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sU = reinterpret_cast<float2*>(smem_raw);  // [EPB][N3] u (hi, lo)
+    float2* sWs = sU + EPB * N3;                       // [EPB][N3] ws
+    float2* sWr = sWs + EPB * N3;                      // [EPB][N3] wr
+    float2* sD = sWr + EPB * N3;                       // D[i][l]   at i*NX+l
+    float2* sDT = sD + N2;                             // D[k][l]   at l*NX+k
+    float* sRow = reinterpret_cast<float*>(sDT + N2);  // sum_l |D[q][l]|
+    float* sCol = sRow + NX;                           // sum_l |D[l][q]|
+    float* sMax = sCol + NX;  // [EPB][4]: max |u|, |wr|, |ws|, |wt| (non-negative floats, compared as ints)
+
+    const int tid = threadIdx.x;
+    const int64_t e0 = (int64_t)blockIdx.x * EPB;
+    const int ne = static_cast<int>(nelt - e0 < EPB ? nelt - e0 : EPB);
+
+    for (int q = tid; q < N2; q += NT) {
+        const float2 d = split_double(D[q]);
+        sD[q] = d;
+        sDT[(q % NX) * NX + q / NX] = d;
+    }
+    for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
+    {
+        const double* src = u + e0 * N3;
+        for (int q = tid; q < ne * N3; q += NT) sU[q] = split_double(__ldg(src + q));
+    }
+    __syncthreads();
+    for (int q = tid; q < NX; q += NT) {
+        float r = 0.f, c = 0.f;
+        for (int l = 0; l < NX; l++) {
+            r += fabsf(sD[q * NX + l].x);
+            c += fabsf(sD[l * NX + q].x);
+        }
+        // inflate for the lo parts and the rounding of the sums themselves
+        sRow[q] = r * 1.0001f;
+        sCol[q] = c * 1.0001f;
+    }
+
+    const int el = tid / N2;
+    const int q2 = tid - el * N2;
+    const int i = q2 % NX, j = q2 / NX;
+    const bool active = el < ne;
+    const float2* ue = sU + el * N3;
+
+    // Column of u along k and its maximum.
+    float2 ucol[NX];
+    if (active) {
+        float m = 0.f;
+#pragma unroll
+        for (int l = 0; l < NX; l++) {
+            ucol[l] = ue[i + NX * (j + NX * l)];
+            m = absmax_bits(ucol[l].x, m);
+        }
+        atomicMax(reinterpret_cast<int*>(sMax + 4 * el), __float_as_int(m));
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------- phase 1
+    float2 wtcol[NX];
+    if (active) {
+        const float umax = sMax[4 * el] * 1.0001f;
+        const T sig_r = splat<T>(offset_for(sRow[i] * umax));
+        const T sig_s = splat<T>(offset_for(sRow[j] * umax));
+        const float4* Ge = Gff + (e0 + el) * (int64_t)N3 * 3;
+        float2* wse = sWs + el * N3;
+        float2* wre = sWr + el * N3;
+        float mr = 0.f, ms = 0.f, mt = 0.f;
+#pragma unroll
+        for (int k0 = 0; k0 < NX; k0 += W) {
+            OffsetAcc<T> ar, as, at;
+            T sig_t;
+#pragma unroll
+            for (int q = 0; q < W; q++) L::set(sig_t, q, offset_for(sRow[k0 + q] * umax));
+            ar.init(sig_r);
+            as.init(sig_s);
+            at.init(sig_t);
+#pragma unroll
+            for (int l = 0; l < NX; l++) {
+                T uh, ul, vh, vl, dh, dl;
+#pragma unroll
+                for (int q = 0; q < W; q++) {
+                    const float2 a = ue[l + NX * (j + NX * (k0 + q))];
+                    const float2 b = ue[i + NX * (l + NX * (k0 + q))];
+                    const float2 d = sDT[l * NX + k0 + q];
+                    L::set(uh, q, a.x);
+                    L::set(ul, q, a.y);
+                    L::set(vh, q, b.x);
+                    L::set(vl, q, b.y);
+                    L::set(dh, q, d.x);
+                    L::set(dl, q, d.y);
+                }
+                const float2 dr = sD[i * NX + l], ds = sD[j * NX + l];
+                ar.add(splat<T>(dr.x), splat<T>(dr.y), uh, ul);
+                as.add(splat<T>(ds.x), splat<T>(ds.y), vh, vl);
+                at.add(dh, dl, splat<T>(ucol[l].x), splat<T>(ucol[l].y));
+            }
+            T urh, url, ush, usl, uth, utl;
+            ar.finish(urh, url);
+            as.finish(ush, usl);
+            at.finish(uth, utl);
+            // geometric factors of the W points: g[2a], g[2a+1] = hi, lo of factor a
+            T g[12];
+#pragma unroll
+            for (int q = 0; q < W; q++) {
+                const int p = i + NX * (j + NX * (k0 + q));
+                const float4 a = __ldg(Ge + 3 * p), b = __ldg(Ge + 3 * p + 1), c = __ldg(Ge + 3 * p + 2);
+                L::set(g[0], q, a.x); L::set(g[1], q, a.y); L::set(g[2], q, a.z); L::set(g[3], q, a.w);
+                L::set(g[4], q, b.x); L::set(g[5], q, b.y); L::set(g[6], q, b.z); L::set(g[7], q, b.w);
+                L::set(g[8], q, c.x); L::set(g[9], q, c.y); L::set(g[10], q, c.z); L::set(g[11], q, c.w);
+            }
+            T wrh, wrl, wsh, wsl, wth, wtl;
+            df_dot3(g[0], g[1], urh, url, g[2], g[3], ush, usl, g[4], g[5], uth, utl, wrh, wrl);
+            df_dot3(g[2], g[3], urh, url, g[6], g[7], ush, usl, g[8], g[9], uth, utl, wsh, wsl);
+            df_dot3(g[4], g[5], urh, url, g[8], g[9], ush, usl, g[10], g[11], uth, utl, wth, wtl);
+#pragma unroll
+            for (int q = 0; q < W; q++) {
+                const int p = i + NX * (j + NX * (k0 + q));
+                wre[p] = make_float2(L::get(wrh, q), L::get(wrl, q));
+                wse[p] = make_float2(L::get(wsh, q), L::get(wsl, q));
+                wtcol[k0 + q] = make_float2(L::get(wth, q), L::get(wtl, q));
+                mr = absmax_bits(L::get(wrh, q), mr);
+                ms = absmax_bits(L::get(wsh, q), ms);
+                mt = absmax_bits(L::get(wth, q), mt);
+            }
+        }
+        atomicMax(reinterpret_cast<int*>(sMax + 4 * el + 1), __float_as_int(mr));
+        atomicMax(reinterpret_cast<int*>(sMax + 4 * el + 2), __float_as_int(ms));
+        atomicMax(reinterpret_cast<int*>(sMax + 4 * el + 3), __float_as_int(mt));
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------- phase 2
+    if (active) {
+        const float2* wre = sWr + el * N3;
+        const float2* wse = sWs + el * N3;
+        const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
+                    mwt = sMax[4 * el + 3] * 1.0001f;
+        const float bij = sCol[i] * mwr + sCol[j] * mws;
+        double* we = w + (e0 + el) * (int64_t)N3;
+#pragma unroll
+        for (int k0 = 0; k0 < NX; k0 += W) {
+            T sig;
+#pragma unroll
+            for (int q = 0; q < W; q++) L::set(sig, q, offset_for(bij + sCol[k0 + q] * mwt));
+            OffsetAcc<T> acc;
+            acc.init(sig);
+#pragma unroll
+            for (int l = 0; l < NX; l++) {
+                T ah, al, bh, bl, dh, dl;
+#pragma unroll
+                for (int q = 0; q < W; q++) {
+                    const float2 a = wre[l + NX * (j + NX * (k0 + q))];
+                    const float2 b = wse[i + NX * (l + NX * (k0 + q))];
+                    const float2 d = sD[l * NX + k0 + q];
+                    L::set(ah, q, a.x);
+                    L::set(al, q, a.y);
+                    L::set(bh, q, b.x);
+                    L::set(bl, q, b.y);
+                    L::set(dh, q, d.x);
+                    L::set(dl, q, d.y);
+                }
+                const float2 ci = sD[l * NX + i], cj = sD[l * NX + j];
+                acc.add(splat<T>(ci.x), splat<T>(ci.y), ah, al);
+                acc.add(splat<T>(cj.x), splat<T>(cj.y), bh, bl);
+                acc.add(dh, dl, splat<T>(wtcol[l].x), splat<T>(wtcol[l].y));
+            }
+            T hi, lo;
+            acc.finish(hi, lo);
+#pragma unroll
+            for (int q = 0; q < W; q++) {
+                const int p = i + NX * (j + NX * (k0 + q));
+                we[p] = (double)L::get(hi, q) + (double)L::get(lo, q);
+            }
+        }
+    }
+}
+
+template <int NX>
+nek_status launch_ax_ff_nx(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
+                           cudaStream_t s)
+{
+    constexpr int EPB = ff_epb<NX>();
+    constexpr size_t smem = ff_smem_bytes<NX, EPB>();
+    static bool configured = false;
+    if (!configured) {
+        nek_status st = check_cuda(
+            cudaFuncSetAttribute(k_ax_ff<NX, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (st != NEK_OK) return st;
+        configured = true;
+    }
+    const int64_t blocks = (nelt + EPB - 1) / EPB;
+    if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
+    k_ax_ff<NX, EPB><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(nelt, D, reinterpret_cast<const float4*>(Gff),
+                                                                     u, w);
+    return check_launch();
+}
+
+// G (FP64, [e][p][6]) -> float-float [e][p][12] = (h0,l0,h1,l1,...,h5,l5).
+__global__ void k_g_to_ff(int64_t npts, const double* __restrict__ G, float2* __restrict__ Gff)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npts * 6;
+         q += (int64_t)gridDim.x * blockDim.x)
+        Gff[q] = split_double(G[q]);
+}
+
+}  // namespace
+
+nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+                        cudaStream_t s)
+{
+    switch (nx) {
+        case 2: return launch_ax_ff_nx<2>(nelt, D, Gff, u, w, s);
+        case 3: return launch_ax_ff_nx<3>(nelt, D, Gff, u, w, s);
+        case 4: return launch_ax_ff_nx<4>(nelt, D, Gff, u, w, s);
+        case 5: return launch_ax_ff_nx<5>(nelt, D, Gff, u, w, s);
+        case 6: return launch_ax_ff_nx<6>(nelt, D, Gff, u, w, s);
+        case 7: return launch_ax_ff_nx<7>(nelt, D, Gff, u, w, s);
+        case 8: return launch_ax_ff_nx<8>(nelt, D, Gff, u, w, s);
+        case 9: return launch_ax_ff_nx<9>(nelt, D, Gff, u, w, s);
+        case 10: return launch_ax_ff_nx<10>(nelt, D, Gff, u, w, s);
+        case 11: return launch_ax_ff_nx<11>(nelt, D, Gff, u, w, s);
+        case 12: return launch_ax_ff_nx<12>(nelt, D, Gff, u, w, s);
+        case 13: return launch_ax_ff_nx<13>(nelt, D, Gff, u, w, s);
+        case 14: return launch_ax_ff_nx<14>(nelt, D, Gff, u, w, s);
+        case 15: return launch_ax_ff_nx<15>(nelt, D, Gff, u, w, s);
+        case 16: return launch_ax_ff_nx<16>(nelt, D, Gff, u, w, s);
+        default: return NEK_ERR_UNSUPPORTED_NX;
+    }
+}
+
+}  // namespace nek
+
+using namespace nek;
+
+extern "C" {
+
+nek_status nek_geom_ff(int64_t nelt, int nx, const double* G, float* Gff, void* stream)
+{
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt < 0) return NEK_ERR_INVALID_ARG;
+    if (nelt == 0) return NEK_OK;
+    if (!G || !Gff || !is_aligned(G, 8) || !is_aligned(Gff, 16)) return NEK_ERR_INVALID_ARG;
+    const int64_t npts = nelt * (int64_t)nx * nx * nx;
+    if (ranges_overlap(G, sizeof(double) * 6 * npts, Gff, sizeof(float) * 12 * npts)) return NEK_ERR_INVALID_ARG;
+    const int64_t nb = (npts * 6 + 255) / 256;
+    const int blocks = static_cast<int>(nb < 152 * 32 ? nb : 152 * 32);
+    k_g_to_ff<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(npts, G, reinterpret_cast<float2*>(Gff));
+    return check_launch();
+}
+
+nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+                     void* stream)
+{
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt < 0) return NEK_ERR_INVALID_ARG;
+    if (nelt == 0) return NEK_OK;
+    if (!D || !Gff || !u || !w) return NEK_ERR_INVALID_ARG;
+    if (!is_aligned(D, 8) || !is_aligned(Gff, 16) || !is_aligned(u, 8) || !is_aligned(w, 8))
+        return NEK_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(double) * (size_t)nelt * nx * nx * nx;
+    if (ranges_overlap(u, bytes, w, bytes)) return NEK_ERR_INVALID_ARG;
+    return launch_ax_ff(nelt, nx, D, Gff, u, w, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

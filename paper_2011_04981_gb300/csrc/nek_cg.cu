@@ -278,6 +278,10 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
     if (workspace && !is_aligned(workspace, 256)) return NEK_ERR_INVALID_ARG;
     const int check_every = (opts && opts->check_every > 0) ? opts->check_every : 1;
     const bool time_ax = opts && opts->time_ax;
+    const int ax_impl = opts ? opts->ax_impl : NEK_AX_FP64;
+    const float* Gff = opts ? opts->Gff : nullptr;
+    if (ax_impl != NEK_AX_FP64 && ax_impl != NEK_AX_FF) return NEK_ERR_INVALID_ARG;
+    if (ax_impl == NEK_AX_FF && (!Gff || !is_aligned(Gff, 16))) return NEK_ERR_INVALID_ARG;
     if (opts) {
         opts->ax_ms_total = 0.0;
         opts->ax_launches = 0;
@@ -331,7 +335,8 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
     for (it = 1; it <= max_iter; it++) {
         const bool timed = time_ax && (size_t)(2 * it) <= ev.size();
         if (timed) cudaEventRecord(ev[2 * (it - 1)], s);
-        if ((st = launch_ax_fp64(nelt, nx, D, G, p, w, s)) != NEK_OK) goto done;
+        st = ax_impl == NEK_AX_FF ? launch_ax_ff(nelt, nx, D, Gff, p, w, s) : launch_ax_fp64(nelt, nx, D, G, p, w, s);
+        if (st != NEK_OK) goto done;
         if (timed) cudaEventRecord(ev[2 * (it - 1) + 1], s);
         if ((st = launch_dssum(gs, w, s)) != NEK_OK) goto done;
         k_cg_pw<<<nb, NT, 0, s>>>(n, gs->d_c, mask, p, w, parts, sc);

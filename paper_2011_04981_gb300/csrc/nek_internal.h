@@ -29,6 +29,8 @@ void gll_host(int nx, double* xi, double* rho, double* D);
 // Kernel launchers (arguments already validated).
 nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w,
                           cudaStream_t s);
+nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+                        cudaStream_t s);
 nek_status launch_mask(int64_t n, const uint8_t* mask, double* v, cudaStream_t s);
 nek_status launch_dssum(const nek_gs* gs, double* v, cudaStream_t s);
 

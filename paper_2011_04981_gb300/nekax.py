@@ -40,9 +40,14 @@ class NekError(RuntimeError):
         super().__init__("%s failed with %s%s" % (func, load().nek_status_string(status).decode(), detail))
 
 
+AX_FP64 = 0
+AX_FF = 1
+
+
 class NekCgOpts(ctypes.Structure):
     _fields_ = [("check_every", ctypes.c_int), ("time_ax", ctypes.c_int), ("ax_ms_total", ctypes.c_double),
-                ("ax_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+                ("ax_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int), ("ax_impl", ctypes.c_int),
+                ("Gff", ctypes.c_void_p)]
 
 
 _lib = None
@@ -58,6 +63,8 @@ _SIGS = {
     "nek_gll": ([_I, _P, _P, _P], _I),
     "nek_geom": ([_I64, _I, _P, _P, _P], _I),
     "nek_ax": ([_I64, _I, _P, _P, _P, _P, _P], _I),
+    "nek_geom_ff": ([_I64, _I, _P, _P, _P], _I),
+    "nek_ax_ff": ([_I64, _I, _P, _P, _P, _P, _P], _I),
     "nek_gs_create": ([_I64, _I, _P, ctypes.POINTER(_P)], _I),
     "nek_gs_destroy": ([_P], _I),
     "nek_gs_info": ([_P, _P, _P, _P], _I),
@@ -148,6 +155,14 @@ def ax(nelt, nx, D, G, u, w, stream=None):
     _check("nek_ax", load().nek_ax(nelt, nx, _ptr(D), _ptr(G), _ptr(u), _ptr(w), _stream(stream)))
 
 
+def geom_ff(nelt, nx, G, Gff, stream=None):
+    _check("nek_geom_ff", load().nek_geom_ff(nelt, nx, _ptr(G), _ptr(Gff), _stream(stream)))
+
+
+def ax_ff(nelt, nx, D, Gff, u, w, stream=None):
+    _check("nek_ax_ff", load().nek_ax_ff(nelt, nx, _ptr(D), _ptr(Gff), _ptr(u), _ptr(w), _stream(stream)))
+
+
 def mask(n, m, v, stream=None):
     _check("nek_mask", load().nek_mask(n, _ptr(m), _ptr(v), _stream(stream)))
 
@@ -216,11 +231,11 @@ def cg_workspace_bytes(nelt, nx, need_minv=True) -> int:
 
 
 def cg_solve(gs: GsPlan, nelt, nx, D, G, m, minv, f, x, tol=1e-8, max_iter=1000, workspace=None, check_every=1,
-             time_ax=False, stream=None):
+             time_ax=False, stream=None, ax_impl=AX_FP64, Gff=None):
     """Jacobi-PCG; returns dict(status, iters, relres, ax_ms_total, ax_launches, kernel_launches)."""
     it = _I(0)
     rr = _D(0.0)
-    opts = NekCgOpts(check_every, 1 if time_ax else 0, 0.0, 0, 0)
+    opts = NekCgOpts(check_every, 1 if time_ax else 0, 0.0, 0, 0, int(ax_impl), _ptr(Gff))
     st = load().nek_cg_solve_ex(gs.handle, nelt, nx, _ptr(D), _ptr(G), _ptr(m), _ptr(minv), _ptr(f), _ptr(x),
                                 float(tol), int(max_iter), _ptr(workspace), ctypes.byref(it), ctypes.byref(rr),
                                 ctypes.byref(opts), _stream(stream))

@@ -105,3 +105,22 @@ def test_other_entry_points_reject_bad_arguments(lib):
     n = 10 * 8 ** 3
     assert L.nek_cg_workspace_bytes(10, 8, 1) >= 5 * 8 * n
     assert L.nek_cg_workspace_bytes(10, 8, 0) >= 4 * 8 * n
+
+
+def test_ff_entry_points_reject_bad_arguments(lib):
+    L = lib
+    A16 = 0x10000
+    assert L.nek_ax_ff(4, 1, A16, A16, A16, A16 * 2, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_ax_ff(-1, 8, A16, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_ff(0, 8, None, None, None, None, None) == nekax.OK
+    assert L.nek_ax_ff(4, 8, A16, None, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_ff(4, 8, A16, A16 + 8, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # Gff misaligned
+    assert L.nek_ax_ff(4, 8, A16, A16, A16 + 4, A16 * 2, None) == nekax.ERR_INVALID_ARG  # u misaligned
+    assert L.nek_ax_ff(4, 8, A16, A16, A16, A16 + 4096, None) == nekax.ERR_INVALID_ARG  # overlap
+    assert L.nek_geom_ff(4, 1, A16, A16, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_geom_ff(4, 4, A16, A16 + 8, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_geom_ff(4, 4, A16, A16 + 64, None) == nekax.ERR_INVALID_ARG  # overlap
+    # CG with the float-float operator but no split G
+    opts = nekax.NekCgOpts(1, 0, 0.0, 0, 0, nekax.AX_FF, None)
+    assert L.nek_cg_solve_ex(None, 1, 3, A16, A16, A16, None, A16, A16, 1e-8, 10, None, None, None,
+                             ctypes.byref(opts), None) == nekax.ERR_INVALID_ARG

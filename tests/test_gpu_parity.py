@@ -260,3 +260,86 @@ def test_cg_special_cases_and_failures():
     # indefinite operator (negated G) -> p.Ap <= 0 -> breakdown on the first iteration
     r = nekax.cg_solve(P.gs, m.nelt, 6, P.D, -P.G, P.mask, P.minv.abs(), f, x, 1e-8, 50)
     assert r["status"] == nekax.ERR_BREAKDOWN and r["iters"] == 1
+
+
+# ------------------------------------------------------------------ FP64-accurate float-float AX
+@pytest.mark.parametrize("nx", list(range(2, 17)))
+@pytest.mark.parametrize("nelt", [1, 7, 37])
+def test_ax_ff_parity_sweep(nx, nelt):
+    """Same bound as the FP64 kernel: 1e-12 relative in the max norm."""
+    rng = np.random.default_rng(nx * 1000 + nelt)
+    xi, rho, D = ref.gll(nx)
+    mesh = inputs.box_mesh(nelt, 1, 1, nx, perturb=0.2, seed=nx + 1)
+    G = ref.geom(mesh.corners, nx, xi, rho)
+    u = rng.uniform(-1, 1, size=(nelt, nx ** 3))
+    Gd = _t(G)
+    Gff = torch.empty((nelt, nx ** 3, 12), dtype=torch.float32, device=DEV)
+    nekax.geom_ff(nelt, nx, Gd, Gff)
+    wd = torch.full((nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+    nekax.ax_ff(nelt, nx, _t(D), Gff, _t(u), wd)
+    torch.cuda.synchronize()
+    w = wd.cpu().numpy()
+    assert np.all(np.isfinite(w)), "unwritten output entries"
+    assert _rel(w, ref.ax(D, G, u)) <= TOL_AX
+
+
+def test_geom_ff_split_is_faithful():
+    nx = 7
+    mesh = inputs.box_mesh(3, 2, 2, nx, perturb=0.2, seed=4)
+    G = ref.geom(mesh.corners, nx)
+    Gff = torch.empty((mesh.nelt, nx ** 3, 12), dtype=torch.float32, device=DEV)
+    nekax.geom_ff(mesh.nelt, nx, _t(G), Gff)
+    g = Gff.cpu().numpy().astype(np.float64)
+    back = g[..., 0::2] + g[..., 1::2]
+    assert np.max(np.abs(back - G) / np.abs(G).max()) <= 2.0 ** -46
+    assert np.array_equal(g[..., 0::2], G.astype(np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("nx", [8, 10, 16])
+def test_ax_ff_wide_dynamic_range(nx):
+    """u spanning 1e-9..1 inside an element and 1e-6..1e3 across elements: still 1e-12 norm-wise per element."""
+    rng = np.random.default_rng(nx)
+    nelt = 9
+    xi, rho, D = ref.gll(nx)
+    mesh = inputs.box_mesh(3, 3, 1, nx, perturb=0.15, seed=nx)
+    G = ref.geom(mesh.corners, nx, xi, rho)
+    u = rng.uniform(-1, 1, size=(nelt, nx ** 3)) * 10.0 ** rng.uniform(-9, 0, size=(nelt, nx ** 3))
+    u *= 10.0 ** np.linspace(-6, 3, nelt)[:, None]
+    Gff = torch.empty((nelt, nx ** 3, 12), dtype=torch.float32, device=DEV)
+    nekax.geom_ff(nelt, nx, _t(G), Gff)
+    wd = torch.empty((nelt, nx ** 3), dtype=torch.float64, device=DEV)
+    nekax.ax_ff(nelt, nx, _t(D), Gff, _t(u), wd)
+    torch.cuda.synchronize()
+    w = wd.cpu().numpy()
+    wr = ref.ax(D, G, u)
+    for e in range(nelt):
+        assert _rel(w[e], wr[e]) <= TOL_AX, e
+
+
+def test_ax_ff_full_size_sampled():
+    nx = 10
+    mesh = inputs.box_mesh(32, 32, 32, nx, perturb=0.1, seed=2)
+    P = DeviceProblem(mesh, DEV, build_minv=False)
+    u = inputs.random_local_field(mesh.nelt, nx, seed=5)
+    w = torch.empty((mesh.nelt, nx ** 3), dtype=torch.float64, device=DEV)
+    P.ax_ff(_t(u), w)
+    torch.cuda.synchronize()
+    sample = np.concatenate([np.random.default_rng(1).choice(mesh.nelt, size=96, replace=False),
+                             [0, mesh.nelt - 1]])
+    xi, rho, D = ref.gll(nx)
+    G = ref.geom(mesh.corners[sample], nx, xi, rho)
+    assert _rel(w.cpu().numpy()[sample], ref.ax(D, G, u[sample])) <= TOL_AX
+
+
+@pytest.mark.parametrize("dims,nx", [((3, 3, 3), 6), ((2, 2, 2), 10), ((3, 2, 2), 7)])
+def test_cg_with_ff_operator(dims, nx):
+    mesh = inputs.box_mesh(*dims, nx, perturb=0.1, seed=3)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=4)
+    x = torch.empty((mesh.nelt, nx ** 3), dtype=torch.float64, device=DEV)
+    res = P.cg(_t(f), x, tol=1e-8, max_iter=2000, ax_impl=nekax.AX_FF)
+    assert res["status"] == nekax.OK, res
+    st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 1e-8, 2000)
+    assert abs(res["iters"] - itr) <= 2, (res["iters"], itr)
+    assert Pr.residual(f, x.cpu().numpy()) <= 1e-8 * (1 + 1e-3)
