@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--sweep", action="store_true", help="also time standalone AX at nx = 8, 10, 12, 16")
     ap.add_argument("--solve", action="store_true", help="also time one solve to 1e-8 relative residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed", action="store_true",
+                    help="also time FP64 defect correction with FP32/BF16/FP16 inner solves (to 1e-8 and 1e-10)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also solve this many uneven problems (nelt log-uniform in [8,4096]) batched")
+    ap.add_argument("--tune", action="store_true", help="pick elements-per-CTA with nek_tune_ax before timing")
     ap.add_argument("--ax", default="fp64", choices=["fp64", "ff"],
                     help="AX operator inside the solve: native FP64 or FP64-accurate float-float")
     return ap.parse_args()
@@ -190,7 +195,7 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ native arm
-def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10):
+def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10, tune=False):
     from paper_2011_04981_gb300 import inputs, nekax, perfmodel
     from paper_2011_04981_gb300.problem import DeviceProblem
 
@@ -205,6 +210,10 @@ def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10):
         s = torch.cuda.current_stream()
         res = {}
         for name, fn in (("fp64", P.ax), ("ff", P.ax_ff)):
+            epb = None
+            if tune:
+                impl = nekax.AX_FF if name == "ff" else nekax.AX_FP64
+                epb, _ = nekax.tune_ax(impl, mesh.nelt, nx, P.D, P.Gff if name == "ff" else P.G, u, w)
             for _ in range(3):
                 fn(u, w)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -218,11 +227,84 @@ def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10):
             g = mesh.npts / t / 1e9
             res[name] = {"gdofs": g, "ms": t * 1e3, "gflops": g * perfmodel.ax_flops_per_point(nx),
                          "hbm_frac": g * 64 / hbm,
-                         "fp64_frac": g * perfmodel.ax_flops_per_point(nx) / 1e3 / FP64_PEAK_TFLOPS}
+                         "fp64_frac": g * perfmodel.ax_flops_per_point(nx) / 1e3 / FP64_PEAK_TFLOPS,
+                         "epb": epb if epb is not None else nekax.get_ax_epb(
+                             nekax.AX_FF if name == "ff" else nekax.AX_FP64, nx)}
         out[str(nx)] = res
         del P, u, w
         torch.cuda.empty_cache()
     return out
+
+
+def mixed_block(torch, P, f, x, ws_bytes_hint=None):
+    """FP64 defect correction with reduced-precision inner PCG on the bench mesh."""
+    from paper_2011_04981_gb300 import nekax
+
+    out = {}
+    nx, nelt = P.nx, P.nelt
+    Gff = P.prepare_ff()
+    u = torch.rand((nelt, nx ** 3), dtype=torch.float64, device="cuda") * 2 - 1
+    w64 = torch.empty_like(u)
+    P.ax_ff(u, w64)
+    u32 = u.float()
+    w32 = torch.empty_like(u32)
+    hbm, _ = peaks()
+    for name, prec, dt in (("f32", nekax.PREC_F32, torch.float32), ("bf16", nekax.PREC_BF16, torch.float16),
+                           ("f16", nekax.PREC_F16, torch.float16)):
+        Glp = torch.empty((nelt, nx ** 3, 6), dtype=dt, device="cuda")
+        gsc = torch.empty(nelt, dtype=torch.float32, device="cuda")
+        nekax.geom_lowp(nelt, nx, prec, P.G, Glp, gsc)
+        nekax.ax_lowp(nelt, nx, prec, P.D, Glp, gsc, u32, w32)
+        torch.cuda.synchronize()
+        err = float((w32.double() - w64).abs().max() / w64.abs().max())
+        # standalone AX rate
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            nekax.ax_lowp(nelt, nx, prec, P.D, Glp, gsc, u32, w32)
+        e1.record()
+        e1.synchronize()
+        t_ax = e0.elapsed_time(e1) / 10 / 1e3
+        bpp = 8 + 6 * (4 if prec == nekax.PREC_F32 else 2)
+        rec = {"ax_rel_err_vs_fp64": err, "ax_gdofs": P.npts / t_ax / 1e9, "ax_bytes_per_point": bpp,
+               "ax_hbm_frac": P.npts * bpp / t_ax / 1e9 / hbm}
+        for tol in (1e-8, 1e-10):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = nekax.cg_solve_mixed(P.gs, nelt, nx, P.D, P.G, Gff, prec, Glp, gsc, P.mask, P.minv, f, x, tol=tol,
+                                     inner_tol=1e-2, max_outer=100, max_inner=20000)
+            torch.cuda.synchronize()
+            rec["to_%g" % tol] = {"seconds": time.perf_counter() - t0, "outer": r["outer"], "inner": r["inner"],
+                                  "relres": r["relres"], "status": nekax.status_string(r["status"])}
+        out[name] = rec
+        del Glp, gsc
+    return out
+
+
+def batch_block(torch, nprob, tol=1e-8):
+    """Configuration 4: nprob uneven deformed-box problems solved together."""
+    from paper_2011_04981_gb300 import inputs
+    from paper_2011_04981_gb300.problem import DeviceBatch
+
+    specs = inputs.batch_problem_specs(nprob, seed=1)
+    meshes = [inputs.box_mesh(sp["ex"], sp["ey"], sp["ez"], sp["nx"], perturb=0.1, seed=sp["seed"]) for sp in specs]
+    fields = [inputs.random_global_field(m, seed=sp["seed"] + 7) for m, sp in zip(meshes, specs)]
+    B = DeviceBatch(meshes, fields, "cuda", ff=True)
+    x = torch.empty((B.npts,), dtype=torch.float64, device="cuda")
+    ws = torch.empty(B.plan.workspace_bytes(False) // 8 + 64, dtype=torch.float64, device="cuda")
+    B.solve(x, tol=tol, max_iter=21, iters_per_graph=10, workspace=ws)  # warm-up (graph instantiation too)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = B.solve(x, tol=tol, max_iter=20000, iters_per_graph=10, workspace=ws)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    pts_iters = sum(m.npts * int(r["iters"][pos]) for pos, m in enumerate(B.meshes))
+    return {"problems": nprob, "points": B.npts, "elements": int(sum(m.nelt for m in meshes)),
+            "nx_counts": {str(n): sum(1 for m in meshes if m.nx == n) for n in sorted({m.nx for m in meshes})},
+            "seconds_to_%g" % tol: dt, "converged": r["converged"], "max_iters": int(r["iters"].max()),
+            "mean_iters": float(r["iters"].mean()), "iterations_run": r["iterations_run"],
+            "graph_launches": r["graph_launches"], "kernel_launches": r["kernel_launches"],
+            "gdofs_useful": pts_iters / dt / 1e9, "operator": "nek_ax_ff (FP64-accurate)"}
 
 
 def run_native(args):
@@ -257,6 +339,10 @@ def run_native(args):
     ax_impl = nekax.AX_FF if args.ax == "ff" else nekax.AX_FP64
     if ax_impl == nekax.AX_FF:
         P.prepare_ff()
+    if args.tune:
+        wt = torch.empty_like(f)
+        nekax.tune_ax(ax_impl, mesh.nelt, nx, P.D, P.Gff if ax_impl == nekax.AX_FF else P.G, f, wt)
+        del wt
     for _ in range(args.warmup):
         P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, ax_impl=ax_impl)
     torch.cuda.synchronize()
@@ -329,7 +415,7 @@ def run_native(args):
         "clocks": clk,
     }
     if args.sweep and rank == 0:
-        line["ax_sweep"] = ax_sweep(torch)
+        line["ax_sweep"] = ax_sweep(torch, tune=args.tune)
     if args.solve and rank == 0:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -337,6 +423,11 @@ def run_native(args):
         torch.cuda.synchronize()
         line["cg_to_1e-8"] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"],
                               "status": nekax.status_string(r["status"]), "precision": "fp64 jacobi-pcg"}
+    if args.mixed and rank == 0:
+        line["mixed"] = mixed_block(torch, P, f, x)
+    if args.batch and rank == 0:
+        del ws
+        line["batch"] = batch_block(torch, args.batch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(nx)
         cb.pop("seconds", None)

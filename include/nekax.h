@@ -24,7 +24,8 @@
  *   - D is nx*nx doubles, row-major, D[i*nx + l] = l_l'(xi_i) (Nekbone's dxm1
  *     read row-wise, i.e. the memory of dxtm1);
  *   - "device" pointers are CUDA device (or managed) memory owned by the caller;
- *     E-vector and G pointers must be 16-byte aligned, D 8-byte aligned;
+ *     G pointers must be 16-byte aligned, E-vectors and D 8-byte aligned
+ *     (unless an entry point states otherwise);
  *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream);
  *     calls are asynchronous unless stated otherwise.
  */
@@ -49,6 +50,15 @@ typedef enum {
     NEK_ERR_NOMEM = 7,          /* host or device allocation failed */
     NEK_ERR_TOO_LARGE = 8       /* problem exceeds an index-width limit */
 } nek_status;
+
+/* Which AX operator a call uses. */
+typedef enum {
+    NEK_AX_FP64 = 0, /* nek_ax: native FP64 */
+    NEK_AX_FF = 1    /* nek_ax_ff: FP64-accurate float-float on the FP32 pipes; needs Gff */
+} nek_ax_impl;
+
+/* Opaque gather-scatter plan (see nek_gs_create). */
+typedef struct nek_gs nek_gs;
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char* nek_status_string(int status);
@@ -112,6 +122,72 @@ nek_status nek_geom_ff(int64_t nelt, int nx, const double* G, float* Gff, void* 
 nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                      void* stream);
 
+/* ------------------------------------------------------------ tuning ---
+ * The AX kernels group elements into CTAs; the group size (1, 2 or 4 elements
+ * per CTA where threads and shared memory allow) changes only occupancy, never
+ * the arithmetic, so results are bit-identical.  nek_tune_ax times each size on
+ * the given data (synchronously; u, G/Gff, w as for nek_ax / nek_ax_ff with
+ * impl = NEK_AX_FP64 / NEK_AX_FF, 16-byte aligned) and keeps the fastest for
+ * all later launches of that (impl, nx) in this process; *epb_out and *ms_out
+ * (nullable) receive it and its time per launch.  nek_set_ax_epb sets the size
+ * directly (0 restores the built-in default); nek_get_ax_epb reads it back.
+ * These settings are process-wide.  No paper counterpart: the paper picks its
+ * FPGA kernel count by hand (Section IV).
+ */
+nek_status nek_tune_ax(int impl, int64_t nelt, int nx, const double* D, const void* Gx, const double* u, double* w,
+                       int* epb_out, float* ms_out, void* stream);
+nek_status nek_set_ax_epb(int impl, int nx, int epb);
+int nek_get_ax_epb(int impl, int nx);
+
+/* ---------------------------------------------- reduced-precision AX ---
+ * The paper's further work (Section V) names single and half precision for the
+ * AX kernel.  These entry points run the operator with its contraction inputs
+ * (u, D and the intermediate wr, ws, wt) rounded to FP32, BF16 or FP16 and FP32
+ * accumulation; u and w are FP32 E-vectors.
+ */
+typedef enum { NEK_PREC_F32 = 0, NEK_PREC_BF16 = 1, NEK_PREC_F16 = 2 } nek_precision;
+
+/* Bytes of one stored value of a precision (4, 2, 2), 0 for an unknown one. */
+size_t nek_lowp_bytes_per_value(int precision);
+
+/* G (FP64 [e][p][6]) -> Glp [e][p][6] in `precision` scaled per element by
+ * gscale[e], a power of two >= max |G_e| (so |Glp| <= 1).  Glp: device,
+ * nelt*nx^3*6 values, 4-byte aligned; gscale: device, nelt floats.  Async. */
+nek_status nek_geom_lowp(int64_t nelt, int nx, int precision, const double* G, void* Glp, float* gscale,
+                         void* stream);
+
+/* w = AX(u) in reduced precision: u scaled per element by a power of two and
+ * rounded, D rounded, FP32 sums, wr/ws/wt rounded before the transposed
+ * contractions, output rescaled to FP32.  D: device FP64 (rounded in the
+ * kernel); Glp, gscale from nek_geom_lowp; u, w: device FP32, no overlap.
+ * Async. */
+nek_status nek_ax_lowp(int64_t nelt, int nx, int precision, const double* D, const void* Glp, const float* gscale,
+                       const float* u, float* w, void* stream);
+
+/* Defect correction (iterative refinement) to FP64 accuracy: the residual
+ * r = mask(f - dssum(AX x)), its norm, inner products and the update x += d are
+ * FP64 on the GPU (AX through nek_ax_ff when Gff is given, else nek_ax); each
+ * correction solves A d = r/||r|| by Jacobi-PCG with FP32 vectors and
+ * nek_ax_lowp until its relative residual is <= inner_tol (or max_inner
+ * iterations).  Stops when ||r||_c/||b||_c <= tol_rel (NEK_OK) or after max_outer
+ * corrections (NEK_ERR_NOT_CONVERGED).  workspace: device, >=
+ * nek_cg_mixed_workspace_bytes(...) bytes, 256-aligned, or NULL.  Synchronous.
+ */
+typedef struct {
+    int outer_iters;     /* corrections applied */
+    int inner_iters;     /* inner PCG iterations, summed */
+    double relres;       /* final ||r||_c / ||b||_c (FP64 residual) */
+    int kernel_launches; /* kernels enqueued */
+} nek_mixed_info;
+
+size_t nek_cg_mixed_workspace_bytes(int64_t nelt, int nx, int need_minv);
+
+nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
+                              const float* Gff, int precision, const void* Glp, const float* gscale,
+                              const uint8_t* mask, const double* minv, const double* f, double* x, double tol_rel,
+                              double inner_tol, int max_outer, int max_inner, void* workspace,
+                              nek_mixed_info* info, void* stream);
+
 /* ------------------------------------------------------- gather-scatter ---
  * Direct stiffness summation over shared face, edge and corner nodes (the
  * nearest-neighbour exchange of Section II-B).  A plan groups every local node
@@ -125,8 +201,6 @@ nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, co
  * handle owned by the caller, released with nek_gs_destroy.  Needs
  * nelt*nx^3 < 2^31.
  */
-typedef struct nek_gs nek_gs;
-
 nek_status nek_gs_create(int64_t nelt, int nx, const int64_t* glo_num_host, nek_gs** out);
 nek_status nek_gs_destroy(nek_gs* gs);
 
@@ -183,6 +257,112 @@ nek_status nek_dot_c(const nek_gs* gs, const double* a, const double* b, double*
 nek_status nek_dot_c_noalloc(int64_t n, const double* c, const double* a, const double* b, double* result,
                              void* stream);
 
+/* ---------------------------------------------------- batched solves ---
+ * Many independent problems solved together by Jacobi-PCG (no paper
+ * counterpart: the paper runs one mesh).  Problems are laid out back to back in
+ * one E-vector space in the order given, which must be sorted by nx
+ * (non-decreasing); problem q holds nelt[q]*nx[q]^3 points and its G block is
+ * [nelt[q]][nx[q]^3][6] at the same offset (x6).  glo_num_host concatenates each
+ * problem's own global ids (each starting anywhere >= 0; they are made disjoint
+ * internally).  All points together must be < 2^31.  The handle owns the
+ * gather-scatter plan over all problems, the reduction chunk table and one D per
+ * distinct nx.  Synchronous.
+ */
+typedef struct nek_batch nek_batch;
+
+typedef struct {
+    int iterations_run;  /* iterations executed for the batch (max over problems) */
+    int converged;       /* problems that met tol */
+    int kernel_launches; /* kernels enqueued, counting those inside graph replays */
+    int graph_launches;  /* CUDA graph replays */
+} nek_batch_stats;
+
+nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const int64_t* glo_num_host,
+                            nek_batch** out);
+nek_status nek_batch_destroy(nek_batch* b);
+nek_status nek_batch_info(const nek_batch* b, int64_t* npts, int* ngroups, int* nchunks);
+/* The plan over all problems (owned by the batch), e.g. for nek_gs_inv_multiplicity. */
+const nek_gs* nek_batch_gs(const nek_batch* b);
+size_t nek_batch_workspace_bytes(const nek_batch* b, int need_minv);
+/* Jacobi inverse diagonal of every problem (device, async). */
+nek_status nek_batch_jacobi_minv(const nek_batch* b, const double* G, const uint8_t* mask, double* minv,
+                                 void* stream);
+/*
+ * Jacobi-PCG on every problem at once, each with its own scalars and stopping
+ * test (same iteration and rules as nek_cg_solve).  AX is nek_ax_ff when Gff
+ * (the batch's G split by nek_geom_ff) is given, else nek_ax.  After one eager
+ * iteration, iters_per_graph (> 0) iterations are captured into a CUDA graph
+ * and replayed until every problem has stopped or max_iter is reached (0 = no
+ * graph).  iters_host, relres_host, status_host: HOST arrays of nprob entries,
+ * nullable.  Returns NEK_OK if all problems converged (or tol_rel == 0),
+ * NEK_ERR_NOT_CONVERGED / NEK_ERR_BREAKDOWN if any did not.  Synchronous.
+ */
+nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* Gff, const uint8_t* mask,
+                              const double* minv, const double* f, double* x, double tol_rel, int max_iter,
+                              int iters_per_graph, void* workspace, int* iters_host, double* relres_host,
+                              int* status_host, nek_batch_stats* stats, void* stream);
+
+/* ------------------------------------------- learned preconditioner ---
+ * No counterpart in the paper (its solver uses Nekbone's fixed preconditioner).
+ * A per-element network for nx = 8 element blocks (8^3 points): input channels
+ * r/rms(r) and (Minv r)/rms(Minv r) of the element; three 3x3x3 convolutions
+ * with zero padding inside the element, 16 hidden channels, GELU after the first
+ * two; weights rounded to BF16, FP32 activations and accumulation.  Parameters
+ * theta: nek_net_param_count() FP32 values, W1 [16][2][27], b1 [16],
+ * W2 [16][16][27], b2 [16], W3 [1][16][27], b3 [1]; tap t = (dk+1)*9 + (dj+1)*3
+ * + (di+1) reads point (i+di, j+dj, k+dk).  All pointers device; async unless
+ * stated.
+ */
+int nek_net_param_count(void);
+
+/* xin[e][0][p] = r/rms_e(r), xin[e][1][p] = (minv r)/rms_e(minv r) (0 where the
+ * rms is 0); scale[e] = rms_e(minv r).  r, minv: FP64 E-vectors (nx = 8). */
+nek_status nek_net_prep(int64_t nelt, int nx, const double* r, const double* minv, float* xin, float* scale,
+                        void* stream);
+
+/* z[e][p] = net(xin[e])[p] * scale[e] * c[e][p] (FP64 out; c = 1/multiplicity). */
+nek_status nek_net_apply(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
+                         const double* c, double* z, void* stream);
+
+/* Training on a batch of `batch` samples (xin [batch][2][512], target
+ * [batch][512]): loss = mean_b |y_b - t_b|^2/|t_b|^2 (device float, nullable)
+ * and its gradient (grad: NPARAM floats, summed over the batch in a fixed
+ * order).  nek_net_forward_batch writes y [batch][512].  workspace: device,
+ * >= nek_net_train_workspace_bytes(batch) bytes, 256-aligned. */
+size_t nek_net_train_workspace_bytes(int batch);
+nek_status nek_net_forward_batch(int batch, const float* theta, const float* xin, float* y, void* workspace,
+                                 void* stream);
+nek_status nek_net_train_grad(int batch, const float* theta, const float* xin, const float* target, float* grad,
+                              float* loss, void* workspace, void* stream);
+
+/* One Adam step (Kingma & Ba) on n parameters; step >= 1 is the step count used
+ * for bias correction. */
+nek_status nek_adam_step(int n, float* theta, const float* grad, float* m, float* v, float lr, float beta1,
+                         float beta2, float eps, int step, void* stream);
+
+/*
+ * Flexible CG (Polak-Ribiere beta) preconditioned by the network,
+ * M(r) = mask(dssum(nek_net_apply(r))), falling back to Jacobi (and restarting
+ * the direction) when the relative residual has not fallen by stag_factor
+ * (0 < stag_factor < 1) in the last stag_window iterations.  theta NULL runs the
+ * same loop with Jacobi throughout.  AX is nek_ax_ff when Gff is given, else
+ * nek_ax.  nx must be 8.  Synchronous.
+ */
+typedef struct {
+    int iters;            /* iterations run */
+    double relres;        /* final ||r||_c/||b||_c */
+    int fell_back_at;     /* iteration at which Jacobi took over (0 = never) */
+    int net_applications; /* network preconditioner applications */
+    double net_ms;        /* GPU time of those applications */
+    int kernel_launches;
+} nek_fcg_info;
+
+size_t nek_fcg_workspace_bytes(int64_t nelt, int nx, int need_minv);
+nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G, const float* Gff,
+                         const uint8_t* mask, const double* minv, const float* theta, const double* f, double* x,
+                         double tol_rel, int max_iter, int stag_window, double stag_factor, void* workspace,
+                         nek_fcg_info* info, void* stream);
+
 /* ----------------------------------------------------------------- CG ---
  * Jacobi-preconditioned conjugate gradients on the masked, assembled operator
  * (Section II-B: vector operations, AX, nearest-neighbour exchange and global
@@ -204,11 +384,6 @@ nek_status nek_dot_c_noalloc(int64_t n, const double* c, const double* a, const 
  * NEK_ERR_BREAKDOWN if p.Ap <= 0 or a scalar becomes non-finite.
  */
 size_t nek_cg_workspace_bytes(int64_t nelt, int nx, int need_minv);
-
-typedef enum {
-    NEK_AX_FP64 = 0, /* nek_ax: native FP64 */
-    NEK_AX_FF = 1    /* nek_ax_ff: FP64-accurate float-float on the FP32 pipes; needs Gff */
-} nek_ax_impl;
 
 typedef struct {
     int check_every;     /* residual read-back period in iterations (>=1; default 1) */

@@ -195,6 +195,18 @@ nek_status nek_gs_create(int64_t nelt, int nx, const int64_t* glo, nek_gs** out)
     const int64_t n = nelt * (int64_t)nx * nx * nx;
     if (n >= (int64_t(1) << 31)) return NEK_ERR_TOO_LARGE;
     if (n > 0 && !glo) return NEK_ERR_INVALID_ARG;
+    return gs_create_flat(n, glo, out);
+}
+
+}  // extern "C"
+
+namespace nek {
+
+// Plan from a flat list of n global ids (the grouping does not depend on how the
+// points are split into elements).
+nek_status gs_create_flat(int64_t n, const int64_t* glo, nek_gs** out)
+{
+    *out = nullptr;
     int64_t gmax = -1;
     for (int64_t p = 0; p < n; p++) {
         if (glo[p] < 0) return NEK_ERR_INVALID_ARG;
@@ -270,6 +282,10 @@ fail:
     nek_gs_destroy(gs);
     return st;
 }
+
+}  // namespace nek
+
+extern "C" {
 
 nek_status nek_gs_destroy(nek_gs* gs)
 {

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(NX* NX* EPB) k_ax_fp64(int64_t nelt, const dou
     const int ne = static_cast<int>(nelt - e0 < EPB ? nelt - e0 : EPB);
 
     for (int q = tid; q < N2; q += NT) sD[q] = D[q];
-    if (((e0 * N3) & 1) == 0) {  // block start is 16-byte aligned (u itself is)
+    if ((reinterpret_cast<uintptr_t>(u + e0 * N3) & 15) == 0) {  // 16-byte aligned block start: vector loads
         const double2* src = reinterpret_cast<const double2*>(u + e0 * N3);
         double2* dst = reinterpret_cast<double2*>(sA);
         const int nv = (ne * N3) / 2;
@@ -121,10 +121,10 @@ __global__ void __launch_bounds__(NX* NX* EPB) k_ax_fp64(int64_t nelt, const dou
     }
 }
 
-template <int NX>
-nek_status launch_ax_nx(int64_t nelt, const double* D, const double* G, const double* u, double* w, cudaStream_t s)
+template <int NX, int EPB>
+nek_status launch_ax_variant(int64_t nelt, const double* D, const double* G, const double* u, double* w,
+                             cudaStream_t s)
 {
-    constexpr int EPB = ax_epb(NX);
     constexpr size_t smem = ax_smem_bytes<NX, EPB>();
     static bool configured = false;
     if (!configured) {
@@ -139,29 +139,64 @@ nek_status launch_ax_nx(int64_t nelt, const double* D, const double* G, const do
     return check_launch();
 }
 
+template <int NX, int EPB>
+constexpr bool ax_fits()
+{
+    return NX * NX * EPB <= 1024 && ax_smem_bytes<NX, EPB>() <= 227 * 1024;
+}
+
+template <int NX>
+nek_status launch_ax_nx(int epb, int64_t nelt, const double* D, const double* G, const double* u, double* w,
+                        cudaStream_t s)
+{
+    if (epb <= 0) epb = ax_epb(NX);
+    switch (epb) {
+        case 1:
+            if constexpr (ax_fits<NX, 1>()) return launch_ax_variant<NX, 1>(nelt, D, G, u, w, s);
+            break;
+        case 2:
+            if constexpr (ax_fits<NX, 2>()) return launch_ax_variant<NX, 2>(nelt, D, G, u, w, s);
+            break;
+        case 4:
+            if constexpr (ax_fits<NX, 4>()) return launch_ax_variant<NX, 4>(nelt, D, G, u, w, s);
+            break;
+        default:
+            break;
+    }
+    if constexpr (ax_epb(NX) != 1 && ax_epb(NX) != 2 && ax_epb(NX) != 4)
+        return launch_ax_variant<NX, ax_epb(NX)>(nelt, D, G, u, w, s);
+    return NEK_ERR_INVALID_ARG;
+}
+
 }  // namespace
+
+nek_status launch_ax_fp64_epb(int epb, int64_t nelt, int nx, const double* D, const double* G, const double* u,
+                              double* w, cudaStream_t s)
+{
+    switch (nx) {
+        case 2: return launch_ax_nx<2>(epb, nelt, D, G, u, w, s);
+        case 3: return launch_ax_nx<3>(epb, nelt, D, G, u, w, s);
+        case 4: return launch_ax_nx<4>(epb, nelt, D, G, u, w, s);
+        case 5: return launch_ax_nx<5>(epb, nelt, D, G, u, w, s);
+        case 6: return launch_ax_nx<6>(epb, nelt, D, G, u, w, s);
+        case 7: return launch_ax_nx<7>(epb, nelt, D, G, u, w, s);
+        case 8: return launch_ax_nx<8>(epb, nelt, D, G, u, w, s);
+        case 9: return launch_ax_nx<9>(epb, nelt, D, G, u, w, s);
+        case 10: return launch_ax_nx<10>(epb, nelt, D, G, u, w, s);
+        case 11: return launch_ax_nx<11>(epb, nelt, D, G, u, w, s);
+        case 12: return launch_ax_nx<12>(epb, nelt, D, G, u, w, s);
+        case 13: return launch_ax_nx<13>(epb, nelt, D, G, u, w, s);
+        case 14: return launch_ax_nx<14>(epb, nelt, D, G, u, w, s);
+        case 15: return launch_ax_nx<15>(epb, nelt, D, G, u, w, s);
+        case 16: return launch_ax_nx<16>(epb, nelt, D, G, u, w, s);
+        default: return NEK_ERR_UNSUPPORTED_NX;
+    }
+}
 
 nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w,
                           cudaStream_t s)
 {
-    switch (nx) {
-        case 2: return launch_ax_nx<2>(nelt, D, G, u, w, s);
-        case 3: return launch_ax_nx<3>(nelt, D, G, u, w, s);
-        case 4: return launch_ax_nx<4>(nelt, D, G, u, w, s);
-        case 5: return launch_ax_nx<5>(nelt, D, G, u, w, s);
-        case 6: return launch_ax_nx<6>(nelt, D, G, u, w, s);
-        case 7: return launch_ax_nx<7>(nelt, D, G, u, w, s);
-        case 8: return launch_ax_nx<8>(nelt, D, G, u, w, s);
-        case 9: return launch_ax_nx<9>(nelt, D, G, u, w, s);
-        case 10: return launch_ax_nx<10>(nelt, D, G, u, w, s);
-        case 11: return launch_ax_nx<11>(nelt, D, G, u, w, s);
-        case 12: return launch_ax_nx<12>(nelt, D, G, u, w, s);
-        case 13: return launch_ax_nx<13>(nelt, D, G, u, w, s);
-        case 14: return launch_ax_nx<14>(nelt, D, G, u, w, s);
-        case 15: return launch_ax_nx<15>(nelt, D, G, u, w, s);
-        case 16: return launch_ax_nx<16>(nelt, D, G, u, w, s);
-        default: return NEK_ERR_UNSUPPORTED_NX;
-    }
+    return launch_ax_fp64_epb(tuned_epb(NEK_AX_FP64, nx), nelt, nx, D, G, u, w, s);
 }
 
 }  // namespace nek
@@ -175,7 +210,7 @@ extern "C" nek_status nek_ax(int64_t nelt, int nx, const double* D, const double
     if (nelt < 0) return NEK_ERR_INVALID_ARG;
     if (nelt == 0) return NEK_OK;
     if (!D || !G || !u || !w) return NEK_ERR_INVALID_ARG;
-    if (!is_aligned(D, 8) || !is_aligned(G, 16) || !is_aligned(u, 16) || !is_aligned(w, 16))
+    if (!is_aligned(D, 8) || !is_aligned(G, 16) || !is_aligned(u, 8) || !is_aligned(w, 8))
         return NEK_ERR_INVALID_ARG;
     const size_t bytes = sizeof(double) * (size_t)nelt * nx * nx * nx;
     if (ranges_overlap(u, bytes, w, bytes)) return NEK_ERR_INVALID_ARG;

@@ -68,20 +68,21 @@ __device__ __forceinline__ float offset_for(float b)
 {
     return __fmul_rn(__int_as_float(__float_as_int(b) & 0x7F800000), 6.0f);
 }
-__device__ __forceinline__ float2 offset_for(float2 b) { return make_float2(offset_for(b.x), offset_for(b.y)); }
 
 template <class T>
 struct OffsetAcc {
-    T S, S2, c, s1, s2;
+    T S, S2, c0, c1, c2, s1;
     __device__ __forceinline__ void init(T sigma)
     {
         s1 = sigma;
-        s2 = vmul(sigma, splat<T>(3.814697265625e-06f));  // 2^-18
         S = s1;
-        S2 = s2;
-        c = vzero<T>();
+        S2 = vmul(sigma, splat<T>(3.814697265625e-06f));  // sigma * 2^-18
+        c0 = vzero<T>();
+        c1 = vzero<T>();
+        c2 = vzero<T>();
     }
-    // += (ah + al) * (bh + bl)
+    // += (ah + al) * (bh + bl).  S, S2, c0, c1 and c2 each carry a one-operation
+    // recurrence, so consecutive terms overlap in the pipeline.
     __device__ __forceinline__ void add(T ah, T al, T bh, T bl)
     {
         const T t = vfma(ah, bh, S);
@@ -90,19 +91,19 @@ struct OffsetAcc {
         const T t2 = vadd(S2, r);
         const T d2 = vsub(S2, t2);
         const T r2 = vadd(r, d2);
-        c = vadd(c, r2);
-        c = vfma(ah, bl, c);
-        c = vfma(al, bh, c);
+        c0 = vadd(c0, r2);
+        c1 = vfma(ah, bl, c1);
+        c2 = vfma(al, bh, c2);
         S = t;
         S2 = t2;
     }
     __device__ __forceinline__ void finish(T& hi, T& lo) const
     {
         const T H1 = vsub(S, s1);
-        const T H2 = vsub(S2, s2);
+        const T H2 = vsub(S2, vmul(s1, splat<T>(3.814697265625e-06f)));
         T e;
         two_sum(H1, H2, hi, e);
-        lo = vadd(e, c);
+        lo = vadd(e, vadd(c0, vadd(c1, c2)));
     }
 };
 
@@ -130,14 +131,48 @@ __device__ __forceinline__ void df_dot3(T ah, T al, T xh, T xl, T bh, T bl, T yh
     l = vadd(vadd(vadd(e1, e2), vadd(e3, f1)), f2);
 }
 
+// x = h + l with h = x truncated to 24 significant bits and l the next 23 bits
+// (relative error <= 2^-46), built from the bit pattern with integer operations
+// only: on GB300 the FP64<->FP32 conversion instructions share the FP64 pipe
+// (2 per SM per clock), which this avoids.  Valid for 2^-80 <= |x| < 2^127
+// (smaller magnitudes give l = 0, or h = l = 0 below 2^-126).
 __device__ __forceinline__ float2 split_double(double x)
 {
-    const float h = __double2float_rn(x);
-    const float l = __double2float_rn(x - (double)h);
-    return make_float2(h, l);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sgn = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    // sign | (e - 896) << 23 | top 23 mantissa bits
+    const unsigned hb = sgn | ((unsigned)(e - 896) << 23) | (((hi & 0xFFFFFu) << 3) | (lo >> 29));
+    // next 23 mantissa bits (bits 6..28 of lo) as an integer, times 2^(e - 1069)
+    const float r = __fsub_rn(__uint_as_float(0x4B000000u | ((lo >> 6) & 0x7FFFFFu)), 8388608.0f);
+    const float l = __fmul_rn(r, __uint_as_float((unsigned)(e - 942) << 23));
+    const float h = e >= 897 ? __uint_as_float(hb) : 0.0f;
+    return make_float2(h, e >= 943 ? __uint_as_float(__float_as_uint(l) | sgn) : 0.0f);
 }
 
+// (double)h + (double)l with the two widenings done by integer operations and a
+// single FP64 add.
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned a = u & 0x7FFFFFFFu;
+    if (a < 0x00800000u) return 0.0;  // zero or FP32-denormal: below the kernel's accuracy scale
+    const unsigned hi = (u & 0x80000000u) | ((((a >> 23) + 896u) << 20) | ((a & 0x7FFFFFu) >> 3));
+    const unsigned lo = (a & 0x7u) << 29;
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+__device__ __forceinline__ double join_pair(float h, float l) { return __dadd_rn(widen(h), widen(l)); }
+
 __device__ __forceinline__ float absmax_bits(float a, float b) { return fmaxf(fabsf(a), b); }
+
+// slot[key] = max(slot[key], v) for v >= 0, one shared-memory atomic per key per warp.
+__device__ __forceinline__ void segmented_max_to_smem(int key, float v, float* slot)
+{
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const unsigned m = __reduce_max_sync(same, __float_as_uint(v));
+    if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(reinterpret_cast<unsigned*>(slot + key), m);
+}
 
 // Lane access for the 1- and 2-wide forms.
 template <class T>
@@ -171,15 +206,23 @@ constexpr int ff_epb()
 template <int NX, int EPB>
 constexpr size_t ff_smem_bytes()
 {
-    // three float2 blocks [EPB][N3] (u, ws, wr), D and D^T as float2 pairs,
+    // four float2 blocks [EPB][N3] (u, wr, ws, wt), D and D^T as float2 pairs,
     // rowabs, colabs and the per-element maxima.
-    return sizeof(float2) * (3 * EPB * NX * NX * NX + 2 * NX * NX) + sizeof(float) * (2 * NX + 4 * EPB + 4) + 16;
+    return sizeof(float2) * (4 * EPB * NX * NX * NX + 2 * NX * NX) + sizeof(float) * (2 * NX + 4 * EPB + 4) + 16;
+}
+
+// CTAs per SM the register budget is set for: about 16 resident warps.
+template <int NX, int EPB>
+constexpr int ff_min_blocks()
+{
+    constexpr int warps = (NX * NX * EPB + 31) / 32;
+    return warps >= 16 ? 1 : (16 / warps > 4 ? 4 : 16 / warps);
 }
 
 template <int NX, int EPB>
-__global__ void __launch_bounds__(NX* NX* EPB, 1) k_ax_ff(int64_t nelt, const double* __restrict__ D,
-                                                           const float4* __restrict__ Gff,
-                                                           const double* __restrict__ u, double* __restrict__ w)
+__global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
+    k_ax_ff(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
+            const double* __restrict__ u, double* __restrict__ w)
 {
     using T = typename std::conditional<(NX % 2 == 0), float2, float>::type;
     using L = Lanes<T>;
@@ -187,9 +230,10 @@ __global__ void __launch_bounds__(NX* NX* EPB, 1) k_ax_ff(int64_t nelt, const do
     constexpr int N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sU = reinterpret_cast<float2*>(smem_raw);  // [EPB][N3] u (hi, lo)
-    float2* sWs = sU + EPB * N3;                       // [EPB][N3] ws
-    float2* sWr = sWs + EPB * N3;                      // [EPB][N3] wr
-    float2* sD = sWr + EPB * N3;                       // D[i][l]   at i*NX+l
+    float2* sWr = sU + EPB * N3;                       // [EPB][N3] wr
+    float2* sWs = sWr + EPB * N3;                      // [EPB][N3] ws
+    float2* sWt = sWs + EPB * N3;                      // [EPB][N3] wt
+    float2* sD = sWt + EPB * N3;                       // D[i][l]   at i*NX+l
     float2* sDT = sD + N2;                             // D[k][l]   at l*NX+k
     float* sRow = reinterpret_cast<float*>(sDT + N2);  // sum_l |D[q][l]|
     float* sCol = sRow + NX;                           // sum_l |D[l][q]|
@@ -226,31 +270,25 @@ __global__ void __launch_bounds__(NX* NX* EPB, 1) k_ax_ff(int64_t nelt, const do
     const int i = q2 % NX, j = q2 / NX;
     const bool active = el < ne;
     const float2* ue = sU + el * N3;
-
-    // Column of u along k and its maximum.
-    float2 ucol[NX];
-    if (active) {
+    {
         float m = 0.f;
-#pragma unroll
-        for (int l = 0; l < NX; l++) {
-            ucol[l] = ue[i + NX * (j + NX * l)];
-            m = absmax_bits(ucol[l].x, m);
-        }
-        atomicMax(reinterpret_cast<int*>(sMax + 4 * el), __float_as_int(m));
+        if (active)
+            for (int l = 0; l < NX; l++) m = absmax_bits(ue[i + NX * (j + NX * l)].x, m);
+        segmented_max_to_smem(4 * el, m, sMax);
     }
     __syncthreads();
 
     // ------------------------------------------------------------- phase 1
-    float2 wtcol[NX];
+    float mx_r = 0.f, mx_s = 0.f, mx_t = 0.f;
     if (active) {
         const float umax = sMax[4 * el] * 1.0001f;
         const T sig_r = splat<T>(offset_for(sRow[i] * umax));
         const T sig_s = splat<T>(offset_for(sRow[j] * umax));
         const float4* Ge = Gff + (e0 + el) * (int64_t)N3 * 3;
-        float2* wse = sWs + el * N3;
         float2* wre = sWr + el * N3;
-        float mr = 0.f, ms = 0.f, mt = 0.f;
-#pragma unroll
+        float2* wse = sWs + el * N3;
+        float2* wte = sWt + el * N3;
+#pragma unroll 1
         for (int k0 = 0; k0 < NX; k0 += W) {
             OffsetAcc<T> ar, as, at;
             T sig_t;
@@ -259,7 +297,7 @@ __global__ void __launch_bounds__(NX* NX* EPB, 1) k_ax_ff(int64_t nelt, const do
             ar.init(sig_r);
             as.init(sig_s);
             at.init(sig_t);
-#pragma unroll
+#pragma unroll 2
             for (int l = 0; l < NX; l++) {
                 T uh, ul, vh, vl, dh, dl;
 #pragma unroll
@@ -274,10 +312,10 @@ __global__ void __launch_bounds__(NX* NX* EPB, 1) k_ax_ff(int64_t nelt, const do
                     L::set(dh, q, d.x);
                     L::set(dl, q, d.y);
                 }
-                const float2 dr = sD[i * NX + l], ds = sD[j * NX + l];
+                const float2 dr = sD[i * NX + l], ds = sD[j * NX + l], uc = ue[i + NX * (j + NX * l)];
                 ar.add(splat<T>(dr.x), splat<T>(dr.y), uh, ul);
                 as.add(splat<T>(ds.x), splat<T>(ds.y), vh, vl);
-                at.add(dh, dl, splat<T>(ucol[l].x), splat<T>(ucol[l].y));
+                at.add(dh, dl, splat<T>(uc.x), splat<T>(uc.y));
             }
             T urh, url, ush, usl, uth, utl;
             ar.finish(urh, url);
@@ -302,34 +340,35 @@ __global__ void __launch_bounds__(NX* NX* EPB, 1) k_ax_ff(int64_t nelt, const do
                 const int p = i + NX * (j + NX * (k0 + q));
                 wre[p] = make_float2(L::get(wrh, q), L::get(wrl, q));
                 wse[p] = make_float2(L::get(wsh, q), L::get(wsl, q));
-                wtcol[k0 + q] = make_float2(L::get(wth, q), L::get(wtl, q));
-                mr = absmax_bits(L::get(wrh, q), mr);
-                ms = absmax_bits(L::get(wsh, q), ms);
-                mt = absmax_bits(L::get(wth, q), mt);
+                wte[p] = make_float2(L::get(wth, q), L::get(wtl, q));
+                mx_r = absmax_bits(L::get(wrh, q), mx_r);
+                mx_s = absmax_bits(L::get(wsh, q), mx_s);
+                mx_t = absmax_bits(L::get(wth, q), mx_t);
             }
         }
-        atomicMax(reinterpret_cast<int*>(sMax + 4 * el + 1), __float_as_int(mr));
-        atomicMax(reinterpret_cast<int*>(sMax + 4 * el + 2), __float_as_int(ms));
-        atomicMax(reinterpret_cast<int*>(sMax + 4 * el + 3), __float_as_int(mt));
     }
+    segmented_max_to_smem(4 * el + 1, mx_r, sMax);
+    segmented_max_to_smem(4 * el + 2, mx_s, sMax);
+    segmented_max_to_smem(4 * el + 3, mx_t, sMax);
     __syncthreads();
 
     // ------------------------------------------------------------- phase 2
     if (active) {
         const float2* wre = sWr + el * N3;
         const float2* wse = sWs + el * N3;
+        const float2* wte = sWt + el * N3;
         const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
                     mwt = sMax[4 * el + 3] * 1.0001f;
         const float bij = sCol[i] * mwr + sCol[j] * mws;
         double* we = w + (e0 + el) * (int64_t)N3;
-#pragma unroll
+#pragma unroll 1
         for (int k0 = 0; k0 < NX; k0 += W) {
             T sig;
 #pragma unroll
             for (int q = 0; q < W; q++) L::set(sig, q, offset_for(bij + sCol[k0 + q] * mwt));
             OffsetAcc<T> acc;
             acc.init(sig);
-#pragma unroll
+#pragma unroll 2
             for (int l = 0; l < NX; l++) {
                 T ah, al, bh, bl, dh, dl;
 #pragma unroll
@@ -344,27 +383,26 @@ __global__ void __launch_bounds__(NX* NX* EPB, 1) k_ax_ff(int64_t nelt, const do
                     L::set(dh, q, d.x);
                     L::set(dl, q, d.y);
                 }
-                const float2 ci = sD[l * NX + i], cj = sD[l * NX + j];
+                const float2 ci = sD[l * NX + i], cj = sD[l * NX + j], tc = wte[i + NX * (j + NX * l)];
                 acc.add(splat<T>(ci.x), splat<T>(ci.y), ah, al);
                 acc.add(splat<T>(cj.x), splat<T>(cj.y), bh, bl);
-                acc.add(dh, dl, splat<T>(wtcol[l].x), splat<T>(wtcol[l].y));
+                acc.add(dh, dl, splat<T>(tc.x), splat<T>(tc.y));
             }
             T hi, lo;
             acc.finish(hi, lo);
 #pragma unroll
             for (int q = 0; q < W; q++) {
                 const int p = i + NX * (j + NX * (k0 + q));
-                we[p] = (double)L::get(hi, q) + (double)L::get(lo, q);
+                we[p] = join_pair(L::get(hi, q), L::get(lo, q));
             }
         }
     }
 }
 
-template <int NX>
-nek_status launch_ax_ff_nx(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                           cudaStream_t s)
+template <int NX, int EPB>
+nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
+                                cudaStream_t s)
 {
-    constexpr int EPB = ff_epb<NX>();
     constexpr size_t smem = ff_smem_bytes<NX, EPB>();
     static bool configured = false;
     if (!configured) {
@@ -380,6 +418,35 @@ nek_status launch_ax_ff_nx(int64_t nelt, const double* D, const float* Gff, cons
     return check_launch();
 }
 
+template <int NX, int EPB>
+constexpr bool ff_fits()
+{
+    return NX * NX * EPB <= 1024 && ff_smem_bytes<NX, EPB>() <= 227 * 1024;
+}
+
+template <int NX>
+nek_status launch_ax_ff_nx(int epb, int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
+                           cudaStream_t s)
+{
+    if (epb <= 0) epb = ff_epb<NX>();
+    switch (epb) {
+        case 1:
+            if constexpr (ff_fits<NX, 1>()) return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s);
+            break;
+        case 2:
+            if constexpr (ff_fits<NX, 2>()) return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s);
+            break;
+        case 4:
+            if constexpr (ff_fits<NX, 4>()) return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s);
+            break;
+        default:
+            break;
+    }
+    if constexpr (ff_epb<NX>() != 1 && ff_epb<NX>() != 2 && ff_epb<NX>() != 4)
+        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s);
+    return NEK_ERR_INVALID_ARG;
+}
+
 // G (FP64, [e][p][6]) -> float-float [e][p][12] = (h0,l0,h1,l1,...,h5,l5).
 __global__ void k_g_to_ff(int64_t npts, const double* __restrict__ G, float2* __restrict__ Gff)
 {
@@ -390,27 +457,33 @@ __global__ void k_g_to_ff(int64_t npts, const double* __restrict__ G, float2* __
 
 }  // namespace
 
+nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
+                            double* w, cudaStream_t s)
+{
+    switch (nx) {
+        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s);
+        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s);
+        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s);
+        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s);
+        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s);
+        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s);
+        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s);
+        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s);
+        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s);
+        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s);
+        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s);
+        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s);
+        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s);
+        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s);
+        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s);
+        default: return NEK_ERR_UNSUPPORTED_NX;
+    }
+}
+
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                         cudaStream_t s)
 {
-    switch (nx) {
-        case 2: return launch_ax_ff_nx<2>(nelt, D, Gff, u, w, s);
-        case 3: return launch_ax_ff_nx<3>(nelt, D, Gff, u, w, s);
-        case 4: return launch_ax_ff_nx<4>(nelt, D, Gff, u, w, s);
-        case 5: return launch_ax_ff_nx<5>(nelt, D, Gff, u, w, s);
-        case 6: return launch_ax_ff_nx<6>(nelt, D, Gff, u, w, s);
-        case 7: return launch_ax_ff_nx<7>(nelt, D, Gff, u, w, s);
-        case 8: return launch_ax_ff_nx<8>(nelt, D, Gff, u, w, s);
-        case 9: return launch_ax_ff_nx<9>(nelt, D, Gff, u, w, s);
-        case 10: return launch_ax_ff_nx<10>(nelt, D, Gff, u, w, s);
-        case 11: return launch_ax_ff_nx<11>(nelt, D, Gff, u, w, s);
-        case 12: return launch_ax_ff_nx<12>(nelt, D, Gff, u, w, s);
-        case 13: return launch_ax_ff_nx<13>(nelt, D, Gff, u, w, s);
-        case 14: return launch_ax_ff_nx<14>(nelt, D, Gff, u, w, s);
-        case 15: return launch_ax_ff_nx<15>(nelt, D, Gff, u, w, s);
-        case 16: return launch_ax_ff_nx<16>(nelt, D, Gff, u, w, s);
-        default: return NEK_ERR_UNSUPPORTED_NX;
-    }
+    return launch_ax_ff_epb(tuned_epb(NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s);
 }
 
 }  // namespace nek

@@ -1,0 +1,596 @@
+// Many independent Poisson problems solved together by Jacobi-PCG.
+//
+// The problems (any element counts, nx in [2,16]) are laid out back to back in
+// one E-vector space, sorted by nx, so that
+//   - AX is one launch per nx group (elements are independent, the operator does
+//     not care which problem an element belongs to);
+//   - gather-scatter is one plan over all problems (each problem's global ids
+//     are offset past the previous problem's);
+//   - vector updates and inner products run over fixed-size chunks that never
+//     straddle two problems: every chunk writes one partial per inner product,
+//     and one warp per problem sums its chunks' partials in order, so every
+//     problem gets its own deterministic scalars (alpha, beta, residual).
+// A problem whose residual test passes (or that breaks down) is frozen by a
+// per-problem flag: later update kernels skip its chunks, so its solution and
+// iteration count are exactly those of a solve on its own.  One iteration for
+// all problems is about ten kernels; `iters_per_graph` iterations are captured
+// once into a CUDA graph and replayed, with a device counter of unfinished
+// problems read back after each replay.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "nek_internal.h"
+#include "nek_pcg.cuh"
+
+namespace nek {
+
+namespace {
+
+constexpr int kChunk = 4096;  // points per reduction chunk
+constexpr int BT = 256;       // threads per chunk block
+
+struct BScal {
+    double rz, pw, alpha, beta, rr, bnorm, relres;
+    int done, status, iters, it;
+};
+
+struct Group {
+    int nx;
+    int64_t elem0, nelt;  // element range of the group
+    int64_t pt0;          // first point of the group
+    double* D;            // device nx*nx (owned)
+};
+
+__device__ __forceinline__ bool bhalted(const BScal& s) { return s.done || s.status != NEK_OK; }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NA>
+__device__ __forceinline__ void chunk_reduce(double (&acc)[NA], double* parts, int nchunks)
+{
+    __shared__ double sh[NA][BT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < NA; a++) {
+        const double v = warp_sum(acc[a]);
+        if (lane == 0) sh[a][wid] = v;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int a = 0; a < NA; a++) {
+            double t = lane < BT / 32 ? sh[a][lane] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) parts[a * nchunks + blockIdx.x] = t;
+        }
+    }
+}
+
+// x = 0; r = mask.f; z = minv r; p = z; partials <r,z>, <r,r>
+__global__ void __launch_bounds__(BT) kb_init(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
+                                              int nchunks, const double* __restrict__ c,
+                                              const uint8_t* __restrict__ mask, const double* __restrict__ minv,
+                                              const double* __restrict__ f, double* __restrict__ x,
+                                              double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
+                                              double* __restrict__ parts)
+{
+    const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
+    double acc[2] = {0.0, 0.0};
+    for (int64_t q = a + threadIdx.x; q < b; q += BT) {
+        const double rq = mask[q] ? f[q] : 0.0;
+        const double zq = minv[q] * rq;
+        x[q] = 0.0;
+        r[q] = rq;
+        z[q] = zq;
+        p[q] = zq;
+        acc[0] += c[q] * rq * zq;
+        acc[1] += c[q] * rq * rq;
+    }
+    chunk_reduce<2>(acc, parts, nchunks);
+}
+
+// one warp per problem: sums its chunk partials in order
+__device__ __forceinline__ double prob_sum(const double* parts, int c0, int c1)
+{
+    const int lane = threadIdx.x & 31;
+    double v = 0.0;
+    for (int q = c0 + lane; q < c1; q += 32) v += parts[q];
+    return warp_sum(v);
+}
+
+__global__ void kb_init_finish(int nprob, const int* __restrict__ pch, const double* __restrict__ parts, int nchunks,
+                               double tol, BScal* __restrict__ sc, int* __restrict__ active)
+{
+    const int pid = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (pid >= nprob) return;
+    const double rz = prob_sum(parts, pch[pid], pch[pid + 1]);
+    const double rr = prob_sum(parts + nchunks, pch[pid], pch[pid + 1]);
+    if ((threadIdx.x & 31) == 0) {
+        BScal s{};
+        s.rz = rz;
+        s.rr = rr;
+        s.bnorm = sqrt(rr);
+        s.relres = 1.0;
+        s.status = NEK_OK;
+        if (!(rr >= 0.0) || !isfinite(rr) || !isfinite(rz)) {
+            s.status = NEK_ERR_BREAKDOWN;
+        } else if (rr == 0.0) {
+            s.done = 1;
+            s.relres = 0.0;
+        }
+        sc[pid] = s;
+        if (!bhalted(s)) atomicAdd(active, 1);
+    }
+}
+
+// w <- mask.w ; partial <p,w>
+__global__ void __launch_bounds__(BT) kb_pw(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
+                                            int nchunks, const double* __restrict__ c,
+                                            const uint8_t* __restrict__ mask, const double* __restrict__ p,
+                                            double* __restrict__ w, double* __restrict__ parts,
+                                            const BScal* __restrict__ sc)
+{
+    if (bhalted(sc[ch_prob[blockIdx.x]])) return;
+    const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
+    double acc[1] = {0.0};
+    for (int64_t q = a + threadIdx.x; q < b; q += BT) {
+        double wq = w[q];
+        if (!mask[q]) {
+            wq = 0.0;
+            w[q] = 0.0;
+        }
+        acc[0] += c[q] * p[q] * wq;
+    }
+    chunk_reduce<1>(acc, parts, nchunks);
+}
+
+__global__ void kb_alpha(int nprob, const int* __restrict__ pch, const double* __restrict__ parts,
+                         BScal* __restrict__ sc, int* __restrict__ active)
+{
+    const int pid = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (pid >= nprob || bhalted(sc[pid])) return;
+    const double pw = prob_sum(parts, pch[pid], pch[pid + 1]);
+    if ((threadIdx.x & 31) == 0) {
+        BScal& s = sc[pid];
+        s.it += 1;
+        s.pw = pw;
+        if (!(pw > 0.0) || !isfinite(pw)) {
+            s.status = NEK_ERR_BREAKDOWN;
+            s.iters = s.it;
+            atomicSub(active, 1);
+        } else {
+            s.alpha = s.rz / pw;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha w; z = minv r; partials <r,r>, <r,z>
+__global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_begin,
+                                                const int32_t* __restrict__ ch_prob, int nchunks,
+                                                const double* __restrict__ c, const double* __restrict__ minv,
+                                                const double* __restrict__ p, const double* __restrict__ w,
+                                                double* __restrict__ x, double* __restrict__ r,
+                                                double* __restrict__ z, double* __restrict__ parts,
+                                                const BScal* __restrict__ sc)
+{
+    const BScal& s = sc[ch_prob[blockIdx.x]];
+    if (bhalted(s)) return;
+    const double alpha = s.alpha;
+    const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
+    double acc[2] = {0.0, 0.0};
+    for (int64_t q = a + threadIdx.x; q < b; q += BT) {
+        x[q] = fma(alpha, p[q], x[q]);
+        const double rq = fma(-alpha, w[q], r[q]);
+        const double zq = minv[q] * rq;
+        r[q] = rq;
+        z[q] = zq;
+        acc[0] += c[q] * rq * rq;
+        acc[1] += c[q] * rq * zq;
+    }
+    chunk_reduce<2>(acc, parts, nchunks);
+}
+
+__global__ void kb_beta(int nprob, const int* __restrict__ pch, const double* __restrict__ parts, int nchunks,
+                        BScal* __restrict__ sc, int* __restrict__ active)
+{
+    const int pid = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (pid >= nprob || bhalted(sc[pid])) return;
+    const double rr = prob_sum(parts, pch[pid], pch[pid + 1]);
+    const double rz = prob_sum(parts + nchunks, pch[pid], pch[pid + 1]);
+    if ((threadIdx.x & 31) == 0) {
+        BScal& s = sc[pid];
+        s.rr = rr;
+        s.relres = sqrt(rr) / s.bnorm;
+        if (!isfinite(s.relres) || !isfinite(rz)) {
+            s.status = NEK_ERR_BREAKDOWN;
+            s.iters = s.it;
+            atomicSub(active, 1);
+        } else {
+            s.beta = rz / s.rz;
+            s.rz = rz;
+        }
+    }
+}
+
+// per-problem convergence test, kept separate from kb_beta so the tolerance is
+// a kernel argument of the captured graph
+__global__ void kb_test(int nprob, double tol, BScal* __restrict__ sc, int* __restrict__ active)
+{
+    const int pid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pid >= nprob) return;
+    BScal& s = sc[pid];
+    if (bhalted(s)) return;
+    if (tol > 0.0 && s.relres <= tol && s.it > 0) {
+        s.done = 1;
+        s.iters = s.it;
+        atomicSub(active, 1);
+    }
+}
+
+__global__ void __launch_bounds__(BT) kb_p(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
+                                           const double* __restrict__ z, double* __restrict__ p,
+                                           const BScal* __restrict__ sc)
+{
+    const BScal& s = sc[ch_prob[blockIdx.x]];
+    if (bhalted(s)) return;
+    const double beta = s.beta;
+    const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
+    for (int64_t q = a + threadIdx.x; q < b; q += BT) p[q] = fma(beta, p[q], z[q]);
+}
+
+__global__ void k_bdiag_local(int64_t nelt, int nx, const double* __restrict__ D, const double* __restrict__ G,
+                              double* __restrict__ d)
+{
+    const int64_t n3 = (int64_t)nx * nx * nx;
+    for (int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gid < nelt * n3;
+         gid += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = gid / n3;
+        const int p = static_cast<int>(gid - e * n3);
+        const int i = p % nx, j = (p / nx) % nx, k = p / (nx * nx);
+        const double* Ge = G + e * n3 * 6;
+        double s = 0.0;
+        for (int l = 0; l < nx; l++) {
+            const double a = D[l * nx + i], b = D[l * nx + j], cc = D[l * nx + k];
+            s += Ge[6 * (l + nx * (j + nx * k)) + 0] * a * a;
+            s += Ge[6 * (i + nx * (l + nx * k)) + 3] * b * b;
+            s += Ge[6 * (i + nx * (j + nx * l)) + 5] * cc * cc;
+        }
+        const double* g = Ge + 6 * p;
+        const double di = D[i * nx + i], dj = D[j * nx + j], dk = D[k * nx + k];
+        s += 2.0 * (g[1] * di * dj + g[2] * di * dk + g[4] * dj * dk);
+        d[gid] = s;
+    }
+}
+
+__global__ void k_binvert(int64_t n, const uint8_t* __restrict__ mask, double* __restrict__ d)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        d[p] = mask[p] ? 1.0 / d[p] : 0.0;
+}
+
+}  // namespace
+
+}  // namespace nek
+
+struct nek_batch {
+    int nprob;
+    int64_t npts, nelt_total;
+    nek_gs* gs;
+    std::vector<nek::Group> groups;
+    std::vector<int64_t> prob_pt0;  // first point of each problem, nprob+1
+    int nchunks;
+    int64_t* d_ch_begin;  // nchunks+1
+    int32_t* d_ch_prob;   // nchunks
+    int* d_pch;           // nprob+1: chunk range of each problem
+};
+
+using namespace nek;
+
+namespace {
+
+inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct BLayout {
+    double *r, *z, *p, *w, *minv, *parts;
+    BScal* sc;
+    int* active;
+    size_t bytes;
+};
+
+BLayout b_layout(char* base, const nek_batch* b, bool need_minv)
+{
+    BLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t n) {
+        char* q = base ? base + off : nullptr;
+        off += al256(n);
+        return q;
+    };
+    const size_t v = sizeof(double) * std::max<int64_t>(b->npts, 1);
+    L.r = reinterpret_cast<double*>(take(v));
+    L.z = reinterpret_cast<double*>(take(v));
+    L.p = reinterpret_cast<double*>(take(v));
+    L.w = reinterpret_cast<double*>(take(v));
+    L.minv = need_minv ? reinterpret_cast<double*>(take(v)) : nullptr;
+    L.parts = reinterpret_cast<double*>(take(sizeof(double) * 2 * (size_t)b->nchunks));
+    L.sc = reinterpret_cast<BScal*>(take(sizeof(BScal) * (size_t)b->nprob));
+    L.active = reinterpret_cast<int*>(take(sizeof(int) * 4));
+    L.bytes = off;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const int64_t* glo_num_host,
+                            nek_batch** out)
+{
+    if (!out) return NEK_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nprob <= 0 || !nelt || !nx || !glo_num_host) return NEK_ERR_INVALID_ARG;
+    int64_t npts = 0, nel = 0;
+    for (int q = 0; q < nprob; q++) {
+        if (nx[q] < kMinNx || nx[q] > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+        if (nelt[q] <= 0) return NEK_ERR_INVALID_ARG;
+        if (q > 0 && nx[q] < nx[q - 1]) return NEK_ERR_INVALID_ARG;  // problems must be sorted by nx
+        npts += nelt[q] * (int64_t)nx[q] * nx[q] * nx[q];
+        nel += nelt[q];
+    }
+    if (npts >= (int64_t(1) << 31)) return NEK_ERR_TOO_LARGE;
+    nek_batch* b = new (std::nothrow) nek_batch();
+    if (!b) return NEK_ERR_NOMEM;
+    b->nprob = nprob;
+    b->npts = npts;
+    b->nelt_total = nel;
+    b->gs = nullptr;
+    b->d_ch_begin = nullptr;
+    b->d_ch_prob = nullptr;
+    b->d_pch = nullptr;
+    nek_status st = NEK_OK;
+    try {
+        // global ids of all problems in one space: problem q's ids are offset by
+        // the sum of the previous problems' (max id + 1)
+        std::vector<int64_t> glo(static_cast<size_t>(npts));
+        std::vector<int64_t> ch_begin;
+        std::vector<int32_t> ch_prob;
+        std::vector<int> pch(1, 0);
+        b->prob_pt0.assign(1, 0);
+        int64_t pt = 0, goff = 0, el = 0;
+        for (int q = 0; q < nprob; q++) {
+            const int64_t n = nelt[q] * (int64_t)nx[q] * nx[q] * nx[q];
+            int64_t gmax = -1;
+            for (int64_t k = 0; k < n; k++) {
+                const int64_t g = glo_num_host[pt + k];
+                if (g < 0) throw 1;
+                glo[pt + k] = g + goff;
+                gmax = std::max(gmax, g);
+            }
+            for (int64_t a = pt; a < pt + n; a += kChunk) {
+                ch_begin.push_back(a);
+                ch_prob.push_back(q);
+            }
+            pch.push_back(static_cast<int>(ch_begin.size()));
+            if (b->groups.empty() || b->groups.back().nx != nx[q]) b->groups.push_back(Group{nx[q], el, 0, pt, nullptr});
+            b->groups.back().nelt += nelt[q];
+            goff += gmax + 1;
+            pt += n;
+            el += nelt[q];
+            b->prob_pt0.push_back(pt);
+        }
+        ch_begin.push_back(npts);
+        b->nchunks = static_cast<int>(ch_prob.size());
+        if ((st = gs_create_flat(npts, glo.data(), &b->gs)) != NEK_OK) throw 3;
+        if ((st = check_cuda(cudaMalloc(&b->d_ch_begin, sizeof(int64_t) * ch_begin.size()))) != NEK_OK) throw 3;
+        if ((st = check_cuda(cudaMalloc(&b->d_ch_prob, sizeof(int32_t) * ch_prob.size()))) != NEK_OK) throw 3;
+        if ((st = check_cuda(cudaMalloc(&b->d_pch, sizeof(int) * pch.size()))) != NEK_OK) throw 3;
+        cudaMemcpy(b->d_ch_begin, ch_begin.data(), sizeof(int64_t) * ch_begin.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(b->d_ch_prob, ch_prob.data(), sizeof(int32_t) * ch_prob.size(), cudaMemcpyHostToDevice);
+        if ((st = check_cuda(cudaMemcpy(b->d_pch, pch.data(), sizeof(int) * pch.size(), cudaMemcpyHostToDevice))) !=
+            NEK_OK)
+            throw 3;
+        for (auto& g : b->groups) {
+            double Dh[kMaxNx * kMaxNx];
+            gll_host(g.nx, nullptr, nullptr, Dh);
+            if ((st = check_cuda(cudaMalloc(&g.D, sizeof(double) * g.nx * g.nx))) != NEK_OK) throw 3;
+            if ((st = check_cuda(cudaMemcpy(g.D, Dh, sizeof(double) * g.nx * g.nx, cudaMemcpyHostToDevice))) != NEK_OK)
+                throw 3;
+        }
+    } catch (const std::bad_alloc&) {
+        st = NEK_ERR_NOMEM;
+    } catch (int code) {
+        if (code == 1) st = NEK_ERR_INVALID_ARG;
+        if (st == NEK_OK) st = NEK_ERR_CUDA;
+    }
+    if (st != NEK_OK) {
+        nek_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return NEK_OK;
+}
+
+nek_status nek_batch_destroy(nek_batch* b)
+{
+    if (!b) return NEK_OK;
+    nek_gs_destroy(b->gs);
+    cudaFree(b->d_ch_begin);
+    cudaFree(b->d_ch_prob);
+    cudaFree(b->d_pch);
+    for (auto& g : b->groups) cudaFree(g.D);
+    delete b;
+    return NEK_OK;
+}
+
+nek_status nek_batch_info(const nek_batch* b, int64_t* npts, int* ngroups, int* nchunks)
+{
+    if (!b) return NEK_ERR_INVALID_ARG;
+    if (npts) *npts = b->npts;
+    if (ngroups) *ngroups = static_cast<int>(b->groups.size());
+    if (nchunks) *nchunks = b->nchunks;
+    return NEK_OK;
+}
+
+const nek_gs* nek_batch_gs(const nek_batch* b) { return b ? b->gs : nullptr; }
+
+size_t nek_batch_workspace_bytes(const nek_batch* b, int need_minv)
+{
+    if (!b) return 0;
+    return b_layout(nullptr, b, need_minv != 0).bytes;
+}
+
+nek_status nek_batch_jacobi_minv(const nek_batch* b, const double* G, const uint8_t* mask, double* minv,
+                                 void* stream)
+{
+    if (!b || !G || !mask || !minv || !is_aligned(G, 16) || !is_aligned(minv, 8)) return NEK_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (const auto& g : b->groups) {
+        const int64_t n = g.nelt * (int64_t)g.nx * g.nx * g.nx;
+        const int64_t nb = (n + 255) / 256;
+        k_bdiag_local<<<static_cast<int>(std::min<int64_t>(nb, 152 * 16)), 256, 0, s>>>(
+            g.nelt, g.nx, g.D, G + g.pt0 * 6, minv + g.pt0);
+    }
+    nek_status st = check_launch();
+    if (st != NEK_OK) return st;
+    if ((st = pcg::dssum<double>(b->gs, minv, s)) != NEK_OK) return st;
+    k_binvert<<<pcg::stream_blocks(b->npts), 256, 0, s>>>(b->npts, mask, minv);
+    return check_launch();
+}
+
+nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* Gff, const uint8_t* mask,
+                              const double* minv, const double* f, double* x, double tol_rel, int max_iter,
+                              int iters_per_graph, void* workspace, int* iters_host, double* relres_host,
+                              int* status_host, nek_batch_stats* stats, void* stream)
+{
+    if (stats) *stats = nek_batch_stats{};
+    if (!b || !G || !mask || !f || !x || max_iter < 0 || !(tol_rel >= 0.0)) return NEK_ERR_INVALID_ARG;
+    if (!is_aligned(G, 16) || !is_aligned(x, 16) || !is_aligned(f, 8) || (Gff && !is_aligned(Gff, 16)) ||
+        (minv && !is_aligned(minv, 8)) || (workspace && !is_aligned(workspace, 256)))
+        return NEK_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = nek_batch_workspace_bytes(b, minv == nullptr);
+    void* ws = workspace;
+    if (!ws && check_cuda(cudaMallocAsync(&ws, bytes, s)) != NEK_OK) return NEK_ERR_NOMEM;
+    BLayout L = b_layout(static_cast<char*>(ws), b, minv == nullptr);
+    nek_status st = NEK_OK;
+    const double* mv = minv;
+    const int nc = b->nchunks, np = b->nprob;
+    const int wblocks = (np + 7) / 8;  // 8 warps (problems) per 256-thread block
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int it_done = 0, launches = 0, graph_launches = 0;
+    int active = 0;
+    const int per_graph = iters_per_graph > 0 ? iters_per_graph : 0;
+
+    auto one_iteration = [&](cudaStream_t ss) -> nek_status {
+        for (const auto& g : b->groups) {
+            const double* pg = L.p + g.pt0;
+            double* wg = L.w + g.pt0;
+            nek_status sa = Gff ? launch_ax_ff(g.nelt, g.nx, g.D, Gff + g.pt0 * 12, pg, wg, ss)
+                                : launch_ax_fp64(g.nelt, g.nx, g.D, G + g.pt0 * 6, pg, wg, ss);
+            if (sa != NEK_OK) return sa;
+        }
+        nek_status sd = pcg::dssum<double>(b->gs, L.w, ss);
+        if (sd != NEK_OK) return sd;
+        kb_pw<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, b->gs->d_c, mask, L.p, L.w, L.parts, L.sc);
+        kb_alpha<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, L.sc, L.active);
+        kb_update<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, b->gs->d_c, mv, L.p, L.w, x, L.r, L.z, L.parts,
+                                     L.sc);
+        kb_beta<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, nc, L.sc, L.active);
+        kb_test<<<(np + 255) / 256, 256, 0, ss>>>(np, tol_rel, L.sc, L.active);
+        kb_p<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, L.z, L.p, L.sc);
+        return check_launch();
+    };
+    const int per_iter_launches = static_cast<int>(b->groups.size()) + 7;
+
+    if (!minv) {
+        if ((st = nek_batch_jacobi_minv(b, G, mask, L.minv, stream)) != NEK_OK) goto done;
+        mv = L.minv;
+        launches += static_cast<int>(b->groups.size()) + 2;
+    }
+    cudaMemsetAsync(L.active, 0, sizeof(int), s);
+    kb_init<<<nc, BT, 0, s>>>(b->d_ch_begin, b->d_ch_prob, nc, b->gs->d_c, mask, mv, f, x, L.r, L.z, L.p, L.parts);
+    kb_init_finish<<<wblocks, 256, 0, s>>>(np, b->d_pch, L.parts, nc, tol_rel, L.sc, L.active);
+    launches += 2;
+    if ((st = check_launch()) != NEK_OK) goto done;
+    // first iteration eagerly (configures every kernel before any capture)
+    if (max_iter > 0) {
+        if ((st = one_iteration(s)) != NEK_OK) goto done;
+        it_done = 1;
+        launches += per_iter_launches;
+    }
+    if (per_graph > 0 && it_done < max_iter) {
+        // Capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); nothing runs during capture.  The
+        // graph is then launched on the caller's stream.
+        cudaStream_t cs = nullptr;
+        if ((st = check_cuda(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) != NEK_OK) goto done;
+        nek_status sc_st = check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        if (sc_st == NEK_OK) {
+            for (int k = 0; k < per_graph && sc_st == NEK_OK; k++) sc_st = one_iteration(cs);
+            cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+            if (sc_st == NEK_OK) sc_st = check_cuda(ce);
+        }
+        cudaStreamDestroy(cs);
+        if ((st = sc_st) != NEK_OK) goto done;
+        if ((st = check_cuda(cudaGraphInstantiate(&gexec, graph, 0))) != NEK_OK) goto done;
+    }
+    while (it_done < max_iter) {
+        if ((st = check_cuda(cudaMemcpyAsync(&active, L.active, sizeof(int), cudaMemcpyDeviceToHost, s))) != NEK_OK)
+            goto done;
+        if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
+        if (active <= 0) break;
+        if (gexec && it_done + per_graph <= max_iter) {
+            if ((st = check_cuda(cudaGraphLaunch(gexec, s))) != NEK_OK) goto done;
+            it_done += per_graph;
+            launches += per_graph * per_iter_launches;
+            graph_launches++;
+        } else {
+            if ((st = one_iteration(s)) != NEK_OK) goto done;
+            it_done += 1;
+            launches += per_iter_launches;
+        }
+    }
+    {
+        std::vector<BScal> h(static_cast<size_t>(np));
+        if ((st = check_cuda(cudaMemcpyAsync(h.data(), L.sc, sizeof(BScal) * np, cudaMemcpyDeviceToHost, s))) !=
+            NEK_OK)
+            goto done;
+        if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
+        int nconv = 0, nbreak = 0;
+        for (int q = 0; q < np; q++) {
+            const bool stopped = h[q].done || h[q].status != NEK_OK;
+            if (iters_host) iters_host[q] = stopped ? h[q].iters : h[q].it;
+            if (relres_host) relres_host[q] = h[q].relres;
+            int sq = h[q].status != NEK_OK ? h[q].status : (h[q].done || tol_rel == 0.0) ? NEK_OK : NEK_ERR_NOT_CONVERGED;
+            if (status_host) status_host[q] = sq;
+            nconv += h[q].done;
+            nbreak += h[q].status != NEK_OK;
+        }
+        if (nbreak) st = NEK_ERR_BREAKDOWN;
+        else if (tol_rel > 0.0 && nconv < np) st = NEK_ERR_NOT_CONVERGED;
+        if (stats) {
+            stats->iterations_run = it_done;
+            stats->converged = nconv;
+            stats->kernel_launches = launches;
+            stats->graph_launches = graph_launches;
+        }
+    }
+done:
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (!workspace) {
+        cudaFreeAsync(ws, s);
+        nek_status st2 = check_cuda(cudaStreamSynchronize(s));
+        if (st == NEK_OK) st = st2;
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -23,8 +23,19 @@ inline bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb)
     return x < y + nb && y < x + na;
 }
 
+// Gather-scatter plan from a flat list of n non-negative global ids (n < 2^31).
+nek_status gs_create_flat(int64_t n, const int64_t* glo, nek_gs** out);
+
 // Host GLL rule: ascending nodes, weights, D[i*nx+l] = l_l'(xi_i).
 void gll_host(int nx, double* xi, double* rho, double* D);
+
+// Elements per CTA of the AX kernels: 0 = built-in default, else the value chosen
+// by nek_tune_ax for (impl, nx).
+int tuned_epb(int impl, int nx);
+nek_status launch_ax_fp64_epb(int epb, int64_t nelt, int nx, const double* D, const double* G, const double* u,
+                              double* w, cudaStream_t s);
+nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
+                            double* w, cudaStream_t s);
 
 // Kernel launchers (arguments already validated).
 nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w,

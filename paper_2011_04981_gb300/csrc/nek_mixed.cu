@@ -1,0 +1,518 @@
+// Reduced-precision AX and the FP64 defect-correction solve around it.
+//
+// The paper's further work (Section V of arXiv 2011.04981) names single, half
+// and fixed-point precision for the AX kernel.  Here the operator's
+// contractions take their inputs in FP32, BF16 or FP16 and accumulate in FP32:
+//   u_q = rnd(u / s_u)          s_u = per-element power of two >= max|u|
+//   D_q = rnd(D)
+//   ur = D_q u_q etc.           FP32 sums of products of rounded inputs
+//   [wr ws wt] = G_q [ur us ut] G_q = rnd(G / s_G), s_G per-element power of two
+//   w  = s_u s_G sum_a D_q^T rnd(w_a)
+// with rnd() rounding to the storage type (identity for FP32).  Products of two
+// BF16/FP16 values are exact in FP32, so this is the arithmetic of a
+// tensor-core contraction with FP32 accumulation.  u and w stay FP32; G is
+// stored in the reduced type, 6 values per point plus one FP32 scale per
+// element, so one apply moves 4 + 6 s + 4 bytes per point (32 B for FP32,
+// 20 B for BF16/FP16).
+//
+// The solve is iterative refinement (defect correction): the residual
+// r = mask(f - dssum(AX x)), its norm, the inner products and the update of x
+// are FP64 on the GPU; each correction d solves A d = r / ||r|| approximately by
+// Jacobi-PCG with FP32 vectors and the reduced-precision operator.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "nek_internal.h"
+#include "nek_pcg.cuh"
+
+namespace nek {
+
+namespace {
+
+template <class S>
+struct Lp;
+template <>
+struct Lp<float> {
+    __device__ static __forceinline__ float rnd(float x) { return x; }
+    __device__ static __forceinline__ float to_f(float v) { return v; }
+    __device__ static __forceinline__ float from_f(float x) { return x; }
+};
+template <>
+struct Lp<__nv_bfloat16> {
+    __device__ static __forceinline__ float rnd(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+    __device__ static __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __forceinline__ __nv_bfloat16 from_f(float x) { return __float2bfloat16_rn(x); }
+};
+template <>
+struct Lp<__half> {
+    __device__ static __forceinline__ float rnd(float x) { return __half2float(__float2half_rn(x)); }
+    __device__ static __forceinline__ float to_f(__half v) { return __half2float(v); }
+    __device__ static __forceinline__ __half from_f(float x) { return __float2half_rn(x); }
+};
+
+// slot[key] = max(slot[key], v) for v >= 0, one shared-memory atomic per key per warp.
+__device__ __forceinline__ void segmented_max_to_smem(int key, float v, float* slot)
+{
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const unsigned m = __reduce_max_sync(same, __float_as_uint(v));
+    if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(reinterpret_cast<unsigned*>(slot + key), m);
+}
+
+// Smallest power of two >= m (m > 0), as a float; 1 for m == 0.
+__device__ __forceinline__ float pow2_ceil(float m)
+{
+    if (!(m > 0.f)) return 1.f;
+    int e;
+    const float f = frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+    return ldexpf(1.f, f == 0.5f ? e - 1 : e);
+}
+
+constexpr int lp_epb(int nx)
+{
+    return nx == 2 ? 32 : nx == 3 ? 32 : nx == 4 ? 8 : nx == 5 ? 16 : nx == 6 ? 8 : nx == 7 ? 8 : nx == 8 ? 4
+         : nx == 9 ? 4 : nx == 10 ? 4 : nx == 11 ? 2 : nx == 12 ? 2 : nx == 13 ? 2 : 1;
+}
+
+template <int NX, int EPB>
+constexpr size_t lp_smem_bytes()
+{
+    return sizeof(float) * (size_t)(NX * NX + 2 * EPB * NX * NX * NX + EPB + 4);
+}
+
+template <class S, int NX, int EPB>
+__global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const double* __restrict__ D,
+                                                          const S* __restrict__ Glp,
+                                                          const float* __restrict__ gscale,
+                                                          const float* __restrict__ u, float* __restrict__ w)
+{
+    using L = Lp<S>;
+    constexpr int N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB;
+    extern __shared__ float fsm[];
+    float* sD = fsm;           // rnd(D)
+    float* sA = sD + N2;       // [EPB][N3] u_q, then wr_q
+    float* sB = sA + EPB * N3; // [EPB][N3] ws_q
+    float* sMax = sB + EPB * N3;
+
+    const int tid = threadIdx.x;
+    const int64_t e0 = (int64_t)blockIdx.x * EPB;
+    const int ne = static_cast<int>(nelt - e0 < EPB ? nelt - e0 : EPB);
+
+    for (int q = tid; q < N2; q += NT) sD[q] = L::rnd((float)D[q]);
+    for (int q = tid; q < EPB; q += NT) sMax[q] = 0.f;
+    {
+        const float* src = u + e0 * N3;
+        for (int q = tid; q < ne * N3; q += NT) sA[q] = __ldg(src + q);
+    }
+    __syncthreads();
+
+    const int el = tid / N2;
+    const int q2 = tid - el * N2;
+    const int i = q2 % NX, j = q2 / NX;
+    const bool active = el < ne;
+    float* ue = sA + el * N3;
+    float* se = sB + el * N3;
+    {
+        float m = 0.f;
+        if (active) {
+#pragma unroll
+            for (int l = 0; l < NX; l++) m = fmaxf(m, fabsf(ue[i + NX * (j + NX * l)]));
+        }
+        segmented_max_to_smem(el, m, sMax);
+    }
+    __syncthreads();
+    for (int q = tid; q < ne * N3; q += NT) sA[q] = L::rnd(sA[q] * (1.f / pow2_ceil(sMax[q / N3])));
+    __syncthreads();
+
+    float ul[NX], wr[NX], wt[NX];
+    if (active) {
+#pragma unroll
+        for (int l = 0; l < NX; l++) ul[l] = ue[i + NX * (j + NX * l)];
+        const S* Ge = Glp + (e0 + el) * (int64_t)N3 * 6;
+#pragma unroll
+        for (int k = 0; k < NX; k++) {
+            const int p = i + NX * (j + NX * k);
+            float ar = 0.f, as = 0.f, at = 0.f;
+#pragma unroll
+            for (int l = 0; l < NX; l++) {
+                ar = fmaf(sD[i * NX + l], ue[l + NX * (j + NX * k)], ar);
+                as = fmaf(sD[j * NX + l], ue[i + NX * (l + NX * k)], as);
+                at = fmaf(sD[k * NX + l], ul[l], at);
+            }
+            const S* g = Ge + 6 * p;
+            const float g0 = L::to_f(g[0]), g1 = L::to_f(g[1]), g2 = L::to_f(g[2]), g3 = L::to_f(g[3]),
+                        g4 = L::to_f(g[4]), g5 = L::to_f(g[5]);
+            wr[k] = L::rnd(fmaf(g0, ar, fmaf(g1, as, g2 * at)));
+            se[p] = L::rnd(fmaf(g1, ar, fmaf(g3, as, g4 * at)));
+            wt[k] = L::rnd(fmaf(g2, ar, fmaf(g4, as, g5 * at)));
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < NX; k++) ue[i + NX * (j + NX * k)] = wr[k];
+    }
+    __syncthreads();
+    if (active) {
+        const float scale = pow2_ceil(sMax[el]) * gscale[e0 + el];
+        float* we = w + (e0 + el) * (int64_t)N3;
+#pragma unroll
+        for (int k = 0; k < NX; k++) {
+            float s = 0.f;
+#pragma unroll
+            for (int l = 0; l < NX; l++) {
+                s = fmaf(sD[l * NX + i], ue[l + NX * (j + NX * k)], s);
+                s = fmaf(sD[l * NX + j], se[i + NX * (l + NX * k)], s);
+                s = fmaf(sD[l * NX + k], wt[l], s);
+            }
+            we[i + NX * (j + NX * k)] = s * scale;
+        }
+    }
+}
+
+template <class S, int NX>
+nek_status launch_lowp_nx(int64_t nelt, const double* D, const void* Glp, const float* gscale, const float* u,
+                          float* w, cudaStream_t s)
+{
+    constexpr int EPB = lp_epb(NX);
+    constexpr size_t smem = lp_smem_bytes<NX, EPB>();
+    static bool configured = false;
+    if (!configured) {
+        nek_status st = check_cuda(
+            cudaFuncSetAttribute(k_ax_lowp<S, NX, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (st != NEK_OK) return st;
+        configured = true;
+    }
+    const int64_t blocks = (nelt + EPB - 1) / EPB;
+    if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
+    k_ax_lowp<S, NX, EPB><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(nelt, D, static_cast<const S*>(Glp),
+                                                                          gscale, u, w);
+    return check_launch();
+}
+
+template <class S>
+nek_status launch_lowp_t(int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
+                         const float* u, float* w, cudaStream_t s)
+{
+    switch (nx) {
+        case 2: return launch_lowp_nx<S, 2>(nelt, D, Glp, gscale, u, w, s);
+        case 3: return launch_lowp_nx<S, 3>(nelt, D, Glp, gscale, u, w, s);
+        case 4: return launch_lowp_nx<S, 4>(nelt, D, Glp, gscale, u, w, s);
+        case 5: return launch_lowp_nx<S, 5>(nelt, D, Glp, gscale, u, w, s);
+        case 6: return launch_lowp_nx<S, 6>(nelt, D, Glp, gscale, u, w, s);
+        case 7: return launch_lowp_nx<S, 7>(nelt, D, Glp, gscale, u, w, s);
+        case 8: return launch_lowp_nx<S, 8>(nelt, D, Glp, gscale, u, w, s);
+        case 9: return launch_lowp_nx<S, 9>(nelt, D, Glp, gscale, u, w, s);
+        case 10: return launch_lowp_nx<S, 10>(nelt, D, Glp, gscale, u, w, s);
+        case 11: return launch_lowp_nx<S, 11>(nelt, D, Glp, gscale, u, w, s);
+        case 12: return launch_lowp_nx<S, 12>(nelt, D, Glp, gscale, u, w, s);
+        case 13: return launch_lowp_nx<S, 13>(nelt, D, Glp, gscale, u, w, s);
+        case 14: return launch_lowp_nx<S, 14>(nelt, D, Glp, gscale, u, w, s);
+        case 15: return launch_lowp_nx<S, 15>(nelt, D, Glp, gscale, u, w, s);
+        case 16: return launch_lowp_nx<S, 16>(nelt, D, Glp, gscale, u, w, s);
+        default: return NEK_ERR_UNSUPPORTED_NX;
+    }
+}
+
+nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
+                          const float* u, float* w, cudaStream_t s)
+{
+    switch (prec) {
+        case NEK_PREC_F32: return launch_lowp_t<float>(nelt, nx, D, Glp, gscale, u, w, s);
+        case NEK_PREC_BF16: return launch_lowp_t<__nv_bfloat16>(nelt, nx, D, Glp, gscale, u, w, s);
+        case NEK_PREC_F16: return launch_lowp_t<__half>(nelt, nx, D, Glp, gscale, u, w, s);
+        default: return NEK_ERR_INVALID_ARG;
+    }
+}
+
+// One block per element: s_G = pow2_ceil(max |G_e|); Glp = rnd(G / s_G).
+template <class S>
+__global__ void k_geom_lowp(int64_t nelt, int n6, const double* __restrict__ G, S* __restrict__ Glp,
+                            float* __restrict__ gscale)
+{
+    __shared__ float smax;
+    for (int64_t e = blockIdx.x; e < nelt; e += gridDim.x) {
+        if (threadIdx.x == 0) smax = 0.f;
+        __syncthreads();
+        float m = 0.f;
+        for (int q = threadIdx.x; q < n6; q += blockDim.x) m = fmaxf(m, fabsf((float)G[e * n6 + q]));
+        atomicMax(reinterpret_cast<int*>(&smax), __float_as_int(m));
+        __syncthreads();
+        const float sc = pow2_ceil(smax);
+        for (int q = threadIdx.x; q < n6; q += blockDim.x) Glp[e * n6 + q] = Lp<S>::from_f((float)(G[e * n6 + q] / sc));
+        if (threadIdx.x == 0) gscale[e] = sc;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- defect correction
+struct MixScalars {
+    double bnorm, rnorm, relres;
+};
+
+constexpr int NT = kReduceThreads;
+
+// x = 0; r = mask.f; partials of <r,r>_c
+__global__ void __launch_bounds__(NT) k_mix_init(int64_t n, const double* __restrict__ c,
+                                                  const uint8_t* __restrict__ mask, const double* __restrict__ f,
+                                                  double* __restrict__ x, double* __restrict__ r,
+                                                  double* __restrict__ parts)
+{
+    __shared__ double sh[NT / 32];
+    double acc = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
+        const double rq = mask[q] ? f[q] : 0.0;
+        x[q] = 0.0;
+        r[q] = rq;
+        acc += c[q] * rq * rq;
+    }
+    const double t = block_sum<NT>(acc, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = t;
+}
+
+// r = mask.(f - w); partials of <r,r>_c
+__global__ void __launch_bounds__(NT) k_mix_residual(int64_t n, const double* __restrict__ c,
+                                                      const uint8_t* __restrict__ mask, const double* __restrict__ f,
+                                                      const double* __restrict__ w, double* __restrict__ r,
+                                                      double* __restrict__ parts)
+{
+    __shared__ double sh[NT / 32];
+    double acc = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
+        const double rq = mask[q] ? f[q] - w[q] : 0.0;
+        r[q] = rq;
+        acc += c[q] * rq * rq;
+    }
+    const double t = block_sum<NT>(acc, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_mix_norm(const double* __restrict__ parts, int nb, int first,
+                                                  MixScalars* ms)
+{
+    __shared__ double sh[NT / 32];
+    const double rr = sum_partials<NT>(parts, nb, sh);
+    if (threadIdx.x == 0) {
+        ms->rnorm = sqrt(rr);
+        if (first) ms->bnorm = ms->rnorm;
+        ms->relres = ms->bnorm > 0.0 ? ms->rnorm / ms->bnorm : 0.0;
+    }
+}
+
+// r32 = r / ||r||
+__global__ void k_mix_scale_down(int64_t n, const double* __restrict__ r, float* __restrict__ r32,
+                                 const MixScalars* __restrict__ ms)
+{
+    const double inv = ms->rnorm > 0.0 ? 1.0 / ms->rnorm : 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        r32[q] = (float)(r[q] * inv);
+}
+
+// x += ||r|| d
+__global__ void k_mix_update_x(int64_t n, const float* __restrict__ d, double* __restrict__ x,
+                               const MixScalars* __restrict__ ms)
+{
+    const double s = ms->rnorm;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        x[q] = fma(s, (double)d[q], x[q]);
+}
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        b[q] = (float)a[q];
+}
+
+struct MixLayout {
+    double *r, *w, *minv64;
+    float *d, *minv, *c;
+    pcg::Buffers<float> b;
+    double* parts;
+    MixScalars* ms;
+    size_t bytes;
+};
+
+MixLayout mix_layout(void* base_, int64_t n, bool need_minv)
+{
+    using pcg::align256;
+    MixLayout L{};
+    char* base = static_cast<char*>(base_);
+    const size_t v8 = align256(sizeof(double) * std::max<int64_t>(n, 1));
+    const size_t v4 = align256(sizeof(float) * std::max<int64_t>(n, 1));
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        char* p = base ? base + off : nullptr;
+        off += b;
+        return p;
+    };
+    L.r = reinterpret_cast<double*>(take(v8));
+    L.w = reinterpret_cast<double*>(take(v8));
+    L.minv64 = need_minv ? reinterpret_cast<double*>(take(v8)) : nullptr;
+    L.d = reinterpret_cast<float*>(take(v4));
+    L.minv = reinterpret_cast<float*>(take(v4));
+    L.c = reinterpret_cast<float*>(take(v4));
+    L.b.r = reinterpret_cast<float*>(take(v4));
+    L.b.z = reinterpret_cast<float*>(take(v4));
+    L.b.p = reinterpret_cast<float*>(take(v4));
+    L.b.w = reinterpret_cast<float*>(take(v4));
+    L.b.parts = reinterpret_cast<double*>(take(align256(sizeof(double) * 2 * kMaxReduceBlocks)));
+    L.b.sc = reinterpret_cast<pcg::Scalars*>(take(align256(sizeof(pcg::Scalars))));
+    L.parts = reinterpret_cast<double*>(take(align256(sizeof(double) * kMaxReduceBlocks)));
+    L.ms = reinterpret_cast<MixScalars*>(take(align256(sizeof(MixScalars))));
+    L.bytes = off;
+    return L;
+}
+
+}  // namespace
+
+}  // namespace nek
+
+using namespace nek;
+
+extern "C" {
+
+size_t nek_lowp_bytes_per_value(int precision)
+{
+    return precision == NEK_PREC_F32 ? 4 : (precision == NEK_PREC_BF16 || precision == NEK_PREC_F16) ? 2 : 0;
+}
+
+nek_status nek_geom_lowp(int64_t nelt, int nx, int precision, const double* G, void* Glp, float* gscale,
+                         void* stream)
+{
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt < 0 || nek_lowp_bytes_per_value(precision) == 0) return NEK_ERR_INVALID_ARG;
+    if (nelt == 0) return NEK_OK;
+    if (!G || !Glp || !gscale || !is_aligned(G, 8) || !is_aligned(Glp, 4) || !is_aligned(gscale, 4))
+        return NEK_ERR_INVALID_ARG;
+    const int n6 = 6 * nx * nx * nx;
+    const int blocks = static_cast<int>(nelt < 152 * 16 ? nelt : 152 * 16);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    switch (precision) {
+        case NEK_PREC_F32: k_geom_lowp<float><<<blocks, 256, 0, s>>>(nelt, n6, G, static_cast<float*>(Glp), gscale); break;
+        case NEK_PREC_BF16:
+            k_geom_lowp<__nv_bfloat16><<<blocks, 256, 0, s>>>(nelt, n6, G, static_cast<__nv_bfloat16*>(Glp), gscale);
+            break;
+        default: k_geom_lowp<__half><<<blocks, 256, 0, s>>>(nelt, n6, G, static_cast<__half*>(Glp), gscale); break;
+    }
+    return check_launch();
+}
+
+nek_status nek_ax_lowp(int64_t nelt, int nx, int precision, const double* D, const void* Glp, const float* gscale,
+                       const float* u, float* w, void* stream)
+{
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt < 0 || nek_lowp_bytes_per_value(precision) == 0) return NEK_ERR_INVALID_ARG;
+    if (nelt == 0) return NEK_OK;
+    if (!D || !Glp || !gscale || !u || !w) return NEK_ERR_INVALID_ARG;
+    if (!is_aligned(D, 8) || !is_aligned(Glp, 4) || !is_aligned(u, 4) || !is_aligned(w, 4)) return NEK_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(float) * (size_t)nelt * nx * nx * nx;
+    if (ranges_overlap(u, bytes, w, bytes)) return NEK_ERR_INVALID_ARG;
+    return launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, u, w, static_cast<cudaStream_t>(stream));
+}
+
+size_t nek_cg_mixed_workspace_bytes(int64_t nelt, int nx, int need_minv)
+{
+    if (nelt < 0 || nx < kMinNx || nx > kMaxNx) return 0;
+    return mix_layout(nullptr, nelt * (int64_t)nx * nx * nx, need_minv != 0).bytes;
+}
+
+nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
+                              const float* Gff, int precision, const void* Glp, const float* gscale,
+                              const uint8_t* mask, const double* minv, const double* f, double* x, double tol_rel,
+                              double inner_tol, int max_outer, int max_inner, void* workspace,
+                              nek_mixed_info* info, void* stream)
+{
+    if (info) *info = nek_mixed_info{};
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (!gs || nelt < 0 || max_outer < 0 || max_inner < 1 || !(tol_rel > 0.0) || !(inner_tol > 0.0) ||
+        !(inner_tol < 1.0) || nek_lowp_bytes_per_value(precision) == 0)
+        return NEK_ERR_INVALID_ARG;
+    const int64_t n = nelt * (int64_t)nx * nx * nx;
+    if (gs->npts != n) return NEK_ERR_INVALID_ARG;
+    if (n == 0) return NEK_OK;
+    if (!D || !G || !Glp || !gscale || !mask || !f || !x) return NEK_ERR_INVALID_ARG;
+    if (!is_aligned(G, 16) || !is_aligned(f, 8) || !is_aligned(x, 16) || (Gff && !is_aligned(Gff, 16)) ||
+        (minv && !is_aligned(minv, 8)) || !is_aligned(Glp, 4))
+        return NEK_ERR_INVALID_ARG;
+    if (workspace && !is_aligned(workspace, 256)) return NEK_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = nek_cg_mixed_workspace_bytes(nelt, nx, minv == nullptr);
+    void* ws = workspace;
+    nek_status st = NEK_OK;
+    if (!ws) {
+        if (check_cuda(cudaMallocAsync(&ws, bytes, s)) != NEK_OK) return NEK_ERR_NOMEM;
+    }
+    MixLayout L = mix_layout(ws, n, minv == nullptr);
+    const double* mv = minv;
+    const int nb = reduce_blocks(n);
+    const int sb = pcg::stream_blocks(n);
+    MixScalars h{};
+    int outer = 0, inner_total = 0, launches = 0;
+    auto ax64 = [&](const double* p, double* w) {
+        return Gff ? launch_ax_ff(nelt, nx, D, Gff, p, w, s) : launch_ax_fp64(nelt, nx, D, G, p, w, s);
+    };
+    auto ax_lo = [&](const float* p, float* w, cudaStream_t ss) {
+        return launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss);
+    };
+
+    if (!minv) {
+        if ((st = nek_jacobi_minv(gs, nelt, nx, D, G, mask, L.minv64, stream)) != NEK_OK) goto done;
+        mv = L.minv64;
+        launches += 3;
+    }
+    k_d2f<<<sb, 256, 0, s>>>(n, mv, L.minv);
+    k_d2f<<<sb, 256, 0, s>>>(n, gs->d_c, L.c);
+    k_mix_init<<<nb, NT, 0, s>>>(n, gs->d_c, mask, f, x, L.r, L.parts);
+    k_mix_norm<<<1, NT, 0, s>>>(L.parts, nb, 1, L.ms);
+    launches += 4;
+    if ((st = check_launch()) != NEK_OK) goto done;
+    for (;;) {
+        if ((st = check_cuda(cudaMemcpyAsync(&h, L.ms, sizeof(h), cudaMemcpyDeviceToHost, s))) != NEK_OK) goto done;
+        if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
+        if (!std::isfinite(h.relres)) {
+            st = NEK_ERR_BREAKDOWN;
+            goto done;
+        }
+        if (h.relres <= tol_rel || h.bnorm == 0.0) break;
+        if (outer >= max_outer) {
+            st = NEK_ERR_NOT_CONVERGED;
+            goto done;
+        }
+        outer++;
+        // the inner right-hand side goes to b.w: pcg::run reads it once, at initialisation
+        k_mix_scale_down<<<sb, 256, 0, s>>>(n, L.r, L.b.w, L.ms);
+        launches += 1;
+        {
+            pcg::Result res;
+            nek_status si = pcg::run<float>(gs, n, L.c, mask, L.minv, L.b.w, L.d, L.b, inner_tol, max_inner, 10,
+                                           false, ax_lo, s, &res);
+            inner_total += res.iters;
+            launches += res.launches;
+            if (si == NEK_ERR_BREAKDOWN || si == NEK_ERR_CUDA) {
+                st = si;
+                goto done;
+            }
+        }
+        k_mix_update_x<<<sb, 256, 0, s>>>(n, L.d, x, L.ms);
+        if ((st = ax64(x, L.w)) != NEK_OK) goto done;
+        if ((st = pcg::dssum<double>(gs, L.w, s)) != NEK_OK) goto done;
+        k_mix_residual<<<nb, NT, 0, s>>>(n, gs->d_c, mask, f, L.w, L.r, L.parts);
+        k_mix_norm<<<1, NT, 0, s>>>(L.parts, nb, 0, L.ms);
+        launches += 5;
+        if ((st = check_launch()) != NEK_OK) goto done;
+    }
+done:
+    if (info) {
+        info->outer_iters = outer;
+        info->inner_iters = inner_total;
+        info->relres = h.relres;
+        info->kernel_launches = launches;
+    }
+    if (!workspace) {
+        cudaFreeAsync(ws, s);
+        nek_status st2 = check_cuda(cudaStreamSynchronize(s));
+        if (st == NEK_OK) st = st2;
+    }
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,314 @@
+// Preconditioned CG on the device, generic over the vector storage type V
+// (double for the FP64 solve, float for the inner solve of the defect
+// correction).  Scalars and all inner products are accumulated in double.
+//
+// One iteration (the CG iteration of Section II-B of arXiv 2011.04981:
+// operator, nearest-neighbour exchange, reductions, vector updates):
+//   w = AX p (caller's operator) ; w = dssum(w) ; w = mask.w ; pw = <p,w>_c
+//   alpha = rz/pw ; x += alpha p ; r -= alpha w ; z = minv r ; rr = <r,r>_c ;
+//   rz' = <r,z>_c ; stop if sqrt(rr)/||b|| <= tol ; beta = rz'/rz ; p = z + beta p
+// Reductions use a fixed grid per length and a fixed shuffle tree, so results
+// are deterministic.  Once the residual test passes, or a breakdown is seen, a
+// device flag makes every later update kernel of the call return at once.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "nek_internal.h"
+#include "nek_reduce.cuh"
+
+namespace nek {
+namespace pcg {
+
+struct Scalars {
+    double rz;      // <r, z>_c of the current iterate
+    double pw;      // <p, w>_c
+    double alpha;
+    double beta;
+    double rr;      // <r, r>_c
+    double bnorm;   // ||b||_c
+    double relres;  // ||r||_c / ||b||_c
+    double tol;
+    int done;       // residual test passed
+    int status;     // NEK_OK or NEK_ERR_BREAKDOWN
+    int iters;      // iterations completed when done/status was set
+    int it;         // iterations executed so far
+};
+
+constexpr int NT = kReduceThreads;
+
+__device__ __forceinline__ bool halted(const Scalars* sc) { return sc->done || sc->status != NEK_OK; }
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+inline int stream_blocks(int64_t n)
+{
+    int64_t nb = (n + 255) / 256;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nb, 152 * 16)));
+}
+
+namespace {
+
+// One thread per group: left-to-right sum over members (ascending local index),
+// written back to every member; groups are disjoint.
+template <class V>
+__global__ void k_dssum_t(int64_t ngroups, const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
+                          V* __restrict__ v)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int a = off[g], b = off[g + 1];
+        V s = v[mem[a]];
+        for (int o = a + 1; o < b; o++) s += v[mem[o]];
+        for (int o = a; o < b; o++) v[mem[o]] = s;
+    }
+}
+
+template <class V>
+nek_status dssum(const nek_gs* gs, V* v, cudaStream_t s)
+{
+    if (gs->ngroups == 0) return NEK_OK;
+    const int64_t nb = (gs->ngroups + 255) / 256;
+    k_dssum_t<V><<<static_cast<int>(std::min<int64_t>(nb, 152 * 64)), 256, 0, s>>>(gs->ngroups, gs->d_offsets,
+                                                                                 gs->d_members, v);
+    return check_launch();
+}
+
+// x = 0, r = mask.f, z = minv r, p = z; partials of <r,z>_c and <r,r>_c.
+template <class V>
+__global__ void __launch_bounds__(NT) k_init(int64_t n, const V* __restrict__ c, const uint8_t* __restrict__ mask,
+                                              const V* __restrict__ minv, const V* __restrict__ f, V* __restrict__ x,
+                                              V* __restrict__ r, V* __restrict__ z, V* __restrict__ p,
+                                              double* __restrict__ parts)
+{
+    __shared__ double sh[NT / 32];
+    double arz = 0.0, arr = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
+        const V rq = mask[q] ? f[q] : V(0);
+        const V zq = minv[q] * rq;
+        x[q] = V(0);
+        r[q] = rq;
+        z[q] = zq;
+        p[q] = zq;
+        arz += (double)c[q] * (double)rq * (double)zq;
+        arr += (double)c[q] * (double)rq * (double)rq;
+    }
+    double t = block_sum<NT>(arz, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = t;
+    t = block_sum<NT>(arr, sh);
+    if (threadIdx.x == 0) parts[gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_init_finish(const double* __restrict__ parts, int nb, double tol,
+                                                     Scalars* sc)
+{
+    __shared__ double sh[NT / 32];
+    const double rz = sum_partials<NT>(parts, nb, sh);
+    const double rr = sum_partials<NT>(parts + nb, nb, sh);
+    if (threadIdx.x == 0) {
+        sc->rz = rz;
+        sc->rr = rr;
+        sc->bnorm = sqrt(rr);
+        sc->tol = tol;
+        sc->it = 0;
+        sc->iters = 0;
+        sc->alpha = sc->beta = sc->pw = 0.0;
+        sc->status = NEK_OK;
+        sc->done = 0;
+        sc->relres = 0.0;
+        if (!(rr >= 0.0) || !isfinite(rr) || !isfinite(rz)) {
+            sc->status = NEK_ERR_BREAKDOWN;
+        } else if (rr == 0.0) {
+            sc->done = 1;  // b = 0: x = 0 is the solution
+        } else {
+            sc->relres = 1.0;
+        }
+    }
+}
+
+// w <- mask.w ; partials of <p,w>_c
+template <class V>
+__global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, const uint8_t* __restrict__ mask,
+                                            const V* __restrict__ p, V* __restrict__ w, double* __restrict__ parts,
+                                            const Scalars* __restrict__ sc)
+{
+    __shared__ double sh[NT / 32];
+    if (halted(sc)) return;
+    double acc = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
+        V wq = w[q];
+        if (!mask[q]) {
+            wq = V(0);
+            w[q] = V(0);
+        }
+        acc += (double)c[q] * (double)p[q] * (double)wq;
+    }
+    const double t = block_sum<NT>(acc, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_alpha(const double* __restrict__ parts, int nb, Scalars* sc)
+{
+    __shared__ double sh[NT / 32];
+    if (halted(sc)) return;
+    const double pw = sum_partials<NT>(parts, nb, sh);
+    if (threadIdx.x == 0) {
+        sc->it += 1;
+        sc->pw = pw;
+        if (!(pw > 0.0) || !isfinite(pw)) {
+            sc->status = NEK_ERR_BREAKDOWN;
+            sc->iters = sc->it;
+        } else {
+            sc->alpha = sc->rz / pw;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha w; z = minv r; partials of <r,r>_c and <r,z>_c
+template <class V>
+__global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ c, const V* __restrict__ minv,
+                                                const V* __restrict__ p, const V* __restrict__ w, V* __restrict__ x,
+                                                V* __restrict__ r, V* __restrict__ z, double* __restrict__ parts,
+                                                const Scalars* __restrict__ sc)
+{
+    __shared__ double sh[NT / 32];
+    if (halted(sc)) return;
+    const V alpha = (V)sc->alpha;
+    double arr = 0.0, arz = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
+        x[q] = fma(alpha, p[q], x[q]);
+        const V rq = fma(-alpha, w[q], r[q]);
+        const V zq = minv[q] * rq;
+        r[q] = rq;
+        z[q] = zq;
+        arr += (double)c[q] * (double)rq * (double)rq;
+        arz += (double)c[q] * (double)rq * (double)zq;
+    }
+    double t = block_sum<NT>(arr, sh);
+    if (threadIdx.x == 0) parts[blockIdx.x] = t;
+    t = block_sum<NT>(arz, sh);
+    if (threadIdx.x == 0) parts[gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(NT) k_beta(const double* __restrict__ parts, int nb, Scalars* sc)
+{
+    __shared__ double sh[NT / 32];
+    if (halted(sc)) return;
+    const double rr = sum_partials<NT>(parts, nb, sh);
+    const double rz = sum_partials<NT>(parts + nb, nb, sh);
+    if (threadIdx.x == 0) {
+        sc->rr = rr;
+        sc->relres = sqrt(rr) / sc->bnorm;
+        if (!isfinite(sc->relres) || !isfinite(rz)) {
+            sc->status = NEK_ERR_BREAKDOWN;
+            sc->iters = sc->it;
+        } else if (sc->tol > 0.0 && sc->relres <= sc->tol) {
+            sc->done = 1;
+            sc->iters = sc->it;
+        } else {
+            sc->beta = rz / sc->rz;
+            sc->rz = rz;
+        }
+    }
+}
+
+template <class V>
+__global__ void k_p(int64_t n, const V* __restrict__ z, V* __restrict__ p, const Scalars* __restrict__ sc)
+{
+    if (halted(sc)) return;
+    const V beta = (V)sc->beta;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        p[q] = fma(beta, p[q], z[q]);
+}
+
+}  // namespace
+
+template <class V>
+struct Buffers {
+    V *r, *z, *p, *w;
+    double* parts;  // 2 * kMaxReduceBlocks
+    Scalars* sc;
+};
+
+struct Result {
+    int iters = 0;
+    double relres = 0.0;
+    int launches = 0;
+    double ax_ms = 0.0;
+    int ax_timed = 0;
+};
+
+// Runs PCG from x = 0.  `ax(p, w, stream)` applies the element operator.
+// tol > 0: stop at convergence (NEK_ERR_NOT_CONVERGED after max_iter);
+// tol == 0: exactly max_iter iterations.  Leaves the stream synchronised.
+template <class V, class AxFn>
+nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, const V* minv, const V* f, V* x,
+               const Buffers<V>& b, double tol, int max_iter, int check_every, bool time_ax, AxFn&& ax,
+               cudaStream_t s, Result* res)
+{
+    const int nb = reduce_blocks(n);
+    const int sb = stream_blocks(n);
+    int launches = 0;
+    std::vector<cudaEvent_t> ev;
+    Scalars h{};
+    nek_status st = NEK_OK;
+    k_init<V><<<nb, NT, 0, s>>>(n, c, mask, minv, f, x, b.r, b.z, b.p, b.parts);
+    k_init_finish<<<1, NT, 0, s>>>(b.parts, nb, tol, b.sc);
+    launches += 2;
+    if ((st = check_launch()) != NEK_OK) goto done;
+    if (time_ax) {
+        ev.resize(2 * (size_t)std::min(max_iter, 100000));
+        for (auto& e : ev)
+            if ((st = check_cuda(cudaEventCreate(&e))) != NEK_OK) goto done;
+    }
+    for (int it = 1; it <= max_iter; it++) {
+        const bool timed = time_ax && (size_t)(2 * it) <= ev.size();
+        if (timed) cudaEventRecord(ev[2 * (it - 1)], s);
+        if ((st = ax(b.p, b.w, s)) != NEK_OK) goto done;
+        if (timed) cudaEventRecord(ev[2 * (it - 1) + 1], s);
+        if ((st = dssum<V>(gs, b.w, s)) != NEK_OK) goto done;
+        k_pw<V><<<nb, NT, 0, s>>>(n, c, mask, b.p, b.w, b.parts, b.sc);
+        k_alpha<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
+        k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.p, b.w, x, b.r, b.z, b.parts, b.sc);
+        k_beta<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
+        launches += 6;
+        if ((st = check_launch()) != NEK_OK) goto done;
+        if (tol > 0.0 && (it % check_every == 0 || it == max_iter)) {
+            if ((st = check_cuda(cudaMemcpyAsync(&h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) != NEK_OK) goto done;
+            if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
+            if (h.done || h.status != NEK_OK) break;
+        }
+        if (it < max_iter) {
+            k_p<V><<<sb, 256, 0, s>>>(n, b.z, b.p, b.sc);
+            launches += 1;
+        }
+    }
+    if ((st = check_cuda(cudaMemcpyAsync(&h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) != NEK_OK) goto done;
+    if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
+    if (time_ax) {
+        const int nt = std::min<int>(std::min(max_iter, h.it), static_cast<int>(ev.size() / 2));
+        double tot = 0.0;
+        for (int q = 0; q < nt; q++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[2 * q], ev[2 * q + 1]) == cudaSuccess) tot += ms;
+        }
+        res->ax_ms = tot;
+        res->ax_timed = nt;
+    }
+    res->iters = (h.done || h.status != NEK_OK) ? h.iters : h.it;
+    res->relres = h.relres;
+    if (h.status != NEK_OK)
+        st = static_cast<nek_status>(h.status);
+    else if (tol > 0.0 && !h.done)
+        st = NEK_ERR_NOT_CONVERGED;
+done:
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    res->launches = launches;
+    return st;
+}
+
+}  // namespace pcg
+}  // namespace nek

@@ -1,0 +1,94 @@
+// Elements-per-CTA selection for the AX kernels.
+//
+// Every AX kernel is compiled for several elements-per-CTA counts (1, 2, 4 where
+// the thread count and shared memory allow).  The count changes only how
+// elements are grouped into CTAs, never the arithmetic on an element, so all
+// variants give bit-identical results; it trades occupancy against how much of
+// a CTA's load phase overlaps other CTAs' compute.  nek_tune_ax times the
+// variants on the caller's data and keeps the fastest for later launches.
+#include <atomic>
+
+#include "nek_internal.h"
+
+namespace nek {
+
+namespace {
+std::atomic<int> g_epb[2][kMaxNx + 1];
+}
+
+int tuned_epb(int impl, int nx)
+{
+    if (impl < 0 || impl > 1 || nx < 0 || nx > kMaxNx) return 0;
+    return g_epb[impl][nx].load(std::memory_order_relaxed);
+}
+
+}  // namespace nek
+
+using namespace nek;
+
+extern "C" {
+
+nek_status nek_set_ax_epb(int impl, int nx, int epb)
+{
+    if (impl != NEK_AX_FP64 && impl != NEK_AX_FF) return NEK_ERR_INVALID_ARG;
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (epb != 0 && epb != 1 && epb != 2 && epb != 4) return NEK_ERR_INVALID_ARG;
+    g_epb[impl][nx].store(epb, std::memory_order_relaxed);
+    return NEK_OK;
+}
+
+int nek_get_ax_epb(int impl, int nx) { return tuned_epb(impl, nx); }
+
+nek_status nek_tune_ax(int impl, int64_t nelt, int nx, const double* D, const void* Gx, const double* u, double* w,
+                       int* epb_out, float* ms_out, void* stream)
+{
+    if (impl != NEK_AX_FP64 && impl != NEK_AX_FF) return NEK_ERR_INVALID_ARG;
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt <= 0 || !D || !Gx || !u || !w || !is_aligned(Gx, 16) || !is_aligned(u, 16) || !is_aligned(w, 16))
+        return NEK_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(double) * (size_t)nelt * nx * nx * nx;
+    if (ranges_overlap(u, bytes, w, bytes)) return NEK_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    nek_status st = check_cuda(cudaEventCreate(&e0));
+    if (st == NEK_OK) st = check_cuda(cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 0.f;
+    const int cand[3] = {1, 2, 4};
+    for (int c = 0; c < 3 && st == NEK_OK; c++) {
+        auto run = [&]() {
+            return impl == NEK_AX_FF
+                       ? launch_ax_ff_epb(cand[c], nelt, nx, D, static_cast<const float*>(Gx), u, w, s)
+                       : launch_ax_fp64_epb(cand[c], nelt, nx, D, static_cast<const double*>(Gx), u, w, s);
+        };
+        nek_status sv = run();
+        if (sv == NEK_ERR_INVALID_ARG) continue;  // this count does not fit this nx
+        if (sv != NEK_OK) {
+            st = sv;
+            break;
+        }
+        if ((st = run()) != NEK_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && st == NEK_OK; r++) st = run();
+        cudaEventRecord(e1, s);
+        if (st != NEK_OK) break;
+        if ((st = check_cuda(cudaEventSynchronize(e1))) != NEK_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 3.f;
+        if (best == 0 || ms < best_ms) {
+            best = cand[c];
+            best_ms = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != NEK_OK) return st;
+    if (best == 0) return NEK_ERR_INVALID_ARG;
+    g_epb[impl][nx].store(best, std::memory_order_relaxed);
+    if (epb_out) *epb_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return NEK_OK;
+}
+
+}  // extern "C"

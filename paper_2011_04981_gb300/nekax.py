@@ -50,6 +50,25 @@ class NekCgOpts(ctypes.Structure):
                 ("Gff", ctypes.c_void_p)]
 
 
+class NekBatchStats(ctypes.Structure):
+    _fields_ = [("iterations_run", ctypes.c_int), ("converged", ctypes.c_int), ("kernel_launches", ctypes.c_int),
+                ("graph_launches", ctypes.c_int)]
+
+
+class NekFcgInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("relres", ctypes.c_double), ("fell_back_at", ctypes.c_int),
+                ("net_applications", ctypes.c_int), ("net_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int)]
+
+
+class NekMixedInfo(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int), ("relres", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int)]
+
+
+PREC_F32 = 0
+PREC_BF16 = 1
+PREC_F16 = 2
+
 _lib = None
 
 _P = ctypes.c_void_p
@@ -76,6 +95,34 @@ _SIGS = {
     "nek_dot_c": ([_P, _P, _P, _P, _P], _I),
     "nek_dot_c_noalloc": ([_I64, _P, _P, _P, _P, _P], _I),
     "nek_cg_workspace_bytes": ([_I64, _I, _I], ctypes.c_size_t),
+    "nek_batch_create": ([_I, _P, _P, _P, ctypes.POINTER(_P)], _I),
+    "nek_batch_destroy": ([_P], _I),
+    "nek_batch_info": ([_P, _P, _P, _P], _I),
+    "nek_batch_gs": ([_P], _P),
+    "nek_batch_workspace_bytes": ([_P, _I], ctypes.c_size_t),
+    "nek_batch_jacobi_minv": ([_P, _P, _P, _P, _P], _I),
+    "nek_batch_cg_solve": ([_P, _P, _P, _P, _P, _P, _P, _D, _I, _I, _P, _P, _P, _P, ctypes.POINTER(NekBatchStats),
+                            _P], _I),
+    "nek_net_param_count": ([], _I),
+    "nek_net_prep": ([_I64, _I, _P, _P, _P, _P, _P], _I),
+    "nek_net_apply": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
+    "nek_net_train_workspace_bytes": ([_I], ctypes.c_size_t),
+    "nek_net_forward_batch": ([_I, _P, _P, _P, _P, _P], _I),
+    "nek_net_train_grad": ([_I, _P, _P, _P, _P, _P, _P, _P], _I),
+    "nek_adam_step": ([_I, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I, _P],
+                      _I),
+    "nek_fcg_workspace_bytes": ([_I64, _I, _I], ctypes.c_size_t),
+    "nek_fcg_solve": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _P, _D, _I, _I, _D, _P, ctypes.POINTER(NekFcgInfo),
+                       _P], _I),
+    "nek_tune_ax": ([_I, _I64, _I, _P, _P, _P, _P, _P, _P, _P], _I),
+    "nek_set_ax_epb": ([_I, _I, _I], _I),
+    "nek_get_ax_epb": ([_I, _I], _I),
+    "nek_lowp_bytes_per_value": ([_I], ctypes.c_size_t),
+    "nek_geom_lowp": ([_I64, _I, _I, _P, _P, _P, _P], _I),
+    "nek_ax_lowp": ([_I64, _I, _I, _P, _P, _P, _P, _P, _P], _I),
+    "nek_cg_mixed_workspace_bytes": ([_I64, _I, _I], ctypes.c_size_t),
+    "nek_cg_solve_mixed": ([_P, _I64, _I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _D, _D, _I, _I, _P,
+                            ctypes.POINTER(NekMixedInfo), _P], _I),
     "nek_cg_solve": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, _P], _I),
     "nek_cg_solve_ex": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, ctypes.POINTER(NekCgOpts), _P],
                         _I),
@@ -224,6 +271,152 @@ def dot_c_noalloc(n, c, a, b, result, stream=None):
     """nek_dot_c_noalloc: the weighted dot with library-resident scratch (no allocation)."""
     _check("nek_dot_c_noalloc", load().nek_dot_c_noalloc(n, _ptr(c), _ptr(a), _ptr(b), _ptr(result),
                                                          _stream(stream)))
+
+
+def tune_ax(impl, nelt, nx, D, Gx, u, w, stream=None):
+    """Time the elements-per-CTA variants and keep the fastest; returns (epb, ms)."""
+    e = _I(0)
+    ms = ctypes.c_float(0.0)
+    _check("nek_tune_ax", load().nek_tune_ax(int(impl), nelt, nx, _ptr(D), _ptr(Gx), _ptr(u), _ptr(w),
+                                             ctypes.byref(e), ctypes.byref(ms), _stream(stream)))
+    return e.value, ms.value
+
+
+def set_ax_epb(impl, nx, epb):
+    _check("nek_set_ax_epb", load().nek_set_ax_epb(int(impl), nx, epb))
+
+
+def get_ax_epb(impl, nx):
+    return load().nek_get_ax_epb(int(impl), nx)
+
+
+def geom_lowp(nelt, nx, precision, G, Glp, gscale, stream=None):
+    _check("nek_geom_lowp", load().nek_geom_lowp(nelt, nx, precision, _ptr(G), _ptr(Glp), _ptr(gscale),
+                                                 _stream(stream)))
+
+
+def ax_lowp(nelt, nx, precision, D, Glp, gscale, u, w, stream=None):
+    _check("nek_ax_lowp", load().nek_ax_lowp(nelt, nx, precision, _ptr(D), _ptr(Glp), _ptr(gscale), _ptr(u),
+                                             _ptr(w), _stream(stream)))
+
+
+def cg_solve_mixed(gs, nelt, nx, D, G, Gff, precision, Glp, gscale, m, minv, f, x, tol=1e-8, inner_tol=1e-2,
+                   max_outer=50, max_inner=5000, workspace=None, stream=None):
+    """FP64 defect correction with reduced-precision inner PCG; returns dict(status, outer, inner, relres)."""
+    info = NekMixedInfo()
+    st = load().nek_cg_solve_mixed(gs.handle, nelt, nx, _ptr(D), _ptr(G), _ptr(Gff), int(precision), _ptr(Glp),
+                                   _ptr(gscale), _ptr(m), _ptr(minv), _ptr(f), _ptr(x), float(tol),
+                                   float(inner_tol), int(max_outer), int(max_inner), _ptr(workspace),
+                                   ctypes.byref(info), _stream(stream))
+    if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+        raise NekError("nek_cg_solve_mixed", st)
+    return dict(status=st, outer=info.outer_iters, inner=info.inner_iters, relres=info.relres,
+                kernel_launches=info.kernel_launches)
+
+
+class BatchPlan:
+    """Owning wrapper of a ``nek_batch*``: problems must be given sorted by nx."""
+
+    def __init__(self, nelts, nxs, glo_concat):
+        self.nprob = len(nelts)
+        ne = np.ascontiguousarray(nelts, dtype=np.int64)
+        nx = np.ascontiguousarray(nxs, dtype=np.int32)
+        glo = np.ascontiguousarray(glo_concat, dtype=np.int64).reshape(-1)
+        h = _P()
+        _check("nek_batch_create", load().nek_batch_create(self.nprob, ne.ctypes.data, nx.ctypes.data,
+                                                           glo.ctypes.data, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def info(self):
+        a, b, c = _I64(), _I(), _I()
+        _check("nek_batch_info", load().nek_batch_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def gs_handle(self):
+        return load().nek_batch_gs(self._h)
+
+    def workspace_bytes(self, need_minv=True):
+        return int(load().nek_batch_workspace_bytes(self._h, 1 if need_minv else 0))
+
+    def jacobi_minv(self, G, m, minv, stream=None):
+        _check("nek_batch_jacobi_minv", load().nek_batch_jacobi_minv(self._h, _ptr(G), _ptr(m), _ptr(minv),
+                                                                     _stream(stream)))
+
+    def cg_solve(self, G, Gff, m, minv, f, x, tol=1e-8, max_iter=1000, iters_per_graph=10, workspace=None,
+                 stream=None):
+        it = np.zeros(self.nprob, dtype=np.int32)
+        rr = np.zeros(self.nprob)
+        stv = np.zeros(self.nprob, dtype=np.int32)
+        stats = NekBatchStats()
+        st = load().nek_batch_cg_solve(self._h, _ptr(G), _ptr(Gff), _ptr(m), _ptr(minv), _ptr(f), _ptr(x),
+                                       float(tol), int(max_iter), int(iters_per_graph), _ptr(workspace),
+                                       it.ctypes.data, rr.ctypes.data, stv.ctypes.data, ctypes.byref(stats),
+                                       _stream(stream))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            raise NekError("nek_batch_cg_solve", st)
+        return dict(status=st, iters=it, relres=rr, statuses=stv, iterations_run=stats.iterations_run,
+                    converged=stats.converged, kernel_launches=stats.kernel_launches,
+                    graph_launches=stats.graph_launches)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().nek_batch_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def net_param_count():
+    return int(load().nek_net_param_count())
+
+
+def net_prep(nelt, nx, r, minv, xin, scale, stream=None):
+    _check("nek_net_prep", load().nek_net_prep(nelt, nx, _ptr(r), _ptr(minv), _ptr(xin), _ptr(scale),
+                                               _stream(stream)))
+
+
+def net_apply(nelt, nx, theta, xin, scale, c, z, stream=None):
+    _check("nek_net_apply", load().nek_net_apply(nelt, nx, _ptr(theta), _ptr(xin), _ptr(scale), _ptr(c), _ptr(z),
+                                                 _stream(stream)))
+
+
+def net_train_workspace_bytes(batch):
+    return int(load().nek_net_train_workspace_bytes(batch))
+
+
+def net_forward_batch(batch, theta, xin, y, workspace, stream=None):
+    _check("nek_net_forward_batch", load().nek_net_forward_batch(batch, _ptr(theta), _ptr(xin), _ptr(y),
+                                                                 _ptr(workspace), _stream(stream)))
+
+
+def net_train_grad(batch, theta, xin, target, grad, loss, workspace, stream=None):
+    _check("nek_net_train_grad", load().nek_net_train_grad(batch, _ptr(theta), _ptr(xin), _ptr(target), _ptr(grad),
+                                                           _ptr(loss), _ptr(workspace), _stream(stream)))
+
+
+def adam_step(n, theta, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check("nek_adam_step", load().nek_adam_step(n, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), float(lr),
+                                                 float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
+
+
+def fcg_solve(gs, nelt, nx, D, G, Gff, m, minv, theta, f, x, tol=1e-8, max_iter=5000, stag_window=50,
+              stag_factor=0.1, workspace=None, stream=None):
+    info = NekFcgInfo()
+    st = load().nek_fcg_solve(gs.handle, nelt, nx, _ptr(D), _ptr(G), _ptr(Gff), _ptr(m), _ptr(minv), _ptr(theta),
+                              _ptr(f), _ptr(x), float(tol), int(max_iter), int(stag_window), float(stag_factor),
+                              _ptr(workspace), ctypes.byref(info), _stream(stream))
+    if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+        raise NekError("nek_fcg_solve", st)
+    return dict(status=st, iters=info.iters, relres=info.relres, fell_back_at=info.fell_back_at,
+                net_applications=info.net_applications, net_ms=info.net_ms, kernel_launches=info.kernel_launches)
 
 
 def cg_workspace_bytes(nelt, nx, need_minv=True) -> int:

@@ -55,3 +55,48 @@ class DeviceProblem:
         Gff = self.prepare_ff() if ax_impl == nekax.AX_FF else None
         return nekax.cg_solve(self.gs, self.nelt, self.nx, self.D, self.G, self.mask, self.minv, f, x, tol,
                               max_iter, workspace, check_every, time_ax, stream, ax_impl=ax_impl, Gff=Gff)
+
+
+class DeviceBatch:
+    """Many meshes solved together: concatenated (sorted by nx) device buffers and a nek_batch plan."""
+
+    def __init__(self, meshes, fields, device="cuda", ff=True):
+        import torch
+
+        order = sorted(range(len(meshes)), key=lambda q: meshes[q].nx)
+        self.order = order
+        self.meshes = [meshes[q] for q in order]
+        self.device = torch.device(device)
+        nelts = [m.nelt for m in self.meshes]
+        nxs = [m.nx for m in self.meshes]
+        glo = np.concatenate([m.glo_num.reshape(-1) for m in self.meshes])
+        self.plan = nekax.BatchPlan(nelts, nxs, glo)
+        self.npts = int(sum(m.npts for m in self.meshes))
+        self.offsets = np.cumsum([0] + [m.npts for m in self.meshes])
+        self.G = torch.empty(self.npts * 6, dtype=torch.float64, device=self.device)
+        # geometric factors per problem (one nek_geom call per problem)
+        for q, m in enumerate(self.meshes):
+            c = torch.from_numpy(np.ascontiguousarray(m.corners)).to(self.device)
+            nekax.geom(m.nelt, m.nx, c, self.G[int(self.offsets[q]) * 6:])
+        self.mask = torch.from_numpy(np.concatenate([m.mask.reshape(-1) for m in self.meshes])).to(self.device)
+        self.f = torch.from_numpy(np.concatenate([fields[q].reshape(-1) for q in order])).to(self.device)
+        self.minv = torch.empty(self.npts, dtype=torch.float64, device=self.device)
+        self.plan.jacobi_minv(self.G, self.mask, self.minv)
+        self.Gff = None
+        if ff:
+            self.Gff = torch.empty(self.npts * 12, dtype=torch.float32, device=self.device)
+            for q, m in enumerate(self.meshes):
+                o = int(self.offsets[q])
+                nekax.geom_ff(m.nelt, m.nx, self.G[o * 6:], self.Gff[o * 12:])
+
+    def solve(self, x, tol=1e-8, max_iter=5000, iters_per_graph=10, workspace=None):
+        return self.plan.cg_solve(self.G, self.Gff, self.mask, self.minv, self.f, x, tol, max_iter, iters_per_graph,
+                                  workspace)
+
+    def split(self, v):
+        """Per-problem views of a concatenated vector, in the caller's original order."""
+        parts = [v[int(self.offsets[q]):int(self.offsets[q + 1])] for q in range(len(self.meshes))]
+        out = [None] * len(parts)
+        for pos, q in enumerate(self.order):
+            out[q] = parts[pos]
+        return out

@@ -26,7 +26,7 @@ def lib():
 
 def _declared_symbols():
     txt = open(os.path.join(ROOT, "include", "nekax.h")).read()
-    return sorted(set(re.findall(r"^(?:const char\*|nek_status|int|size_t)\s+(nek_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^(?:const\s+)?\w+\s*\*?\s*(nek_\w+)\s*\(", txt, re.M)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -64,7 +64,7 @@ def test_ax_rejects_bad_arguments_before_launch(lib):
     assert L.nek_ax(4, 8, None, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
     assert L.nek_ax(4, 8, A16, None, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
     assert L.nek_ax(4, 8, A16, A16 + 8, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # G misaligned
-    assert L.nek_ax(4, 8, A16, A16, A16 + 8, A16 * 2, None) == nekax.ERR_INVALID_ARG  # u misaligned
+    assert L.nek_ax(4, 8, A16, A16, A16 + 4, A16 * 2, None) == nekax.ERR_INVALID_ARG  # u misaligned
     assert L.nek_ax(4, 8, A16 + 4, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # D misaligned
     # u and w overlap (4 elements of 512 doubles = 16 KiB each)
     assert L.nek_ax(4, 8, A16, A16, A16, A16 + 4096, None) == nekax.ERR_INVALID_ARG
@@ -124,3 +124,49 @@ def test_ff_entry_points_reject_bad_arguments(lib):
     opts = nekax.NekCgOpts(1, 0, 0.0, 0, 0, nekax.AX_FF, None)
     assert L.nek_cg_solve_ex(None, 1, 3, A16, A16, A16, None, A16, A16, 1e-8, 10, None, None, None,
                              ctypes.byref(opts), None) == nekax.ERR_INVALID_ARG
+
+
+def test_tuning_and_lowp_entry_points_reject_bad_arguments(lib):
+    L = lib
+    A16 = 0x10000
+    assert L.nek_set_ax_epb(7, 8, 1) == nekax.ERR_INVALID_ARG
+    assert L.nek_set_ax_epb(0, 1, 1) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_set_ax_epb(0, 8, 3) == nekax.ERR_INVALID_ARG
+    assert L.nek_set_ax_epb(1, 8, 2) == nekax.OK and L.nek_get_ax_epb(1, 8) == 2
+    assert L.nek_set_ax_epb(1, 8, 0) == nekax.OK and L.nek_get_ax_epb(1, 8) == 0
+    assert L.nek_tune_ax(0, 0, 8, A16, A16, A16, A16 * 2, None, None, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_tune_ax(0, 4, 8, A16, A16 + 8, A16, A16 * 2, None, None, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_tune_ax(0, 4, 8, A16, A16, A16, A16 + 64, None, None, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_lowp_bytes_per_value(0) == 4 and L.nek_lowp_bytes_per_value(1) == 2
+    assert L.nek_lowp_bytes_per_value(2) == 2 and L.nek_lowp_bytes_per_value(3) == 0
+    assert L.nek_geom_lowp(4, 8, 3, A16, A16, A16, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_geom_lowp(4, 1, 0, A16, A16, A16, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_ax_lowp(4, 8, 1, A16, A16, A16, A16, A16 + 64, None) == nekax.ERR_INVALID_ARG  # overlap
+    assert L.nek_ax_lowp(4, 8, 5, A16, A16, A16, A16, A16 * 4, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_lowp(0, 8, 1, None, None, None, None, None, None) == nekax.OK
+    info = nekax.NekMixedInfo()
+    # inner_tol must be in (0, 1); tol must be > 0
+    assert L.nek_cg_solve_mixed(None, 1, 3, A16, A16, None, 0, A16, A16, A16, None, A16, A16, 1e-8, 1.5, 5, 10,
+                                None, ctypes.byref(info), None) == nekax.ERR_INVALID_ARG
+    assert L.nek_cg_mixed_workspace_bytes(10, 8, 1) > 10 * 512 * (3 * 8 + 7 * 4)
+
+
+def test_batch_entry_points_reject_bad_arguments(lib):
+    L = lib
+    h = ctypes.c_void_p()
+    ne = np.array([2, 2], dtype=np.int64)
+    nx_bad_order = np.array([8, 6], dtype=np.int32)
+    nx_bad = np.array([6, 20], dtype=np.int32)
+    glo = np.zeros(2 * 512, dtype=np.int64)
+    assert L.nek_batch_create(0, ne.ctypes.data, nx_bad.ctypes.data, glo.ctypes.data, ctypes.byref(h)) == \
+        nekax.ERR_INVALID_ARG
+    assert L.nek_batch_create(2, ne.ctypes.data, nx_bad.ctypes.data, glo.ctypes.data, ctypes.byref(h)) == \
+        nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_batch_create(2, ne.ctypes.data, nx_bad_order.ctypes.data, glo.ctypes.data, ctypes.byref(h)) == \
+        nekax.ERR_INVALID_ARG
+    assert L.nek_batch_destroy(None) == nekax.OK
+    assert L.nek_batch_info(None, None, None, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_batch_workspace_bytes(None, 1) == 0
+    stats = nekax.NekBatchStats()
+    assert L.nek_batch_cg_solve(None, 0x100, None, 0x100, None, 0x100, 0x100, 1e-8, 10, 5, None, None, None, None,
+                                ctypes.byref(stats), None) == nekax.ERR_INVALID_ARG

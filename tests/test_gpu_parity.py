@@ -291,8 +291,9 @@ def test_geom_ff_split_is_faithful():
     nekax.geom_ff(mesh.nelt, nx, _t(G), Gff)
     g = Gff.cpu().numpy().astype(np.float64)
     back = g[..., 0::2] + g[..., 1::2]
-    assert np.max(np.abs(back - G) / np.abs(G).max()) <= 2.0 ** -46
-    assert np.array_equal(g[..., 0::2], G.astype(np.float32).astype(np.float64))
+    # hi carries the leading 24 bits (truncated), lo the next 23: |G - hi - lo| <= 2^-46 |G|
+    assert np.all(np.abs(back - G) <= 2.0 ** -46 * np.abs(G))
+    assert np.all(np.abs(g[..., 0::2]) <= np.abs(G)) and np.all(np.abs(G - g[..., 0::2]) <= 2.0 ** -23 * np.abs(G))
 
 
 @pytest.mark.parametrize("nx", [8, 10, 16])
@@ -343,3 +344,128 @@ def test_cg_with_ff_operator(dims, nx):
     st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 1e-8, 2000)
     assert abs(res["iters"] - itr) <= 2, (res["iters"], itr)
     assert Pr.residual(f, x.cpu().numpy()) <= 1e-8 * (1 + 1e-3)
+
+
+# ------------------------------------------------------------------ elements-per-CTA variants
+@pytest.mark.parametrize("impl", [nekax.AX_FP64, nekax.AX_FF])
+@pytest.mark.parametrize("nx", [5, 8, 10])
+def test_epb_variants_bit_identical_and_tuner(impl, nx):
+    mesh = inputs.box_mesh(5, 3, 3, nx, perturb=0.1, seed=nx)
+    P = DeviceProblem(mesh, DEV, build_minv=False)
+    Gx = P.prepare_ff() if impl == nekax.AX_FF else P.G
+    u = _t(inputs.random_local_field(mesh.nelt, nx, seed=3))
+    outs = []
+    try:
+        for epb in (1, 2, 4):
+            nekax.set_ax_epb(impl, nx, epb)
+            w = torch.full_like(u, float("nan"))
+            (P.ax_ff if impl == nekax.AX_FF else P.ax)(u, w)
+            outs.append(w)
+        torch.cuda.synchronize()
+        for w in outs[1:]:
+            assert torch.equal(w, outs[0])
+        epb, ms = nekax.tune_ax(impl, mesh.nelt, nx, P.D, Gx, u, outs[0])
+        assert epb in (1, 2, 4) and ms > 0 and nekax.get_ax_epb(impl, nx) == epb
+    finally:
+        nekax.set_ax_epb(impl, nx, 0)
+
+
+# ------------------------------------------------------------------ reduced precision (FP32 / BF16 / FP16)
+UNIT_IN = {nekax.PREC_F32: 2.0 ** -24, nekax.PREC_BF16: 2.0 ** -8, nekax.PREC_F16: 2.0 ** -11}
+
+
+@pytest.mark.parametrize("prec", [nekax.PREC_F32, nekax.PREC_BF16, nekax.PREC_F16])
+@pytest.mark.parametrize("nx", [4, 8, 10, 13, 16])
+def test_ax_lowp_componentwise_bound(prec, nx):
+    """|w - w_ref| <= C (u_in + (2 nx + 3) u_acc) w_abs with w_abs = AX(|D|, |G|, |u|) from the oracle, C = 4."""
+    mesh = inputs.box_mesh(3, 2, 2, nx, perturb=0.15, seed=nx)
+    xi, rho, D = ref.gll(nx)
+    G = ref.geom(mesh.corners, nx, xi, rho)
+    u = inputs.random_local_field(mesh.nelt, nx, seed=7) * 10.0 ** np.linspace(-3, 3, mesh.nelt)[:, None]
+    nb = nekax.load().nek_lowp_bytes_per_value(prec)
+    dt = {4: torch.float32, 2: torch.float16}[nb]
+    Glp = torch.empty((mesh.nelt, nx ** 3, 6), dtype=dt, device=DEV)
+    gsc = torch.empty(mesh.nelt, dtype=torch.float32, device=DEV)
+    nekax.geom_lowp(mesh.nelt, nx, prec, _t(G), Glp, gsc)
+    ud = torch.from_numpy(u.astype(np.float32)).to(DEV)
+    wd = torch.full_like(ud, float("nan"))
+    nekax.ax_lowp(mesh.nelt, nx, prec, _t(D), Glp, gsc, ud, wd)
+    torch.cuda.synchronize()
+    w = wd.cpu().numpy().astype(np.float64)
+    u32 = u.astype(np.float32).astype(np.float64)
+    w_ref = ref.ax(D, G, u32)
+    w_abs = ref.ax(np.abs(D), np.abs(G), np.abs(u32))
+    bound = 4.0 * (UNIT_IN[prec] + (2 * nx + 3) * 2.0 ** -24) * w_abs
+    ratio = np.max(np.abs(w - w_ref) / bound)
+    assert ratio <= 1.0, ratio
+
+
+@pytest.mark.parametrize("prec", [nekax.PREC_F32, nekax.PREC_BF16, nekax.PREC_F16])
+@pytest.mark.parametrize("outer_ff", [False, True])
+def test_cg_mixed_defect_correction(prec, outer_ff):
+    nx = 6
+    mesh = inputs.box_mesh(4, 3, 3, nx, perturb=0.1, seed=5)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=6)
+    nb = nekax.load().nek_lowp_bytes_per_value(prec)
+    Glp = torch.empty((mesh.nelt, nx ** 3, 6), dtype={4: torch.float32, 2: torch.float16}[nb], device=DEV)
+    gsc = torch.empty(mesh.nelt, dtype=torch.float32, device=DEV)
+    nekax.geom_lowp(mesh.nelt, nx, prec, P.G, Glp, gsc)
+    x = torch.full((mesh.nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+    Gff = P.prepare_ff() if outer_ff else None
+    res = nekax.cg_solve_mixed(P.gs, mesh.nelt, nx, P.D, P.G, Gff, prec, Glp, gsc, P.mask, P.minv, _t(f), x,
+                               tol=1e-10, inner_tol=1e-2, max_outer=40, max_inner=2000)
+    assert res["status"] == nekax.OK, res
+    assert res["relres"] <= 1e-10
+    assert Pr.residual(f, x.cpu().numpy()) <= 1e-10 * 1.01
+    assert res["outer"] >= 2 and res["inner"] > res["outer"]
+
+
+# ------------------------------------------------------------------ batched solves
+def _batch_case(seed=0):
+    specs = [dict(ex=2, ey=2, ez=2, nx=8), dict(ex=3, ey=2, ez=1, nx=6), dict(ex=2, ey=1, ez=1, nx=10),
+             dict(ex=4, ey=2, ez=2, nx=6), dict(ex=1, ey=1, ez=1, nx=3), dict(ex=2, ey=2, ez=1, nx=8)]
+    meshes = [inputs.box_mesh(sp["ex"], sp["ey"], sp["ez"], sp["nx"], perturb=0.1, seed=seed + q)
+              for q, sp in enumerate(specs)]
+    fields = [inputs.random_global_field(m, seed=seed + 50 + q) for q, m in enumerate(meshes)]
+    return meshes, fields
+
+
+@pytest.mark.parametrize("ff", [False, True])
+def test_batch_matches_oracle_per_problem(ff):
+    from paper_2011_04981_gb300.problem import DeviceBatch
+
+    meshes, fields = _batch_case()
+    B = DeviceBatch(meshes, fields, DEV, ff=ff)
+    x = torch.full((B.npts,), float("nan"), dtype=torch.float64, device=DEV)
+    res = B.solve(x, tol=1e-9, max_iter=3000, iters_per_graph=7)
+    assert res["status"] == nekax.OK and res["converged"] == len(meshes), res
+    assert res["graph_launches"] > 0
+    xs = B.split(x.cpu().numpy())
+    iters = [None] * len(meshes)
+    for pos, q in enumerate(B.order):
+        iters[q] = int(res["iters"][pos])
+    for q, m in enumerate(meshes):
+        Pr = ref.Problem(m)
+        st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, m.mask, Pr.minv, fields[q], 1e-9, 3000)
+        assert abs(iters[q] - itr) <= 2, (q, iters[q], itr)
+        assert Pr.residual(fields[q], xs[q].reshape(m.nelt, -1)) <= 1e-9 * 1.001
+
+
+def test_batch_graph_replay_is_bit_identical_to_eager():
+    from paper_2011_04981_gb300.problem import DeviceBatch
+
+    meshes, fields = _batch_case(seed=10)
+    fields[2] = np.zeros_like(fields[2])  # a problem with b = 0 stops at once
+    B = DeviceBatch(meshes, fields, DEV, ff=True)
+    x1 = torch.empty((B.npts,), dtype=torch.float64, device=DEV)
+    x2 = torch.empty_like(x1)
+    r1 = B.solve(x1, tol=1e-9, max_iter=3000, iters_per_graph=0)
+    r2 = B.solve(x2, tol=1e-9, max_iter=3000, iters_per_graph=5)
+    assert r1["graph_launches"] == 0 and r2["graph_launches"] > 0
+    assert np.array_equal(r1["iters"], r2["iters"])
+    assert torch.equal(x1, x2)
+    zero_pos = B.order.index(2)
+    assert r1["iters"][zero_pos] == 0
+    assert float(B.split(x1)[2].abs().max()) == 0.0
