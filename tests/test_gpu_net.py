@@ -1,0 +1,136 @@
+"""GPU parity of the learned-preconditioner kernels against the FP64 network oracle.
+
+Weights are drawn and rounded to BF16 first (the kernels stage BF16 weights), so
+the only difference left is FP32 accumulation and FP32 erf in GELU: forward and
+gradients are compared norm-wise at 1e-4 and 2e-3.  Flexible CG is checked by the
+oracle's residual of its result.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from oracle import net as onet  # noqa: E402
+from oracle import ref  # noqa: E402
+from paper_2011_04981_gb300 import inputs, nekax  # noqa: E402
+from paper_2011_04981_gb300.problem import DeviceProblem  # noqa: E402
+
+DEV = "cuda"
+
+
+def _bf16(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def _theta(seed, scale=0.25):
+    rng = np.random.default_rng(seed)
+    th = rng.normal(scale=scale, size=onet.NPARAM)
+    return _bf16(th).astype(np.float64)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def test_param_count():
+    assert nekax.net_param_count() == onet.NPARAM == 8241
+
+
+def test_forward_matches_oracle():
+    B = 5
+    rng = np.random.default_rng(1)
+    th = _theta(2)
+    x = rng.normal(size=(B, 2, 8, 8, 8))
+    ws = torch.empty(nekax.net_train_workspace_bytes(B) // 4 + 64, dtype=torch.float32, device=DEV)
+    y = torch.empty((B, 512), dtype=torch.float32, device=DEV)
+    nekax.net_forward_batch(B, torch.from_numpy(th.astype(np.float32)).to(DEV),
+                            torch.from_numpy(x.astype(np.float32)).to(DEV), y, ws)
+    torch.cuda.synchronize()
+    yr = onet.forward(th, x.astype(np.float32).astype(np.float64))[:, 0].reshape(B, 512)
+    assert _rel(y.cpu().numpy().astype(np.float64), yr) <= 1e-4
+
+
+def test_gradient_matches_oracle():
+    B = 4
+    rng = np.random.default_rng(3)
+    th = _theta(4)
+    x = rng.normal(size=(B, 2, 8, 8, 8)).astype(np.float32).astype(np.float64)
+    t = rng.normal(size=(B, 8, 8, 8)).astype(np.float32).astype(np.float64)
+    ws = torch.empty(nekax.net_train_workspace_bytes(B) // 4 + 64, dtype=torch.float32, device=DEV)
+    g = torch.empty(onet.NPARAM, dtype=torch.float32, device=DEV)
+    loss = torch.empty(1, dtype=torch.float32, device=DEV)
+    nekax.net_train_grad(B, torch.from_numpy(th.astype(np.float32)).to(DEV),
+                         torch.from_numpy(x.astype(np.float32)).to(DEV),
+                         torch.from_numpy(t.reshape(B, 512).astype(np.float32)).to(DEV), g, loss, ws)
+    torch.cuda.synchronize()
+    L, gr, _ = onet.loss_and_grad(th, x, t)
+    assert abs(float(loss.item()) - L) <= 1e-4 * L
+    gg = g.cpu().numpy().astype(np.float64)
+    o = 0
+    for name, shp in onet.SHAPES:
+        n = int(np.prod(shp))
+        assert _rel(gg[o:o + n], gr[o:o + n]) <= 2e-3, name
+        o += n
+
+
+def test_prep_and_apply_match_oracle():
+    mesh = inputs.box_mesh(3, 2, 2, 8, perturb=0.15, seed=2)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    th = _theta(7)
+    r = inputs.random_local_field(mesh.nelt, 8, seed=9) * mesh.mask
+    rd = torch.from_numpy(r).to(DEV)
+    xin = torch.empty((mesh.nelt, 2, 512), dtype=torch.float32, device=DEV)
+    sc = torch.empty(mesh.nelt, dtype=torch.float32, device=DEV)
+    nekax.net_prep(mesh.nelt, 8, rd, P.minv, xin, sc)
+    c = torch.empty_like(rd)
+    P.gs.inv_multiplicity(c)
+    z = torch.empty_like(rd)
+    nekax.net_apply(mesh.nelt, 8, torch.from_numpy(th.astype(np.float32)).to(DEV), xin, sc, c, z)
+    torch.cuda.synchronize()
+    x_ref, sr, sj = onet.element_inputs(r, Pr.minv * r)
+    assert _rel(xin.cpu().numpy().reshape(mesh.nelt, 2, 512).astype(np.float64), x_ref) <= 1e-6
+    assert np.allclose(sc.cpu().numpy(), sj, rtol=1e-6)
+    y = onet.forward(th, xin.cpu().numpy().astype(np.float64).reshape(mesh.nelt, 2, 8, 8, 8))[:, 0]
+    z_ref = y.reshape(mesh.nelt, 512) * sc.cpu().numpy().astype(np.float64)[:, None] * Pr.c
+    assert _rel(z.cpu().numpy(), z_ref) <= 1e-4
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(5)
+    n = 1000
+    th = rng.normal(size=n).astype(np.float32)
+    m = np.zeros(n, dtype=np.float32)
+    v = np.zeros(n, dtype=np.float32)
+    thd, md, vd = (torch.from_numpy(a.copy()).to(DEV) for a in (th, m, v))
+    th64, m64, v64 = th.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for step in range(1, 4):
+        g = rng.normal(size=n).astype(np.float32)
+        nekax.adam_step(n, thd, torch.from_numpy(g).to(DEV), md, vd, 1e-2, step)
+        th64, m64, v64 = onet.adam(th64, g.astype(np.float64), m64, v64, step, lr=1e-2)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(thd.cpu().numpy() - th64)) <= 1e-6
+
+
+def test_fcg_jacobi_mode_and_random_net():
+    mesh = inputs.box_mesh(4, 3, 3, 8, perturb=0.15, seed=4)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=5)
+    fd = torch.from_numpy(f).to(DEV)
+    x = torch.empty_like(fd)
+    r0 = nekax.fcg_solve(P.gs, mesh.nelt, 8, P.D, P.G, None, P.mask, P.minv, None, fd, x, tol=1e-8)
+    assert r0["status"] == nekax.OK and r0["net_applications"] == 0
+    st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 1e-8, 5000)
+    assert abs(r0["iters"] - itr) <= 3, (r0["iters"], itr)
+    assert Pr.residual(f, x.cpu().numpy()) <= 1e-8 * 1.001
+    # an untrained network: flexible CG still converges (with Jacobi taking over on stagnation)
+    th = torch.from_numpy(_theta(11, scale=0.05).astype(np.float32)).to(DEV)
+    x2 = torch.empty_like(fd)
+    r1 = nekax.fcg_solve(P.gs, mesh.nelt, 8, P.D, P.G, P.prepare_ff(), P.mask, P.minv, th, fd, x2, tol=1e-8,
+                         max_iter=20000, stag_window=30, stag_factor=0.5)
+    assert r1["status"] == nekax.OK, r1
+    assert r1["net_applications"] >= 1
+    assert Pr.residual(f, x2.cpu().numpy()) <= 1e-8 * 1.001
