@@ -50,6 +50,10 @@ def parse():
                     help="also time FP64 defect correction with FP32/BF16/FP16 inner solves (to 1e-8 and 1e-10)")
     ap.add_argument("--batch", type=int, default=0,
                     help="also solve this many uneven problems (nelt log-uniform in [8,4096]) batched")
+    ap.add_argument("--learned", action="store_true",
+                    help="also train the element network and compare flexible CG with it against Jacobi-PCG")
+    ap.add_argument("--learned-meshes", type=int, default=200)
+    ap.add_argument("--learned-epochs", type=int, default=30)
     ap.add_argument("--tune", action="store_true", help="pick elements-per-CTA with nek_tune_ax before timing")
     ap.add_argument("--ax", default="fp64", choices=["fp64", "ff"],
                     help="AX operator inside the solve: native FP64 or FP64-accurate float-float")
@@ -307,6 +311,31 @@ def batch_block(torch, nprob, tol=1e-8):
             "gdofs_useful": pts_iters / dt / 1e9, "operator": "nek_ax_ff (FP64-accurate)"}
 
 
+def learned_block(torch, n_meshes=200, epochs=30, eval_elems=24):
+    """Configuration 5: pairs from the solver on n_meshes random meshes of the family, GPU training with the
+    library's kernels, then time to 1e-8 on a held-out eval_elems^3 mesh with and without the network."""
+    from paper_2011_04981_gb300 import learned
+
+    t0 = time.perf_counter()
+    data = learned.make_training_data(n_meshes=n_meshes, pairs_per_mesh=100, seed=0)
+    t_data = time.perf_counter() - t0
+    val_data = learned.make_training_data(n_meshes=max(2, n_meshes // 20), pairs_per_mesh=100, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    theta, hist = learned.train(data, epochs=epochs, batch=256, lr=2e-3, seed=0, kind="energy")
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    val = learned.validation_loss(theta, val_data)
+    theta0 = learned.init_params(0, "cuda")
+    val0 = learned.validation_loss(theta0, val_data)
+    mesh = learned.mesh_family(seed=777, e=eval_elems)
+    cmp = learned.compare_on_mesh(theta, mesh, seed=3)
+    return {"pairs": len(data), "data_seconds": t_data, "train_seconds": t_train, "epochs": epochs,
+            "loss": "element energy norm", "train_loss_first_last": [hist[0], hist[-1]],
+            "val_loss_untrained": val0, "val_loss_trained": val,
+            "eval_mesh": "%d^3 elements, nx=8, perturbation 0.15 h, stretch up to 8:1" % eval_elems, **cmp}
+
+
 def run_native(args):
     import torch
 
@@ -423,6 +452,8 @@ def run_native(args):
         torch.cuda.synchronize()
         line["cg_to_1e-8"] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"],
                               "status": nekax.status_string(r["status"]), "precision": "fp64 jacobi-pcg"}
+    if args.learned and rank == 0:
+        line["learned"] = learned_block(torch, args.learned_meshes, args.learned_epochs)
     if args.mixed and rank == 0:
         line["mixed"] = mixed_block(torch, P, f, x)
     if args.batch and rank == 0:

@@ -130,7 +130,9 @@ nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, co
  * impl = NEK_AX_FP64 / NEK_AX_FF, 16-byte aligned) and keeps the fastest for
  * all later launches of that (impl, nx) in this process; *epb_out and *ms_out
  * (nullable) receive it and its time per launch.  nek_set_ax_epb sets the size
- * directly (0 restores the built-in default); nek_get_ax_epb reads it back.
+ * directly (0 restores the built-in default; a size that does not fit the
+ * kernel's thread or shared-memory limits for that nx is NEK_ERR_INVALID_ARG);
+ * nek_get_ax_epb reads it back.
  * These settings are process-wide.  No paper counterpart: the paper picks its
  * FPGA kernel count by hand (Section IV).
  */
@@ -334,6 +336,17 @@ nek_status nek_net_forward_batch(int batch, const float* theta, const float* xin
                                  void* stream);
 nek_status nek_net_train_grad(int batch, const float* theta, const float* xin, const float* target, float* grad,
                               float* loss, void* workspace, void* stream);
+
+/* Same with the loss measured in each sample's element energy norm:
+ * loss = mean_b (y_b - t_b)^T A_b (y_b - t_b) / t_b^T A_b t_b, where A_b is the
+ * element operator of sample b given by its FP32 geometric factors Glp32
+ * [batch][512][6] with per-sample scales gscale [batch] (nek_geom_lowp layout
+ * with NEK_PREC_F32) and D (device FP64, nx = 8).  The norm ignores the
+ * constants, which an element-local prediction cannot fix, and weights the
+ * high-frequency error a local preconditioner must remove. */
+nek_status nek_net_train_grad_energy(int batch, const float* theta, const float* xin, const float* target,
+                                     const double* D, const float* Glp32, const float* gscale, float* grad,
+                                     float* loss, void* workspace, void* stream);
 
 /* One Adam step (Kingma & Ba) on n parameters; step >= 1 is the step count used
  * for bias correction. */

@@ -112,15 +112,10 @@ def loss(theta, x, t):
     return float(np.mean(num / den))
 
 
-def loss_and_grad(theta, x, t):
-    """Loss and its gradient with respect to theta (and to the input x)."""
+def backward(theta, cache, dy):
+    """Gradients of sum(dy * y) with respect to theta and to the input."""
     P = unpack(theta)
-    y, (x0, h1, a1, h2, a2) = forward(theta, x, keep=True)
-    B = x.shape[0]
-    den = np.sum(t ** 2, axis=(1, 2, 3))
-    r = y[:, 0] - t
-    L = float(np.mean(np.sum(r ** 2, axis=(1, 2, 3)) / den))
-    dy = (2.0 / B) * (r / den[:, None, None, None])[:, None]
+    x0, h1, a1, h2, a2 = cache
     g = {}
     g["W3"] = conv_weight_grad(dy, a2)
     g["b3"] = dy.sum(axis=(0, 2, 3, 4))
@@ -131,7 +126,44 @@ def loss_and_grad(theta, x, t):
     g["W1"] = conv_weight_grad(dh1, x0)
     g["b1"] = dh1.sum(axis=(0, 2, 3, 4))
     dx = conv_input_grad(dh1, P["W1"])
-    return L, pack(g), dx
+    return pack(g), dx
+
+
+def loss_and_grad(theta, x, t):
+    """Loss and its gradient with respect to theta (and to the input x)."""
+    y, cache = forward(theta, x, keep=True)
+    B = x.shape[0]
+    den = np.sum(t ** 2, axis=(1, 2, 3))
+    r = y[:, 0] - t
+    L = float(np.mean(np.sum(r ** 2, axis=(1, 2, 3)) / den))
+    dy = (2.0 / B) * (r / den[:, None, None, None])[:, None]
+    g, dx = backward(theta, cache, dy)
+    return L, g, dx
+
+
+def energy_loss(theta, x, t, A):
+    """mean_b (y_b - t_b)^T A_b (y_b - t_b) / t_b^T A_b t_b with A [B, n^3, n^3] (element matrices)."""
+    B = x.shape[0]
+    y = forward(theta, x)[:, 0].reshape(B, -1)
+    tt = t.reshape(B, -1)
+    d = y - tt
+    num = np.einsum("bp,bpq,bq->b", d, A, d)
+    den = np.einsum("bp,bpq,bq->b", tt, A, tt)
+    return float(np.mean(num / den))
+
+
+def energy_loss_and_grad(theta, x, t, A):
+    B = x.shape[0]
+    y, cache = forward(theta, x, keep=True)
+    yf = y[:, 0].reshape(B, -1)
+    tt = t.reshape(B, -1)
+    d = yf - tt
+    Ad = np.einsum("bpq,bq->bp", A, d)
+    den = np.einsum("bp,bpq,bq->b", tt, A, tt)
+    L = float(np.mean(np.sum(d * Ad, axis=1) / den))
+    dy = ((2.0 / B) * Ad / den[:, None]).reshape(y.shape)
+    g, dx = backward(theta, cache, dy)
+    return L, g, dx
 
 
 def adam(theta, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):

@@ -193,6 +193,36 @@ nek_status launch_ax_fp64_epb(int epb, int64_t nelt, int nx, const double* D, co
     }
 }
 
+namespace {
+template <int NX>
+bool ax_fits_rt(int epb)
+{
+    return (epb == 1 && ax_fits<NX, 1>()) || (epb == 2 && ax_fits<NX, 2>()) || (epb == 4 && ax_fits<NX, 4>());
+}
+}  // namespace
+
+bool ax_fp64_epb_fits(int nx, int epb)
+{
+    switch (nx) {
+        case 2: return ax_fits_rt<2>(epb);
+        case 3: return ax_fits_rt<3>(epb);
+        case 4: return ax_fits_rt<4>(epb);
+        case 5: return ax_fits_rt<5>(epb);
+        case 6: return ax_fits_rt<6>(epb);
+        case 7: return ax_fits_rt<7>(epb);
+        case 8: return ax_fits_rt<8>(epb);
+        case 9: return ax_fits_rt<9>(epb);
+        case 10: return ax_fits_rt<10>(epb);
+        case 11: return ax_fits_rt<11>(epb);
+        case 12: return ax_fits_rt<12>(epb);
+        case 13: return ax_fits_rt<13>(epb);
+        case 14: return ax_fits_rt<14>(epb);
+        case 15: return ax_fits_rt<15>(epb);
+        case 16: return ax_fits_rt<16>(epb);
+        default: return false;
+    }
+}
+
 nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w,
                           cudaStream_t s)
 {

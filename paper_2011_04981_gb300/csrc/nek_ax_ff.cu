@@ -197,11 +197,7 @@ struct Lanes<float2> {
 };
 
 template <int NX>
-constexpr int ff_epb()
-{
-    return NX == 2 ? 32 : NX == 3 ? 32 : NX == 4 ? 8 : NX == 5 ? 16 : NX == 6 ? 8 : NX == 7 ? 8 : NX == 8 ? 4
-         : NX == 9 ? 4 : NX == 10 ? 4 : NX == 11 ? 2 : NX == 12 ? 2 : NX == 13 ? 2 : 1;
-}
+constexpr int ff_epb();
 
 template <int NX, int EPB>
 constexpr size_t ff_smem_bytes()
@@ -211,23 +207,42 @@ constexpr size_t ff_smem_bytes()
     return sizeof(float2) * (4 * EPB * NX * NX * NX + 2 * NX * NX) + sizeof(float) * (2 * NX + 4 * EPB + 4) + 16;
 }
 
+// k-planes per thread.  Up to nx = 12 a thread walks its whole (i, j) column
+// (measured fastest: the per-thread set-up is amortised over nx planes); above,
+// columns are split into groups of 4 planes (3 at nx = 13) so that one element
+// spreads over up to 1024 threads.
+constexpr int ff_ppt(int nx) { return nx <= 12 ? nx : nx == 13 ? 3 : 4; }
+constexpr int ff_groups(int nx) { return (nx + ff_ppt(nx) - 1) / ff_ppt(nx); }
+constexpr int ff_threads_per_elem(int nx) { return nx * nx * ff_groups(nx); }
+
+// Default elements per CTA: at least ~128 threads per CTA, 1, 2 or 4 where possible.
+template <int NX>
+constexpr int ff_epb()
+{
+    return ff_threads_per_elem(NX) >= 128 ? 1 : ff_threads_per_elem(NX) >= 64 ? 2 : 4;
+}
+
 // CTAs per SM the register budget is set for: about 16 resident warps.
 template <int NX, int EPB>
 constexpr int ff_min_blocks()
 {
-    constexpr int warps = (NX * NX * EPB + 31) / 32;
+    constexpr int warps = (NX * NX * EPB * ff_groups(NX) + 31) / 32;
     return warps >= 16 ? 1 : (16 / warps > 4 ? 4 : 16 / warps);
 }
 
+// Thread (e, i, j, g) computes the W-wide k-groups of planes [g*PPT, g*PPT + PPT)
+// of element e.
 template <int NX, int EPB>
-__global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
+__global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ff(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
             const double* __restrict__ u, double* __restrict__ w)
 {
     using T = typename std::conditional<(NX % 2 == 0), float2, float>::type;
     using L = Lanes<T>;
     constexpr int W = L::W;
-    constexpr int N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB;
+    constexpr int PPT = ff_ppt(NX), NG = ff_groups(NX);
+    constexpr int N2 = NX * NX, N3 = NX * NX * NX, TPE = N2 * NG, NT = TPE * EPB;
+    static_assert(PPT % W == 0, "plane groups hold whole k-pairs");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* sU = reinterpret_cast<float2*>(smem_raw);  // [EPB][N3] u (hi, lo)
     float2* sWr = sU + EPB * N3;                       // [EPB][N3] wr
@@ -265,15 +280,19 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
         sCol[q] = c * 1.0001f;
     }
 
-    const int el = tid / N2;
-    const int q2 = tid - el * N2;
+    const int el = tid / TPE;
+    const int q3 = tid - el * TPE;
+    const int g = q3 / N2;
+    const int q2 = q3 - g * N2;
     const int i = q2 % NX, j = q2 / NX;
+    const int kbeg = g * PPT;
+    const int kend = kbeg + PPT < NX ? kbeg + PPT : NX;
     const bool active = el < ne;
     const float2* ue = sU + el * N3;
     {
         float m = 0.f;
         if (active)
-            for (int l = 0; l < NX; l++) m = absmax_bits(ue[i + NX * (j + NX * l)].x, m);
+            for (int k = kbeg; k < kend; k++) m = absmax_bits(ue[i + NX * (j + NX * k)].x, m);
         segmented_max_to_smem(4 * el, m, sMax);
     }
     __syncthreads();
@@ -289,7 +308,7 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
         float2* wse = sWs + el * N3;
         float2* wte = sWt + el * N3;
 #pragma unroll 1
-        for (int k0 = 0; k0 < NX; k0 += W) {
+        for (int k0 = kbeg; k0 < kend; k0 += W) {
             OffsetAcc<T> ar, as, at;
             T sig_t;
 #pragma unroll
@@ -322,19 +341,19 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
             as.finish(ush, usl);
             at.finish(uth, utl);
             // geometric factors of the W points: g[2a], g[2a+1] = hi, lo of factor a
-            T g[12];
+            T gf[12];
 #pragma unroll
             for (int q = 0; q < W; q++) {
                 const int p = i + NX * (j + NX * (k0 + q));
                 const float4 a = __ldg(Ge + 3 * p), b = __ldg(Ge + 3 * p + 1), c = __ldg(Ge + 3 * p + 2);
-                L::set(g[0], q, a.x); L::set(g[1], q, a.y); L::set(g[2], q, a.z); L::set(g[3], q, a.w);
-                L::set(g[4], q, b.x); L::set(g[5], q, b.y); L::set(g[6], q, b.z); L::set(g[7], q, b.w);
-                L::set(g[8], q, c.x); L::set(g[9], q, c.y); L::set(g[10], q, c.z); L::set(g[11], q, c.w);
+                L::set(gf[0], q, a.x); L::set(gf[1], q, a.y); L::set(gf[2], q, a.z); L::set(gf[3], q, a.w);
+                L::set(gf[4], q, b.x); L::set(gf[5], q, b.y); L::set(gf[6], q, b.z); L::set(gf[7], q, b.w);
+                L::set(gf[8], q, c.x); L::set(gf[9], q, c.y); L::set(gf[10], q, c.z); L::set(gf[11], q, c.w);
             }
             T wrh, wrl, wsh, wsl, wth, wtl;
-            df_dot3(g[0], g[1], urh, url, g[2], g[3], ush, usl, g[4], g[5], uth, utl, wrh, wrl);
-            df_dot3(g[2], g[3], urh, url, g[6], g[7], ush, usl, g[8], g[9], uth, utl, wsh, wsl);
-            df_dot3(g[4], g[5], urh, url, g[8], g[9], ush, usl, g[10], g[11], uth, utl, wth, wtl);
+            df_dot3(gf[0], gf[1], urh, url, gf[2], gf[3], ush, usl, gf[4], gf[5], uth, utl, wrh, wrl);
+            df_dot3(gf[2], gf[3], urh, url, gf[6], gf[7], ush, usl, gf[8], gf[9], uth, utl, wsh, wsl);
+            df_dot3(gf[4], gf[5], urh, url, gf[8], gf[9], ush, usl, gf[10], gf[11], uth, utl, wth, wtl);
 #pragma unroll
             for (int q = 0; q < W; q++) {
                 const int p = i + NX * (j + NX * (k0 + q));
@@ -362,7 +381,7 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
         const float bij = sCol[i] * mwr + sCol[j] * mws;
         double* we = w + (e0 + el) * (int64_t)N3;
 #pragma unroll 1
-        for (int k0 = 0; k0 < NX; k0 += W) {
+        for (int k0 = kbeg; k0 < kend; k0 += W) {
             T sig;
 #pragma unroll
             for (int q = 0; q < W; q++) L::set(sig, q, offset_for(bij + sCol[k0 + q] * mwt));
@@ -413,15 +432,15 @@ nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff,
     }
     const int64_t blocks = (nelt + EPB - 1) / EPB;
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
-    k_ax_ff<NX, EPB><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(nelt, D, reinterpret_cast<const float4*>(Gff),
-                                                                     u, w);
+    k_ax_ff<NX, EPB><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
+        nelt, D, reinterpret_cast<const float4*>(Gff), u, w);
     return check_launch();
 }
 
 template <int NX, int EPB>
 constexpr bool ff_fits()
 {
-    return NX * NX * EPB <= 1024 && ff_smem_bytes<NX, EPB>() <= 227 * 1024;
+    return ff_threads_per_elem(NX) * EPB <= 1024 && ff_smem_bytes<NX, EPB>() <= 227 * 1024;
 }
 
 template <int NX>
@@ -477,6 +496,36 @@ nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, cons
         case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s);
         case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s);
         default: return NEK_ERR_UNSUPPORTED_NX;
+    }
+}
+
+namespace {
+template <int NX>
+bool ff_fits_rt(int epb)
+{
+    return (epb == 1 && ff_fits<NX, 1>()) || (epb == 2 && ff_fits<NX, 2>()) || (epb == 4 && ff_fits<NX, 4>());
+}
+}  // namespace
+
+bool ax_ff_epb_fits(int nx, int epb)
+{
+    switch (nx) {
+        case 2: return ff_fits_rt<2>(epb);
+        case 3: return ff_fits_rt<3>(epb);
+        case 4: return ff_fits_rt<4>(epb);
+        case 5: return ff_fits_rt<5>(epb);
+        case 6: return ff_fits_rt<6>(epb);
+        case 7: return ff_fits_rt<7>(epb);
+        case 8: return ff_fits_rt<8>(epb);
+        case 9: return ff_fits_rt<9>(epb);
+        case 10: return ff_fits_rt<10>(epb);
+        case 11: return ff_fits_rt<11>(epb);
+        case 12: return ff_fits_rt<12>(epb);
+        case 13: return ff_fits_rt<13>(epb);
+        case 14: return ff_fits_rt<14>(epb);
+        case 15: return ff_fits_rt<15>(epb);
+        case 16: return ff_fits_rt<16>(epb);
+        default: return false;
     }
 }
 

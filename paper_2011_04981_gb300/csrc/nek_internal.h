@@ -32,6 +32,8 @@ void gll_host(int nx, double* xi, double* rho, double* D);
 // Elements per CTA of the AX kernels: 0 = built-in default, else the value chosen
 // by nek_tune_ax for (impl, nx).
 int tuned_epb(int impl, int nx);
+bool ax_fp64_epb_fits(int nx, int epb);
+bool ax_ff_epb_fits(int nx, int epb);
 nek_status launch_ax_fp64_epb(int epb, int64_t nelt, int nx, const double* D, const double* G, const double* u,
                               double* w, cudaStream_t s);
 nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
@@ -42,6 +44,8 @@ nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G
                           cudaStream_t s);
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                         cudaStream_t s);
+nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
+                          const float* u, float* w, cudaStream_t s);
 nek_status launch_mask(int64_t n, const uint8_t* mask, double* v, cudaStream_t s);
 nek_status launch_dssum(const nek_gs* gs, double* v, cudaStream_t s);
 

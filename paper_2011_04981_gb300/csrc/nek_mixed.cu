@@ -213,6 +213,8 @@ nek_status launch_lowp_t(int64_t nelt, int nx, const double* D, const void* Glp,
     }
 }
 
+}  // namespace
+
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
                           const float* u, float* w, cudaStream_t s)
 {
@@ -223,6 +225,8 @@ nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const
         default: return NEK_ERR_INVALID_ARG;
     }
 }
+
+namespace {
 
 // One block per element: s_G = pow2_ceil(max |G_e|); Glp = rnd(G / s_G).
 template <class S>

@@ -67,6 +67,36 @@ __device__ __forceinline__ void conv_point(const float* xin, const float* sW, co
     }
 }
 
+// Two points per thread, p and p + NP/2 (planes k and k + 4): every weight read
+// from shared memory feeds two FMAs.
+template <int CI, int CO>
+__device__ __forceinline__ void conv_2pts(const float* xin, const float* sW, const float* sb, int i, int j, int k,
+                                          float (&acc0)[CO], float (&acc1)[CO])
+{
+#pragma unroll
+    for (int o = 0; o < CO; o++) acc0[o] = acc1[o] = sb[o];
+#pragma unroll
+    for (int t = 0; t < 27; t++) {
+        const int dk = t / 9 - 1, dj = (t / 3) % 3 - 1, di = t % 3 - 1;
+        const int ii = i + di, jj = j + dj, k0 = k + dk, k1 = k + 4 + dk;
+        if (ii < 0 || ii >= NXN || jj < 0 || jj >= NXN) continue;
+        const bool v0 = k0 >= 0, v1 = k1 < NXN;  // k0 < 8 and k1 >= 0 always hold for k in [0,4)
+        const int q0 = ii + NXN * (jj + NXN * k0), q1 = ii + NXN * (jj + NXN * k1);
+#pragma unroll 4
+        for (int c = 0; c < CI; c++) {
+            const float x0 = v0 ? xin[c * NP + q0] : 0.f;
+            const float x1 = v1 ? xin[c * NP + q1] : 0.f;
+            const float* w = sW + (c * 27 + t) * CO;
+#pragma unroll
+            for (int o = 0; o < CO; o++) {
+                const float wo = w[o];
+                acc0[o] = fmaf(wo, x0, acc0[o]);
+                acc1[o] = fmaf(wo, x1, acc1[o]);
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ prep
 // xin[e][0][p] = r/rms(r), xin[e][1][p] = (minv r)/rms(minv r); scale[e] = rms(minv r).
 __global__ void __launch_bounds__(NP) k_net_prep(int64_t nelt, const double* __restrict__ r,
@@ -113,10 +143,13 @@ struct ApplySmem {
     float b1[CH], b2[CH], b3[4];
 };
 
-// z[e][p] = net(xin[e])[p] * scale[e] * c[e][p] (FP64 out).
-__global__ void __launch_bounds__(NP) k_net_apply(int64_t nelt, const float* __restrict__ theta,
-                                                  const float* __restrict__ xin, const float* __restrict__ scale,
-                                                  const double* __restrict__ c, double* __restrict__ z)
+// z[e][p] = net(xin[e])[p] * scale[e] * c[e][p] (FP64 out).  NP/2 threads per
+// element, each computing points p and p + NP/2.
+constexpr int NT_APPLY = NP / 2;
+__global__ void __launch_bounds__(NT_APPLY) k_net_apply(int64_t nelt, const float* __restrict__ theta,
+                                                        const float* __restrict__ xin,
+                                                        const float* __restrict__ scale,
+                                                        const double* __restrict__ c, double* __restrict__ z)
 {
     extern __shared__ __align__(16) unsigned char raw[];
     ApplySmem& S = *reinterpret_cast<ApplySmem*>(raw);
@@ -128,30 +161,39 @@ __global__ void __launch_bounds__(NP) k_net_apply(int64_t nelt, const float* __r
         S.b2[threadIdx.x] = bf16r(theta[OB2 + threadIdx.x]);
     }
     if (threadIdx.x == 0) S.b3[0] = bf16r(theta[OB3]);
-    const int p = threadIdx.x;
-    const int i = p % NXN, j = (p / NXN) % NXN, k = p / (NXN * NXN);
+    const int p = threadIdx.x, p1 = p + NT_APPLY;
+    const int i = p % NXN, j = (p / NXN) % NXN, k = p / (NXN * NXN);  // k in [0, 4)
     for (int64_t e = blockIdx.x; e < nelt; e += gridDim.x) {
         __syncthreads();
         S.x[p] = xin[(e * CIN + 0) * NP + p];
+        S.x[p1] = xin[(e * CIN + 0) * NP + p1];
         S.x[NP + p] = xin[(e * CIN + 1) * NP + p];
+        S.x[NP + p1] = xin[(e * CIN + 1) * NP + p1];
         __syncthreads();
         {
-            float acc[CH];
-            conv_point<CIN, CH>(S.x, S.w1, S.b1, i, j, k, acc);
+            float a0[CH], a1[CH];
+            conv_2pts<CIN, CH>(S.x, S.w1, S.b1, i, j, k, a0, a1);
 #pragma unroll
-            for (int o = 0; o < CH; o++) S.a1[o * NP + p] = gelu(acc[o]);
+            for (int o = 0; o < CH; o++) {
+                S.a1[o * NP + p] = gelu(a0[o]);
+                S.a1[o * NP + p1] = gelu(a1[o]);
+            }
         }
         __syncthreads();
         {
-            float acc[CH];
-            conv_point<CH, CH>(S.a1, S.w2, S.b2, i, j, k, acc);
+            float a0[CH], a1[CH];
+            conv_2pts<CH, CH>(S.a1, S.w2, S.b2, i, j, k, a0, a1);
 #pragma unroll
-            for (int o = 0; o < CH; o++) S.a2[o * NP + p] = gelu(acc[o]);
+            for (int o = 0; o < CH; o++) {
+                S.a2[o * NP + p] = gelu(a0[o]);
+                S.a2[o * NP + p1] = gelu(a1[o]);
+            }
         }
         __syncthreads();
-        float y[1];
-        conv_point<CH, 1>(S.a2, S.w3, S.b3, i, j, k, y);
-        z[e * NP + p] = (double)y[0] * (double)scale[e] * c[e * NP + p];
+        float y0[1], y1[1];
+        conv_2pts<CH, 1>(S.a2, S.w3, S.b3, i, j, k, y0, y1);
+        z[e * NP + p] = (double)y0[0] * (double)scale[e] * c[e * NP + p];
+        z[e * NP + p1] = (double)y1[0] * (double)scale[e] * c[e * NP + p1];
     }
 }
 
@@ -232,6 +274,45 @@ __global__ void __launch_bounds__(NP) k_net_loss(int B, const float* __restrict_
         __syncthreads();
         den = den > 0.f ? den : 1.f;
         dy[(int64_t)b * NP + p] = 2.f / (float)B * d / den;
+        if (p == 0) loss_b[b] = num / den;
+    }
+}
+
+// d = y - t (FP32, in place into d)
+__global__ void k_net_diff(int64_t n, const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ d)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        d[q] = y[q] - t[q];
+}
+
+// Per sample: loss_b = d.Ad / t.At ; dy = (2/B) Ad / t.At  (A = the sample element's operator).
+__global__ void __launch_bounds__(NP) k_net_energy_loss(int B, const float* __restrict__ d, const float* __restrict__ Ad,
+                                                        const float* __restrict__ t, const float* __restrict__ At,
+                                                        float* __restrict__ dy, float* __restrict__ loss_b)
+{
+    __shared__ float sh[2][NP / 32];
+    const int p = threadIdx.x;
+    for (int b = blockIdx.x; b < B; b += gridDim.x) {
+        const int64_t o = (int64_t)b * NP + p;
+        float a = d[o] * Ad[o], c = t[o] * At[o];
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, s);
+            c += __shfl_xor_sync(0xffffffffu, c, s);
+        }
+        if ((p & 31) == 0) {
+            sh[0][p >> 5] = a;
+            sh[1][p >> 5] = c;
+        }
+        __syncthreads();
+        float num = 0.f, den = 0.f;
+        for (int q = 0; q < NP / 32; q++) {
+            num += sh[0][q];
+            den += sh[1][q];
+        }
+        __syncthreads();
+        den = den > 0.f ? den : 1.f;
+        dy[o] = 2.f / (float)B * Ad[o] / den;
         if (p == 0) loss_b[b] = num / den;
     }
 }
@@ -447,7 +528,8 @@ nek_status launch_net_apply(int64_t nelt, const float* theta, const float* xin, 
         if (st != NEK_OK) return st;
         conf = true;
     }
-    k_net_apply<<<grid_for(nelt), NP, sizeof(ApplySmem), s>>>(nelt, theta, xin, scale, c, z);
+    k_net_apply<<<static_cast<int>(nelt < 152 * 2 ? nelt : 152 * 2), NT_APPLY, sizeof(ApplySmem), s>>>(nelt, theta,
+                                                                                                  xin, scale, c, z);
     return check_launch();
 }
 
@@ -467,7 +549,7 @@ namespace {
 inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct TrainLayout {
-    float *h1, *h2, *y, *dy, *lossb, *gs;
+    float *h1, *h2, *y, *dy, *lossb, *gs, *d, *Ad, *At;
     size_t bytes;
 };
 
@@ -486,6 +568,9 @@ TrainLayout train_layout(char* base, int B)
     L.dy = take(sizeof(float) * (size_t)B * NP);
     L.lossb = take(sizeof(float) * (size_t)B);
     L.gs = take(sizeof(float) * (size_t)B * NPARAM);
+    L.d = take(sizeof(float) * (size_t)B * NP);
+    L.Ad = take(sizeof(float) * (size_t)B * NP);
+    L.At = take(sizeof(float) * (size_t)B * NP);
     L.bytes = off;
     return L;
 }
@@ -550,6 +635,35 @@ nek_status nek_net_train_grad(int batch, const float* theta, const float* xin, c
     }
     k_net_fwd_train<<<grid_for(batch), NP, sizeof(ApplySmem), s>>>(batch, theta, xin, L.h1, L.h2, L.y);
     k_net_loss<<<grid_for(batch), NP, 0, s>>>(batch, L.y, target, L.dy, L.lossb);
+    k_net_bwd<<<grid_for(batch), NP, sizeof(BwdSmem), s>>>(batch, theta, xin, L.h1, L.h2, L.dy, L.gs);
+    k_net_reduce<<<(NPARAM + 255) / 256, 256, 0, s>>>(batch, L.gs, L.lossb, grad, loss);
+    return check_launch();
+}
+
+nek_status nek_net_train_grad_energy(int batch, const float* theta, const float* xin, const float* target,
+                                     const double* D, const float* Glp32, const float* gscale, float* grad,
+                                     float* loss, void* workspace, void* stream)
+{
+    if (batch <= 0 || !theta || !xin || !target || !D || !Glp32 || !gscale || !grad || !workspace ||
+        !is_aligned(workspace, 256))
+        return NEK_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    TrainLayout L = train_layout(static_cast<char*>(workspace), batch);
+    static bool conf = false;
+    if (!conf) {
+        nek_status st = set_smem(k_net_fwd_train, sizeof(ApplySmem));
+        if (st == NEK_OK) st = set_smem(k_net_bwd, sizeof(BwdSmem));
+        if (st != NEK_OK) return st;
+        conf = true;
+    }
+    const int64_t n = (int64_t)batch * NP;
+    k_net_fwd_train<<<grid_for(batch), NP, sizeof(ApplySmem), s>>>(batch, theta, xin, L.h1, L.h2, L.y);
+    k_net_diff<<<pcg::stream_blocks(n), 256, 0, s>>>(n, L.y, target, L.d);
+    nek_status st = check_launch();
+    if (st != NEK_OK) return st;
+    if ((st = launch_ax_lowp(NEK_PREC_F32, batch, NXN, D, Glp32, gscale, L.d, L.Ad, s)) != NEK_OK) return st;
+    if ((st = launch_ax_lowp(NEK_PREC_F32, batch, NXN, D, Glp32, gscale, target, L.At, s)) != NEK_OK) return st;
+    k_net_energy_loss<<<grid_for(batch), NP, 0, s>>>(batch, L.d, L.Ad, target, L.At, L.dy, L.lossb);
     k_net_bwd<<<grid_for(batch), NP, sizeof(BwdSmem), s>>>(batch, theta, xin, L.h1, L.h2, L.dy, L.gs);
     k_net_reduce<<<(NPARAM + 255) / 256, 256, 0, s>>>(batch, L.gs, L.lossb, grad, loss);
     return check_launch();

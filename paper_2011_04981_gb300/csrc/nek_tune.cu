@@ -32,7 +32,8 @@ nek_status nek_set_ax_epb(int impl, int nx, int epb)
 {
     if (impl != NEK_AX_FP64 && impl != NEK_AX_FF) return NEK_ERR_INVALID_ARG;
     if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
-    if (epb != 0 && epb != 1 && epb != 2 && epb != 4) return NEK_ERR_INVALID_ARG;
+    if (epb != 0 && !(impl == NEK_AX_FF ? ax_ff_epb_fits(nx, epb) : ax_fp64_epb_fits(nx, epb)))
+        return NEK_ERR_INVALID_ARG;  // not one of the compiled counts, or too many threads / too much smem
     g_epb[impl][nx].store(epb, std::memory_order_relaxed);
     return NEK_OK;
 }

@@ -10,8 +10,9 @@ for each training mesh the solution x* is computed to a relative residual of
 iterations for a few k; with x_k, r_k = mask(b - dssum(AX x_k)) and the error
 e_k = x* - x_k, every sampled element contributes the network input
 (r_k, Minv r_k normalised by their element RMS) and the target
-e_k / multiplicity / rms(Minv r_k).  Training minimises the relative squared
-error per sample with Adam.
+e_k / rms(Minv r_k) (the preconditioner multiplies the network output back by
+rms(Minv r_k) and by 1/multiplicity before summing over elements).  Training
+minimises the per-sample relative error in the element energy norm with Adam.
 """
 from __future__ import annotations
 
@@ -40,23 +41,36 @@ def _residual(P, f, x, w):
     nekax.mask(P.npts, P.mask, w)
 
 
+class TrainingSet:
+    """Network inputs, targets and each sample's element operator (FP32 G with its scale)."""
+
+    def __init__(self, xin, target, Glp, gscale, D):
+        self.xin, self.target, self.Glp, self.gscale, self.D = xin, target, Glp, gscale, D
+
+    def __len__(self):
+        return self.xin.shape[0]
+
+
 def make_training_data(n_meshes=200, pairs_per_mesh=100, snapshots=5, e=8, seed=0, device="cuda"):
-    """Returns (xin [N,2,512] float32, target [N,512] float32) on the device."""
+    """Returns a TrainingSet on the device: xin [N,2,512], target [N,512], Glp [N,512,6] (FP32), gscale [N]."""
     import torch
 
     rng = np.random.default_rng(seed)
-    X, T = [], []
+    X, T, GL, GS = [], [], [], []
+    D = None
     for m in range(n_meshes):
         mesh = mesh_family(10_000 + seed * 1000 + m, e)
         P = DeviceProblem(mesh, device)
         P.prepare_ff()
+        D = P.D
+        Glp = torch.empty((mesh.nelt, 512, 6), dtype=torch.float32, device=device)
+        gsc = torch.empty(mesh.nelt, dtype=torch.float32, device=device)
+        nekax.geom_lowp(mesh.nelt, NX, nekax.PREC_F32, P.G, Glp, gsc)
         f = torch.from_numpy(inputs.random_global_field(mesh, seed=m)).to(device)
         xs = torch.empty_like(f)
         res = P.cg(f, xs, tol=1e-13, max_iter=20000, ax_impl=nekax.AX_FF, check_every=10)
         n_it = max(2, res["iters"])
         ks = np.unique(np.sort(np.exp(rng.uniform(0.0, math.log(0.8 * n_it), size=snapshots)).astype(int) + 1))
-        c = torch.empty_like(f)
-        P.gs.inv_multiplicity(c)
         xk = torch.empty_like(f)
         r = torch.empty_like(f)
         xin = torch.empty((mesh.nelt, 2, 512), dtype=torch.float32, device=device)
@@ -66,14 +80,16 @@ def make_training_data(n_meshes=200, pairs_per_mesh=100, snapshots=5, e=8, seed=
             P.cg(f, xk, tol=0.0, max_iter=int(k), ax_impl=nekax.AX_FF)
             _residual(P, f, xk, r)
             nekax.net_prep(mesh.nelt, NX, r, P.minv, xin, sc)
-            err = (xs - xk) * c
+            err = xs - xk  # nek_net_apply weights each element's output by 1/multiplicity
             good = torch.nonzero(sc > 0).flatten()
             sel = good[torch.from_numpy(rng.choice(good.numel(), size=min(per, good.numel()), replace=False)).to(
                 device)]
             X.append(xin[sel].clone())
             T.append((err[sel] / sc[sel, None].double()).float())
+            GL.append(Glp[sel].clone())
+            GS.append(gsc[sel].clone())
         del P
-    return torch.cat(X), torch.cat(T)
+    return TrainingSet(torch.cat(X), torch.cat(T), torch.cat(GL), torch.cat(GS), D)
 
 
 def init_params(seed=0, device="cuda"):
@@ -90,12 +106,23 @@ def init_params(seed=0, device="cuda"):
     return torch.from_numpy(th).to(device)
 
 
-def train(xin, target, epochs=20, batch=256, lr=2e-3, seed=0, log=None):
-    """Adam on the relative squared error; returns (theta, per-epoch mean loss)."""
+def _grad(data, idx, batch, theta, g, loss, ws, kind):
+    xb = data.xin[idx].contiguous()
+    tb = data.target[idx].contiguous()
+    if kind == "energy":
+        nekax.net_train_grad_energy(batch, theta, xb, tb, data.D, data.Glp[idx].contiguous(),
+                                    data.gscale[idx].contiguous(), g, loss, ws)
+    else:
+        nekax.net_train_grad(batch, theta, xb, tb, g, loss, ws)
+
+
+def train(data, epochs=20, batch=256, lr=2e-3, seed=0, kind="energy", log=None):
+    """Adam on the per-sample relative error (element energy norm, or plain squared
+    error with kind="l2"); returns (theta, per-epoch mean loss)."""
     import torch
 
-    dev = xin.device
-    n = xin.shape[0]
+    dev = data.xin.device
+    n = len(data)
     theta = init_params(seed, dev)
     npar = theta.numel()
     m = torch.zeros_like(theta)
@@ -112,9 +139,7 @@ def train(xin, target, epochs=20, batch=256, lr=2e-3, seed=0, log=None):
         tot, cnt = 0.0, 0
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
-            xb = xin[idx].contiguous()
-            tb = target[idx].contiguous()
-            nekax.net_train_grad(batch, theta, xb, tb, g, loss, ws)
+            _grad(data, idx, batch, theta, g, loss, ws, kind)
             step += 1
             nekax.adam_step(npar, theta, g, m, v, lr * (0.5 ** (ep / max(1, epochs / 3))), step)
             tot += float(loss.item())
@@ -125,22 +150,23 @@ def train(xin, target, epochs=20, batch=256, lr=2e-3, seed=0, log=None):
     return theta, hist
 
 
-def validation_loss(theta, xin, target, batch=256):
+def validation_loss(theta, data, batch=256, kind="energy"):
     import torch
 
-    ws = torch.empty(nekax.net_train_workspace_bytes(batch) // 4 + 64, dtype=torch.float32, device=xin.device)
+    dev = data.xin.device
+    ws = torch.empty(nekax.net_train_workspace_bytes(batch) // 4 + 64, dtype=torch.float32, device=dev)
     g = torch.empty_like(theta)
-    loss = torch.zeros(1, dtype=torch.float32, device=xin.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
     tot, cnt = 0.0, 0
-    for b0 in range(0, xin.shape[0] - batch + 1, batch):
-        nekax.net_train_grad(batch, theta, xin[b0:b0 + batch].contiguous(), target[b0:b0 + batch].contiguous(), g,
-                             loss, ws)
+    for b0 in range(0, len(data) - batch + 1, batch):
+        idx = torch.arange(b0, b0 + batch, device=dev)
+        _grad(data, idx, batch, theta, g, loss, ws, kind)
         tot += float(loss.item())
         cnt += 1
     return tot / max(cnt, 1)
 
 
-def compare_on_mesh(theta, mesh, seed=0, tol=1e-8, device="cuda", stag_window=50, stag_factor=0.1):
+def compare_on_mesh(theta, mesh, seed=0, tol=1e-8, device="cuda", stag_window=100, stag_factor=0.5):
     """Time and iterations to tol: Jacobi-PCG versus flexible CG with the network."""
     import torch
 

@@ -109,6 +109,7 @@ _SIGS = {
     "nek_net_train_workspace_bytes": ([_I], ctypes.c_size_t),
     "nek_net_forward_batch": ([_I, _P, _P, _P, _P, _P], _I),
     "nek_net_train_grad": ([_I, _P, _P, _P, _P, _P, _P, _P], _I),
+    "nek_net_train_grad_energy": ([_I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "nek_adam_step": ([_I, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _I, _P],
                       _I),
     "nek_fcg_workspace_bytes": ([_I64, _I, _I], ctypes.c_size_t),
@@ -402,13 +403,19 @@ def net_train_grad(batch, theta, xin, target, grad, loss, workspace, stream=None
                                                            _ptr(loss), _ptr(workspace), _stream(stream)))
 
 
+def net_train_grad_energy(batch, theta, xin, target, D, Glp32, gscale, grad, loss, workspace, stream=None):
+    _check("nek_net_train_grad_energy", load().nek_net_train_grad_energy(
+        batch, _ptr(theta), _ptr(xin), _ptr(target), _ptr(D), _ptr(Glp32), _ptr(gscale), _ptr(grad), _ptr(loss),
+        _ptr(workspace), _stream(stream)))
+
+
 def adam_step(n, theta, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     _check("nek_adam_step", load().nek_adam_step(n, _ptr(theta), _ptr(grad), _ptr(m), _ptr(v), float(lr),
                                                  float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
 
 
-def fcg_solve(gs, nelt, nx, D, G, Gff, m, minv, theta, f, x, tol=1e-8, max_iter=5000, stag_window=50,
-              stag_factor=0.1, workspace=None, stream=None):
+def fcg_solve(gs, nelt, nx, D, G, Gff, m, minv, theta, f, x, tol=1e-8, max_iter=5000, stag_window=100,
+              stag_factor=0.5, workspace=None, stream=None):
     info = NekFcgInfo()
     st = load().nek_fcg_solve(gs.handle, nelt, nx, _ptr(D), _ptr(G), _ptr(Gff), _ptr(m), _ptr(minv), _ptr(theta),
                               _ptr(f), _ptr(x), float(tol), int(max_iter), int(stag_window), float(stag_factor),

@@ -132,6 +132,7 @@ def test_tuning_and_lowp_entry_points_reject_bad_arguments(lib):
     assert L.nek_set_ax_epb(7, 8, 1) == nekax.ERR_INVALID_ARG
     assert L.nek_set_ax_epb(0, 1, 1) == nekax.ERR_UNSUPPORTED_NX
     assert L.nek_set_ax_epb(0, 8, 3) == nekax.ERR_INVALID_ARG
+    assert L.nek_set_ax_epb(1, 16, 4) == nekax.ERR_INVALID_ARG  # 4 x 1024 threads does not fit
     assert L.nek_set_ax_epb(1, 8, 2) == nekax.OK and L.nek_get_ax_epb(1, 8) == 2
     assert L.nek_set_ax_epb(1, 8, 0) == nekax.OK and L.nek_get_ax_epb(1, 8) == 0
     assert L.nek_tune_ax(0, 0, 8, A16, A16, A16, A16 * 2, None, None, None) == nekax.ERR_INVALID_ARG

@@ -134,3 +134,57 @@ def test_fcg_jacobi_mode_and_random_net():
     assert r1["status"] == nekax.OK, r1
     assert r1["net_applications"] >= 1
     assert Pr.residual(f, x2.cpu().numpy()) <= 1e-8 * 1.001
+
+
+def test_energy_gradient_matches_oracle():
+    B = 3
+    mesh = inputs.box_mesh(3, 1, 1, 8, perturb=0.2, seed=6)
+    P = DeviceProblem(mesh, DEV, build_minv=False)
+    Glp = torch.empty((mesh.nelt, 512, 6), dtype=torch.float32, device=DEV)
+    gsc = torch.empty(mesh.nelt, dtype=torch.float32, device=DEV)
+    nekax.geom_lowp(mesh.nelt, 8, nekax.PREC_F32, P.G, Glp, gsc)
+    rng = np.random.default_rng(8)
+    th = _theta(12)
+    x = rng.normal(size=(B, 2, 8, 8, 8)).astype(np.float32).astype(np.float64)
+    t = rng.normal(size=(B, 8, 8, 8)).astype(np.float32).astype(np.float64)
+    ws = torch.empty(nekax.net_train_workspace_bytes(B) // 4 + 64, dtype=torch.float32, device=DEV)
+    g = torch.empty(onet.NPARAM, dtype=torch.float32, device=DEV)
+    loss = torch.empty(1, dtype=torch.float32, device=DEV)
+    nekax.net_train_grad_energy(B, torch.from_numpy(th.astype(np.float32)).to(DEV),
+                                torch.from_numpy(x.astype(np.float32)).to(DEV),
+                                torch.from_numpy(t.reshape(B, 512).astype(np.float32)).to(DEV), P.D, Glp, gsc, g,
+                                loss, ws)
+    torch.cuda.synchronize()
+    D32 = P.D_host.astype(np.float32).astype(np.float64)
+    G = Glp.cpu().numpy().astype(np.float64) * gsc.cpu().numpy().astype(np.float64)[:, None, None]
+    A = np.stack([ref.element_matrix(D32, G[e]) for e in range(B)])
+    L, gr, _ = onet.energy_loss_and_grad(th, x, t, A)
+    assert abs(float(loss.item()) - L) <= 1e-4 * L
+    gg = g.cpu().numpy().astype(np.float64)
+    o = 0
+    for name, shp in onet.SHAPES:
+        n = int(np.prod(shp))
+        if name != "b3":  # constants are in the kernel of A: d loss / d b3 is zero up to rounding
+            assert _rel(gg[o:o + n], gr[o:o + n]) <= 2e-3, name
+        o += n
+
+
+def test_training_reduces_loss_and_learned_fcg_converges():
+    """Small-scale version of the learned-preconditioner experiment: pairs from the
+    solver, GPU training with the library's kernels, flexible CG on a held-out mesh.
+    The network must lower the validation loss; the comparison with Jacobi-PCG is
+    reported (the full-size numbers are in the benchmark's learned block)."""
+    from paper_2011_04981_gb300 import learned
+
+    data = learned.make_training_data(n_meshes=8, pairs_per_mesh=64, e=4, seed=0)
+    val = learned.make_training_data(n_meshes=2, pairs_per_mesh=64, e=4, seed=1)
+    assert len(data) >= 400
+    theta, hist = learned.train(data, epochs=15, batch=64, lr=3e-3, seed=0)
+    assert hist[-1] < hist[0]
+    v_trained = learned.validation_loss(theta, val, batch=64)
+    v_init = learned.validation_loss(learned.init_params(0, DEV), val, batch=64)
+    assert v_trained < v_init, (v_trained, v_init)
+    out = learned.compare_on_mesh(theta, learned.mesh_family(seed=5, e=6), seed=2)
+    assert out["jacobi_pcg"]["relres"] <= 1e-8 and out["learned_fcg"]["relres"] <= 1e-8
+    print("learned FCG %d iterations (fallback at %d) vs Jacobi-PCG %d" % (
+        out["learned_fcg"]["iters"], out["learned_fcg"]["fell_back_at"], out["jacobi_pcg"]["iters"]))

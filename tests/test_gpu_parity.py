@@ -357,11 +357,13 @@ def test_epb_variants_bit_identical_and_tuner(impl, nx):
     outs = []
     try:
         for epb in (1, 2, 4):
-            nekax.set_ax_epb(impl, nx, epb)
+            if nekax.load().nek_set_ax_epb(int(impl), nx, epb) != nekax.OK:
+                continue  # this element count does not fit the kernel at this nx
             w = torch.full_like(u, float("nan"))
             (P.ax_ff if impl == nekax.AX_FF else P.ax)(u, w)
             outs.append(w)
         torch.cuda.synchronize()
+        assert len(outs) >= 2
         for w in outs[1:]:
             assert torch.equal(w, outs[0])
         epb, ms = nekax.tune_ax(impl, mesh.nelt, nx, P.D, Gx, u, outs[0])

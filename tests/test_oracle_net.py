@@ -102,3 +102,34 @@ def test_element_inputs_normalisation():
     for e in (0, 2, 3):
         assert abs(np.sqrt(np.mean(x[e, 0] ** 2)) - 1.0) < 1e-14
         assert abs(np.sqrt(np.mean(x[e, 1] ** 2)) - 1.0) < 1e-14
+
+
+def test_energy_loss_gradient_by_central_differences():
+    from oracle import ref
+    from paper_2011_04981_gb300 import inputs
+
+    n = 3
+    rng = np.random.default_rng(9)
+    mesh = inputs.box_mesh(2, 1, 1, n, perturb=0.2, seed=2)
+    xi, rho, D = ref.gll(n)
+    G = ref.geom(mesh.corners, n, xi, rho)
+    A = np.stack([ref.element_matrix(D, G[e]) for e in range(2)])
+    theta = rng.normal(scale=0.3, size=net.NPARAM)
+    x = rng.normal(size=(2, net.CIN, n, n, n))
+    t = rng.normal(size=(2, n, n, n))
+    L, g, dx = net.energy_loss_and_grad(theta, x, t, A)
+    assert abs(L - net.energy_loss(theta, x, t, A)) <= 1e-12 * L
+    # constants are in the kernel of every element matrix: adding one to y changes nothing
+    P = net.unpack(theta)
+    P["b3"] = P["b3"] + 0.7
+    assert abs(net.energy_loss(net.pack(P), x, t, A) - L) <= 1e-10 * L
+    h = 1e-6
+    o = 0
+    for name, shp in net.SHAPES:
+        size = int(np.prod(shp))
+        for idx in rng.choice(size, size=min(size, 5), replace=False):
+            e = np.zeros(net.NPARAM)
+            e[o + idx] = h
+            fd = (net.energy_loss(theta + e, x, t, A) - net.energy_loss(theta - e, x, t, A)) / (2 * h)
+            assert abs(fd - g[o + idx]) <= 1e-6 * max(1.0, abs(fd)), (name, idx)
+        o += size
