@@ -54,8 +54,9 @@ def parse():
                     help="also train the element network and compare flexible CG with it against Jacobi-PCG")
     ap.add_argument("--learned-meshes", type=int, default=200)
     ap.add_argument("--learned-epochs", type=int, default=30)
-    ap.add_argument("--tune", action="store_true", help="pick elements-per-CTA with nek_tune_ax before timing")
-    ap.add_argument("--ax", default="fp64", choices=["fp64", "ff"],
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the elements-per-CTA tuning (nek_tune_ax) before timing")
+    ap.add_argument("--ax", default="ff", choices=["fp64", "ff"],
                     help="AX operator inside the solve: native FP64 or FP64-accurate float-float")
     return ap.parse_args()
 
@@ -128,17 +129,20 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-def kernel_source_sha():
-    with open(os.path.join(ROOT, "paper_2011_04981_gb300", "csrc", "nek_ax.cu"), "rb") as fh:
+AX_SOURCES = {"fp64": ("nek_ax.cu", "ax_fp64_traffic.json"), "ff": ("nek_ax_ff.cu", "ax_ff_traffic.json")}
+
+
+def kernel_source_sha(which="fp64"):
+    with open(os.path.join(ROOT, "paper_2011_04981_gb300", "csrc", AX_SOURCES[which][0]), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def traffic_from_profile(nx, nelt):
+def traffic_from_profile(nx, nelt, which="fp64"):
     """DRAM bytes per AX launch from the committed ncu summary, if it matches this kernel source."""
     try:
-        with open(os.path.join(ROOT, "profiles", "ax_fp64_traffic.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", AX_SOURCES[which][1])) as fh:
             t = json.load(fh)
-        if t.get("source_sha") != kernel_source_sha() or int(t["nx"]) != nx:
+        if t.get("source_sha") != kernel_source_sha(which) or int(t["nx"]) != nx:
             return None
         return float(t["dram_bytes_per_element"]) * nelt
     except Exception:
@@ -421,13 +425,16 @@ def run_native(args):
     ax_gdofs = pts / ax_t / 1e9
     flops = perfmodel.ax_flops_per_point(nx) * pts
     hbm, hbm_kind = peaks()
-    traffic = traffic_from_profile(nx, mesh.nelt)
+    traffic = traffic_from_profile(nx, mesh.nelt, args.ax)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.ax == "fp64" else "f64 (AX in f32-pair float-float)",
+        "data": "synthetic",
         "config": {"workload": "Jacobi-PCG, %d PCG iterations per step (AX+dssum+mask+dots+updates), "
-                               "%dx%dx%d deformed box (perturbation 0.1 h), nx=%d, FP64" % (iters, e, e, e, nx),
+                               "%dx%dx%d deformed box (perturbation 0.1 h), nx=%d, FP64-accurate, AX %s"
+                               % (iters, e, e, e, nx, "native FP64 (nek_ax)" if args.ax == "fp64" else
+                                  "float-float on the FP32 pipes (nek_ax_ff)"),
                    "elements": mesh.nelt, "nx": nx, "points": pts, "iters_per_step": iters,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (G alone %.2f GB), no flush" % (pts * 48 / 1e9)},
@@ -436,11 +443,16 @@ def run_native(args):
         "ax": {"gdofs": ax_gdofs, "ms_per_launch": ax_t * 1e3, "gflops": flops / ax_t / 1e9,
                "hbm_gbs": 64 * pts / ax_t / 1e9, "hbm_frac": 64 * pts / ax_t / 1e9 / hbm, "launches": ax_n,
                "share_of_step": ax_ms / 1e3 / t_dev},
-        "roofline": {"bound": "alu", "achieved": flops / ax_t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flops / ax_t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "k_ax_fp64<%d>" % nx,
-                     "note": "FP64 DFMA-pipe bound; peak = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz; HBM %s peak %.0f GB/s"
-                             % (hbm_kind, hbm)},
+        "roofline": ({"bound": "alu", "achieved": flops / ax_t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                      "frac": flops / ax_t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic,
+                      "kernel": "k_ax_fp64<%d>" % nx,
+                      "note": "native FP64: DFMA-pipe bound; peak = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal "
+                              "1.25 TFLOP/s); HBM %s peak %.0f GB/s" % (hbm_kind, hbm)}
+                     if args.ax == "fp64" else
+                     {"bound": "hbm", "achieved": 64 * pts / ax_t / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": 64 * pts / ax_t / 1e9 / hbm, "traffic": traffic, "kernel": ("k_ax_ffe<%d>" if nx in (10, 12) else "k_ax_ff<%d>") % nx,
+                      "note": "FP64-accurate float-float AX, 64 algorithmic B/point (u 8 + G 48 + w 8); peak = %s "
+                              "HBM copy; its instruction limit is the FP32 pipe (see profiles)" % hbm_kind}),
         "clocks": clk,
     }
     if args.sweep and rank == 0:
