@@ -54,6 +54,8 @@ def parse():
                     help="also train the element network and compare flexible CG with it against Jacobi-PCG")
     ap.add_argument("--learned-meshes", type=int, default=200)
     ap.add_argument("--learned-epochs", type=int, default=30)
+    ap.add_argument("--lvec", action="store_true",
+                    help="also time the unique-node (L-vector) solve against the E-vector solve")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the elements-per-CTA tuning (nek_tune_ax) before timing")
     ap.add_argument("--ax", default="ff", choices=["fp64", "ff"],
@@ -241,6 +243,48 @@ def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10, tune=False):
         out[str(nx)] = res
         del P, u, w
         torch.cuda.empty_cache()
+    return out
+
+
+def lvec_block(torch, P, iters, reps=3):
+    """Unique-node (L-vector) Jacobi-PCG against the E-vector solve on the bench mesh, same operator
+    (nek_ax_ff): fixed-iteration rate in E-points x iterations / s, and time to 1e-8."""
+    import numpy as np
+
+    from paper_2011_04981_gb300 import nekax
+
+    lv, minvL, _ = P.lvec()
+    gL = torch.from_numpy(np.random.default_rng(2).uniform(-1.0, 1.0, lv.size)).to("cuda")
+    fE = torch.empty(P.npts, dtype=torch.float64, device="cuda")
+    lv.scatter(gL, fE)
+    xL = torch.empty_like(gL)
+    xE = torch.empty_like(fE)
+    s = torch.cuda.current_stream()
+    out = {"unique_nodes": lv.size, "element_points": P.npts, "unique_fraction": lv.size / P.npts}
+    for name, run in (("evec", lambda it, tol: P.cg(fE, xE, tol=tol, max_iter=it, ax_impl=nekax.AX_FF,
+                                                    check_every=20 if tol > 0 else 1)),
+                      ("lvec", lambda it, tol: P.cg_lvec(gL, xL, tol=tol, max_iter=it,
+                                                         check_every=20 if tol > 0 else 1))):
+        run(iters, 0.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            r = run(iters, 0.0)
+        e1.record(s)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r8 = run(20000, 1e-8)
+        torch.cuda.synchronize()
+        out[name] = {"gdofs_element_points": P.npts * iters / t / 1e9, "ms_per_iteration": 1e3 * t / iters,
+                     "to_1e-8": {"seconds": time.perf_counter() - t0, "iters": r8["iters"], "relres": r8["relres"],
+                                 "status": nekax.status_string(r8["status"])}}
+    xLE = torch.empty_like(fE)
+    lv.scatter(xL, xLE)
+    out["max_rel_diff_x"] = float((xLE - xE).abs().max() / xE.abs().max())
+    out["speedup"] = out["evec"]["ms_per_iteration"] / out["lvec"]["ms_per_iteration"]
     return out
 
 
@@ -468,6 +512,8 @@ def run_native(args):
         line["learned"] = learned_block(torch, args.learned_meshes, args.learned_epochs)
     if args.mixed and rank == 0:
         line["mixed"] = mixed_block(torch, P, f, x)
+    if args.lvec and rank == 0:
+        line["lvec"] = lvec_block(torch, P, iters)
     if args.batch and rank == 0:
         del ws
         line["batch"] = batch_block(torch, args.batch)

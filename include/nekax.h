@@ -418,6 +418,50 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
                            int max_iter, void* workspace, int* iters_out, double* relres_out, nek_cg_opts* opts,
                            void* stream);
 
+/* ------------------------------------------------- unique-node vectors ---
+ * The solve on unique-node ("L-") vectors: every global node is stored once,
+ * ordered by ascending global id.  With Q the map from unique nodes to element
+ * points (u_local[p] = u[l2g[p]]), the assembled operator of Section II-B's
+ * AX plus nearest-neighbour exchange is w = Q^T AX Q u: AX gathers its input
+ * through l2g (inside the kernel), and the copies of each node are summed in
+ * ascending local index, the order of nek_dssum.  CG vectors then have the
+ * unique length and inner products need no 1/multiplicity weight.
+ *
+ * nek_lvec_create: glo_num [npts] (host, >= 0) and mask [npts] (host; copies
+ *   of a node must agree, else NEK_ERR_INVALID_ARG).  npts < 2^31
+ *   (NEK_ERR_TOO_LARGE).  The plan owns its device arrays; free it with
+ *   nek_lvec_destroy.  nek_lvec_size: unique nodes (-1 for NULL).
+ * nek_lvec_scatter: uE = Q uL.  nek_lvec_restrict: uL[g] = uE at the first
+ *   copy of g (the inverse of scatter on consistent E-vectors).
+ *   nek_lvec_assemble: wL = Q^T wE.  All device, asynchronous, no aliasing.
+ * nek_lvec_ax_ff: wL = Q^T AX Q uL with the FP64-accurate operator of
+ *   nek_ax_ff (Gff from nek_geom_ff), unmasked; wE is caller-provided device
+ *   scratch of npts doubles.
+ * nek_lvec_jacobi_minv: minvL = 1 / diag(Q^T A Q), 0 on Dirichlet nodes;
+ *   scratchE: npts doubles.
+ * nek_lvec_cg_solve: Jacobi-PCG of nek_cg_solve on L-vectors (fL, xL, minvL
+ *   of nek_lvec_size entries), AX as in nek_lvec_ax_ff.  opts (nullable):
+ *   check_every, time_ax and the outputs; ax_impl and Gff in opts are ignored.
+ *   workspace: >= nek_lvec_cg_workspace_bytes(lv) bytes, 256-aligned, or NULL.
+ *   Same stopping rules, statuses and synchronisation as nek_cg_solve.
+ */
+typedef struct nek_lvec nek_lvec;
+
+nek_status nek_lvec_create(int64_t npts, const int64_t* glo_num, const uint8_t* mask, nek_lvec** out);
+nek_status nek_lvec_destroy(nek_lvec* lv);
+int64_t nek_lvec_size(const nek_lvec* lv);
+nek_status nek_lvec_scatter(const nek_lvec* lv, const double* uL, double* uE, void* stream);
+nek_status nek_lvec_restrict(const nek_lvec* lv, const double* uE, double* uL, void* stream);
+nek_status nek_lvec_assemble(const nek_lvec* lv, const double* wE, double* wL, void* stream);
+nek_status nek_lvec_ax_ff(const nek_lvec* lv, int64_t nelt, int nx, const double* D, const float* Gff,
+                          const double* uL, double* wL, double* wE, void* stream);
+nek_status nek_lvec_jacobi_minv(const nek_lvec* lv, int64_t nelt, int nx, const double* D, const double* G,
+                                double* minvL, double* scratchE, void* stream);
+size_t nek_lvec_cg_workspace_bytes(const nek_lvec* lv);
+nek_status nek_lvec_cg_solve(const nek_lvec* lv, int64_t nelt, int nx, const double* D, const float* Gff,
+                             const double* minvL, const double* fL, double* xL, double tol_rel, int max_iter,
+                             void* workspace, int* iters_out, double* relres_out, nek_cg_opts* opts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

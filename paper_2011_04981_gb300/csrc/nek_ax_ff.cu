@@ -235,7 +235,7 @@ constexpr int ff_min_blocks()
 template <int NX, int EPB>
 __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ff(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
-            const double* __restrict__ u, double* __restrict__ w)
+            const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g)
 {
     using T = typename std::conditional<(NX % 2 == 0), float2, float>::type;
     using L = Lanes<T>;
@@ -264,7 +264,10 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
         sDT[(q % NX) * NX + q / NX] = d;
     }
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
-    {
+    if (l2g) {
+        const int32_t* idx = l2g + e0 * N3;
+        for (int q = tid; q < ne * N3; q += NT) sU[q] = split_double(__ldg(u + __ldg(idx + q)));
+    } else {
         const double* src = u + e0 * N3;
         for (int q = tid; q < ne * N3; q += NT) sU[q] = split_double(__ldg(src + q));
     }
@@ -438,7 +441,7 @@ constexpr size_t ffe_smem_bytes(int epb)
 template <int NX, int EPB>
 __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ffe(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
-             const double* __restrict__ u, double* __restrict__ w)
+             const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g)
 {
     static_assert(NX % 2 == 0 && NX <= 12, "even nx up to 12");
     using T = float2;
@@ -473,10 +476,11 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
     {
         const double* src = u + e0 * N3;
+        const int32_t* idx = l2g ? l2g + e0 * N3 : nullptr;
         for (int q = tid; q < ne * N3; q += NT) {
             const int el = q / N3, p = q - el * N3;
             const int k = p / N2, ji = p - k * N2;
-            const float2 v = split_double(__ldg(src + q));
+            const float2 v = split_double(idx ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
             float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
             dst[k & 1] = v.x;
             dst[2 + (k & 1)] = v.y;
@@ -639,7 +643,7 @@ constexpr size_t ff_variant_smem()
 
 template <int NX, int EPB>
 nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                                cudaStream_t s)
+                                cudaStream_t s, const int32_t* l2g)
 {
     constexpr size_t smem = ff_variant_smem<NX, EPB>();
     static bool configured = false;
@@ -653,7 +657,7 @@ nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff,
             configured = true;
         }
         k_ax_ffe<NX, EPB><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(nelt, D, reinterpret_cast<const float4*>(Gff),
-                                                                          u, w);
+                                                                          u, w, l2g);
     } else {
         if (!configured) {
             nek_status st = check_cuda(
@@ -662,7 +666,7 @@ nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff,
             configured = true;
         }
         k_ax_ff<NX, EPB><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
-            nelt, D, reinterpret_cast<const float4*>(Gff), u, w);
+            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g);
     }
     return check_launch();
 }
@@ -675,24 +679,24 @@ constexpr bool ff_fits()
 
 template <int NX>
 nek_status launch_ax_ff_nx(int epb, int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                           cudaStream_t s)
+                           cudaStream_t s, const int32_t* l2g)
 {
     if (epb <= 0) epb = ff_epb<NX>();
     switch (epb) {
         case 1:
-            if constexpr (ff_fits<NX, 1>()) return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s);
+            if constexpr (ff_fits<NX, 1>()) return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s, l2g);
             break;
         case 2:
-            if constexpr (ff_fits<NX, 2>()) return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s);
+            if constexpr (ff_fits<NX, 2>()) return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s, l2g);
             break;
         case 4:
-            if constexpr (ff_fits<NX, 4>()) return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s);
+            if constexpr (ff_fits<NX, 4>()) return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s, l2g);
             break;
         default:
             break;
     }
     if constexpr (ff_epb<NX>() != 1 && ff_epb<NX>() != 2 && ff_epb<NX>() != 4)
-        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s);
+        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s, l2g);
     return NEK_ERR_INVALID_ARG;
 }
 
@@ -707,24 +711,24 @@ __global__ void k_g_to_ff(int64_t npts, const double* __restrict__ G, float2* __
 }  // namespace
 
 nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
-                            double* w, cudaStream_t s)
+                            double* w, cudaStream_t s, const int32_t* l2g)
 {
     switch (nx) {
-        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s);
-        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s);
-        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s);
-        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s);
-        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s);
-        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s);
-        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s);
-        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s);
-        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s);
-        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s);
-        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s);
-        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s);
-        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s);
-        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s);
-        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s);
+        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s, l2g);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
 }
@@ -760,9 +764,9 @@ bool ax_ff_epb_fits(int nx, int epb)
 }
 
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
-                        cudaStream_t s)
+                        cudaStream_t s, const int32_t* l2g)
 {
-    return launch_ax_ff_epb(tuned_epb(NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s);
+    return launch_ax_ff_epb(tuned_epb(NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s, l2g);
 }
 
 }  // namespace nek

@@ -55,6 +55,12 @@ __global__ void k_invert_masked(int64_t n, const uint8_t* __restrict__ mask, dou
 
 }  // namespace
 
+nek_status launch_diag_local(int64_t nelt, int nx, const double* D, const double* G, double* d, cudaStream_t s)
+{
+    k_diag_local<<<stream_blocks(nelt * (int64_t)nx * nx * nx), 256, 0, s>>>(nelt, nx, D, G, d);
+    return check_launch();
+}
+
 }  // namespace nek
 
 using namespace nek;

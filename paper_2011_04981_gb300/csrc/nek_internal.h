@@ -36,17 +36,21 @@ bool ax_fp64_epb_fits(int nx, int epb);
 bool ax_ff_epb_fits(int nx, int epb);
 nek_status launch_ax_fp64_epb(int epb, int64_t nelt, int nx, const double* D, const double* G, const double* u,
                               double* w, cudaStream_t s);
+// l2g (optional): u is then a unique-node vector and element point p of the
+// launch reads u[l2g[p]] (the gather Q u of the unique-node form).
 nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
-                            double* w, cudaStream_t s);
+                            double* w, cudaStream_t s, const int32_t* l2g = nullptr);
 
 // Kernel launchers (arguments already validated).
 nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w,
                           cudaStream_t s);
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
-                        cudaStream_t s);
+                        cudaStream_t s, const int32_t* l2g = nullptr);
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
                           const float* u, float* w, cudaStream_t s);
 nek_status launch_mask(int64_t n, const uint8_t* mask, double* v, cudaStream_t s);
+// Diagonal of the element operators (before summation over shared nodes).
+nek_status launch_diag_local(int64_t nelt, int nx, const double* D, const double* G, double* d, cudaStream_t s);
 nek_status launch_dssum(const nek_gs* gs, double* v, cudaStream_t s);
 
 // Deterministic block-partial reductions use this fixed grid for a given length.

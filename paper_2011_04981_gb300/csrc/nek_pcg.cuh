@@ -41,6 +41,14 @@ constexpr int NT = kReduceThreads;
 
 __device__ __forceinline__ bool halted(const Scalars* sc) { return sc->done || sc->status != NEK_OK; }
 
+// Inner-product weight of entry q: 1/multiplicity on E-vectors, 1 when c is
+// null (unique-node vectors, where every node is stored once).
+template <class V>
+__device__ __forceinline__ double cw(const V* __restrict__ c, int64_t q)
+{
+    return c ? (double)c[q] : 1.0;
+}
+
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 inline int stream_blocks(int64_t n)
@@ -69,7 +77,7 @@ __global__ void k_dssum_t(int64_t ngroups, const int32_t* __restrict__ off, cons
 template <class V>
 nek_status dssum(const nek_gs* gs, V* v, cudaStream_t s)
 {
-    if (gs->ngroups == 0) return NEK_OK;
+    if (!gs || gs->ngroups == 0) return NEK_OK;  // no plan: the operator is already assembled
     const int64_t nb = (gs->ngroups + 255) / 256;
     k_dssum_t<V><<<static_cast<int>(std::min<int64_t>(nb, 152 * 64)), 256, 0, s>>>(gs->ngroups, gs->d_offsets,
                                                                                  gs->d_members, v);
@@ -92,8 +100,8 @@ __global__ void __launch_bounds__(NT) k_init(int64_t n, const V* __restrict__ c,
         r[q] = rq;
         z[q] = zq;
         p[q] = zq;
-        arz += (double)c[q] * (double)rq * (double)zq;
-        arr += (double)c[q] * (double)rq * (double)rq;
+        arz += cw(c, q) * (double)rq * (double)zq;
+        arr += cw(c, q) * (double)rq * (double)rq;
     }
     double t = block_sum<NT>(arz, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -143,7 +151,7 @@ __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, c
             wq = V(0);
             w[q] = V(0);
         }
-        acc += (double)c[q] * (double)p[q] * (double)wq;
+        acc += cw(c, q) * (double)p[q] * (double)wq;
     }
     const double t = block_sum<NT>(acc, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -183,8 +191,8 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
         const V zq = minv[q] * rq;
         r[q] = rq;
         z[q] = zq;
-        arr += (double)c[q] * (double)rq * (double)rq;
-        arz += (double)c[q] * (double)rq * (double)zq;
+        arr += cw(c, q) * (double)rq * (double)rq;
+        arz += cw(c, q) * (double)rq * (double)zq;
     }
     double t = block_sum<NT>(arr, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -240,7 +248,9 @@ struct Result {
     int ax_timed = 0;
 };
 
-// Runs PCG from x = 0.  `ax(p, w, stream)` applies the element operator.
+// Runs PCG from x = 0.  `ax(p, w, stream)` applies the element operator, which
+// gs then sums over shared nodes; with gs null, ax applies the assembled
+// operator itself.  c null weights every entry by 1.
 // tol > 0: stop at convergence (NEK_ERR_NOT_CONVERGED after max_iter);
 // tol == 0: exactly max_iter iterations.  Leaves the stream synchronised.
 template <class V, class AxFn>

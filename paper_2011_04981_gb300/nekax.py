@@ -127,6 +127,17 @@ _SIGS = {
     "nek_cg_solve": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, _P], _I),
     "nek_cg_solve_ex": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, ctypes.POINTER(NekCgOpts), _P],
                         _I),
+    "nek_lvec_create": ([_I64, _P, _P, ctypes.POINTER(_P)], _I),
+    "nek_lvec_destroy": ([_P], _I),
+    "nek_lvec_size": ([_P], _I64),
+    "nek_lvec_scatter": ([_P, _P, _P, _P], _I),
+    "nek_lvec_restrict": ([_P, _P, _P, _P], _I),
+    "nek_lvec_assemble": ([_P, _P, _P, _P], _I),
+    "nek_lvec_ax_ff": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P], _I),
+    "nek_lvec_jacobi_minv": ([_P, _I64, _I, _P, _P, _P, _P, _P], _I),
+    "nek_lvec_cg_workspace_bytes": ([_P], ctypes.c_size_t),
+    "nek_lvec_cg_solve": ([_P, _I64, _I, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, ctypes.POINTER(NekCgOpts), _P],
+                          _I),
 }
 
 
@@ -443,3 +454,68 @@ def cg_solve(gs: GsPlan, nelt, nx, D, G, m, minv, f, x, tol=1e-8, max_iter=1000,
         raise NekError("nek_cg_solve", st)
     return dict(status=st, iters=it.value, relres=rr.value, ax_ms_total=opts.ax_ms_total,
                 ax_launches=opts.ax_launches, kernel_launches=opts.kernel_launches)
+
+
+class LvecPlan:
+    """Owning wrapper of a ``nek_lvec*`` plan (unique-node vectors, ascending global id)."""
+
+    def __init__(self, glo_num, mask):
+        glo = np.ascontiguousarray(glo_num, dtype=np.int64).reshape(-1)
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        if m.shape != glo.shape:
+            raise ValueError("glo_num and mask differ in size")
+        h = _P()
+        _check("nek_lvec_create", load().nek_lvec_create(glo.shape[0], glo.ctypes.data, m.ctypes.data,
+                                                         ctypes.byref(h)))
+        self._h = h
+        self.npts = glo.shape[0]
+        self.size = int(load().nek_lvec_size(h))
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def scatter(self, uL, uE, stream=None):
+        _check("nek_lvec_scatter", load().nek_lvec_scatter(self._h, _ptr(uL), _ptr(uE), _stream(stream)))
+
+    def restrict(self, uE, uL, stream=None):
+        _check("nek_lvec_restrict", load().nek_lvec_restrict(self._h, _ptr(uE), _ptr(uL), _stream(stream)))
+
+    def assemble(self, wE, wL, stream=None):
+        _check("nek_lvec_assemble", load().nek_lvec_assemble(self._h, _ptr(wE), _ptr(wL), _stream(stream)))
+
+    def ax_ff(self, nelt, nx, D, Gff, uL, wL, wE, stream=None):
+        _check("nek_lvec_ax_ff", load().nek_lvec_ax_ff(self._h, nelt, nx, _ptr(D), _ptr(Gff), _ptr(uL), _ptr(wL),
+                                                       _ptr(wE), _stream(stream)))
+
+    def jacobi_minv(self, nelt, nx, D, G, minvL, scratchE, stream=None):
+        _check("nek_lvec_jacobi_minv", load().nek_lvec_jacobi_minv(self._h, nelt, nx, _ptr(D), _ptr(G), _ptr(minvL),
+                                                                   _ptr(scratchE), _stream(stream)))
+
+    def workspace_bytes(self):
+        return int(load().nek_lvec_cg_workspace_bytes(self._h))
+
+    def cg_solve(self, nelt, nx, D, Gff, minvL, fL, xL, tol=1e-8, max_iter=1000, workspace=None, check_every=1,
+                 time_ax=False, stream=None):
+        """Jacobi-PCG on unique-node vectors; returns the dict of :func:`cg_solve`."""
+        it = _I(0)
+        rr = _D(0.0)
+        opts = NekCgOpts(check_every, 1 if time_ax else 0, 0.0, 0, 0, AX_FF, None)
+        st = load().nek_lvec_cg_solve(self._h, nelt, nx, _ptr(D), _ptr(Gff), _ptr(minvL), _ptr(fL), _ptr(xL),
+                                      float(tol), int(max_iter), _ptr(workspace), ctypes.byref(it), ctypes.byref(rr),
+                                      ctypes.byref(opts), _stream(stream))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            raise NekError("nek_lvec_cg_solve", st)
+        return dict(status=st, iters=it.value, relres=rr.value, ax_ms_total=opts.ax_ms_total,
+                    ax_launches=opts.ax_launches, kernel_launches=opts.kernel_launches)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().nek_lvec_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -56,6 +56,26 @@ class DeviceProblem:
         return nekax.cg_solve(self.gs, self.nelt, self.nx, self.D, self.G, self.mask, self.minv, f, x, tol,
                               max_iter, workspace, check_every, time_ax, stream, ax_impl=ax_impl, Gff=Gff)
 
+    def lvec(self):
+        """Unique-node plan, its Jacobi inverse diagonal and solve workspace (built once)."""
+        import torch
+
+        if getattr(self, "_lv", None) is None:
+            lv = nekax.LvecPlan(self.mesh.glo_num, self.mesh.mask)
+            minvL = torch.empty(lv.size, dtype=torch.float64, device=self.device)
+            scratch = torch.empty(self.npts, dtype=torch.float64, device=self.device)
+            lv.jacobi_minv(self.nelt, self.nx, self.D, self.G, minvL, scratch)
+            del scratch
+            ws = torch.empty(lv.workspace_bytes() // 8 + 64, dtype=torch.float64, device=self.device)
+            self._lv = (lv, minvL, ws)
+        return self._lv
+
+    def cg_lvec(self, fL, xL, tol=1e-8, max_iter=1000, check_every=1, time_ax=False, stream=None):
+        """Jacobi-PCG on unique-node vectors (fL, xL of lvec()[0].size entries), AX = nek_ax_ff."""
+        lv, minvL, ws = self.lvec()
+        return lv.cg_solve(self.nelt, self.nx, self.D, self.prepare_ff(), minvL, fL, xL, tol, max_iter, ws,
+                           check_every, time_ax, stream)
+
 
 class DeviceBatch:
     """Many meshes solved together: concatenated (sorted by nx) device buffers and a nek_batch plan."""

@@ -171,3 +171,31 @@ def test_batch_entry_points_reject_bad_arguments(lib):
     stats = nekax.NekBatchStats()
     assert L.nek_batch_cg_solve(None, 0x100, None, 0x100, None, 0x100, 0x100, 1e-8, 10, 5, None, None, None, None,
                                 ctypes.byref(stats), None) == nekax.ERR_INVALID_ARG
+
+
+def test_lvec_entry_points_reject_bad_arguments(lib):
+    L = lib
+    h = ctypes.c_void_p()
+    glo = np.array([0, 1, 1, 2], dtype=np.int64)
+    good = np.array([1, 1, 1, 0], dtype=np.uint8)
+    disagree = np.array([1, 1, 0, 0], dtype=np.uint8)  # the two copies of node 1 differ
+    neg = np.array([0, -1, 1, 2], dtype=np.int64)
+    assert L.nek_lvec_create(4, glo.ctypes.data, good.ctypes.data, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_lvec_create(-1, glo.ctypes.data, good.ctypes.data, ctypes.byref(h)) == nekax.ERR_INVALID_ARG
+    assert L.nek_lvec_create(4, None, good.ctypes.data, ctypes.byref(h)) == nekax.ERR_INVALID_ARG
+    assert L.nek_lvec_create(4, glo.ctypes.data, disagree.ctypes.data, ctypes.byref(h)) == nekax.ERR_INVALID_ARG
+    assert L.nek_lvec_create(4, neg.ctypes.data, good.ctypes.data, ctypes.byref(h)) == nekax.ERR_INVALID_ARG
+    assert L.nek_lvec_create(1 << 31, glo.ctypes.data, good.ctypes.data, ctypes.byref(h)) == nekax.ERR_TOO_LARGE
+    assert h.value is None
+    assert L.nek_lvec_destroy(None) == nekax.OK
+    assert L.nek_lvec_size(None) == -1
+    assert L.nek_lvec_cg_workspace_bytes(None) == 0
+    for f in (L.nek_lvec_scatter, L.nek_lvec_restrict, L.nek_lvec_assemble):
+        assert f(None, 0x100, 0x100, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_lvec_ax_ff(None, 1, 8, 0x100, 0x100, 0x100, 0x200, 0x300, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_lvec_ax_ff(None, 1, 17, 0x100, 0x100, 0x100, 0x200, 0x300, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_lvec_jacobi_minv(None, 1, 8, 0x100, 0x100, 0x100, 0x200, None) == nekax.ERR_INVALID_ARG
+    it, rr = ctypes.c_int(7), ctypes.c_double(7.0)
+    assert L.nek_lvec_cg_solve(None, 1, 8, 0x100, 0x100, 0x100, 0x100, 0x200, 1e-8, 10, None, ctypes.byref(it),
+                               ctypes.byref(rr), None, None) == nekax.ERR_INVALID_ARG
+    assert it.value == 0 and rr.value == 0.0
