@@ -42,12 +42,14 @@ struct Lp<__nv_bfloat16> {
     __device__ static __forceinline__ float rnd(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
     __device__ static __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __forceinline__ __nv_bfloat16 from_f(float x) { return __float2bfloat16_rn(x); }
+    __device__ static __forceinline__ float bits_to_f(unsigned short h) { return __uint_as_float((unsigned)h << 16); }
 };
 template <>
 struct Lp<__half> {
     __device__ static __forceinline__ float rnd(float x) { return __half2float(__float2half_rn(x)); }
     __device__ static __forceinline__ float to_f(__half v) { return __half2float(v); }
     __device__ static __forceinline__ __half from_f(float x) { return __float2half_rn(x); }
+    __device__ static __forceinline__ float bits_to_f(unsigned short h) { return __half2float(__ushort_as_half(h)); }
 };
 
 // slot[key] = max(slot[key], v) for v >= 0, one shared-memory atomic per key per warp.
@@ -73,12 +75,90 @@ constexpr int lp_epb(int nx)
          : nx == 9 ? 4 : nx == 10 ? 4 : nx == 11 ? 2 : nx == 12 ? 2 : nx == 13 ? 2 : 1;
 }
 
+// D rows padded to a multiple of 4 floats so a row is read with 16-byte broadcast loads.
+constexpr int lp_row(int nx) { return (nx + 3) & ~3; }
+
 template <int NX, int EPB>
 constexpr size_t lp_smem_bytes()
 {
-    return sizeof(float) * (size_t)(NX * NX + 2 * EPB * NX * NX * NX + EPB + 4);
+    // rnd(D) and rnd(D)^T (padded rows), three [EPB][N3] float blocks, per-element maxima
+    return sizeof(float) * (size_t)(2 * NX * lp_row(NX) + 3 * EPB * NX * NX * NX + EPB + 4);
 }
 
+// Six G values of point p as floats (3 paired loads where alignment allows).
+template <class S>
+struct GLoad;
+template <>
+struct GLoad<float> {
+    __device__ static __forceinline__ void get(const float* __restrict__ g, bool al8, float* v)
+    {
+        if (al8) {
+            const float2* g2 = reinterpret_cast<const float2*>(g);
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const float2 t = __ldg(g2 + q);
+                v[2 * q] = t.x;
+                v[2 * q + 1] = t.y;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 6; q++) v[q] = __ldg(g + q);
+        }
+    }
+};
+template <class H>
+struct GLoad16 {
+    // 6 values of 2 bytes at a 4-byte aligned address (12 p bytes from a 4-byte aligned base)
+    __device__ static __forceinline__ void get(const H* __restrict__ g, bool, float* v)
+    {
+        const unsigned* g4 = reinterpret_cast<const unsigned*>(g);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const unsigned t = __ldg(g4 + q);
+            v[2 * q] = Lp<H>::bits_to_f(static_cast<unsigned short>(t & 0xffffu));
+            v[2 * q + 1] = Lp<H>::bits_to_f(static_cast<unsigned short>(t >> 16));
+        }
+    }
+};
+template <>
+struct GLoad<__nv_bfloat16> : GLoad16<__nv_bfloat16> {
+};
+template <>
+struct GLoad<__half> : GLoad16<__half> {
+};
+
+// out[o] = sum_l M[o][l] x[l], l ascending (one FP32 FMA chain per output); M rows
+// are read as 16-byte broadcasts from shared memory (every lane reads the same row).
+template <int NX>
+__device__ __forceinline__ void line_apply(const float* __restrict__ M, const float (&x)[NX], float (&out)[NX])
+{
+    constexpr int R = lp_row(NX);
+#pragma unroll
+    for (int o = 0; o < NX; o++) {
+        // Load each row of M just before its use: hoisted ahead (within or across
+        // calls), the nx^2 values of M would crowd the lines out of registers.
+        asm volatile("" ::: "memory");
+        float acc = 0.f;
+#pragma unroll
+        for (int l4 = 0; l4 < R / 4; l4++) {
+            const float4 m = reinterpret_cast<const float4*>(M + o * R)[l4];
+            const float mv[4] = {m.x, m.y, m.z, m.w};
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+                if (4 * l4 + c < NX) acc = fmaf(mv[c], x[4 * l4 + c], acc);
+        }
+        out[o] = acc;
+    }
+}
+
+// Line-pass form: every contraction is done by a thread that holds one whole
+// line of nx values in registers and produces the nx results of that line
+// (nx^2 FMAs per nx shared-memory reads).  Thread (a, b) of an element owns the
+// r-line (j, k) = (a, b), the s-line (i, k) = (a, b) and the t-line
+// (i, j) = (a, b).  Phase 1 writes ur and us to shared memory and keeps ut in
+// registers; the pointwise G product runs on the t-lines; phase 2 sums the
+// r- and s-contributions through shared memory and adds the t-contribution in
+// registers before the store.
 template <class S, int NX, int EPB>
 __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const double* __restrict__ D,
                                                           const S* __restrict__ Glp,
@@ -86,85 +166,126 @@ __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const dou
                                                           const float* __restrict__ u, float* __restrict__ w)
 {
     using L = Lp<S>;
-    constexpr int N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB;
-    extern __shared__ float fsm[];
-    float* sD = fsm;           // rnd(D)
-    float* sA = sD + N2;       // [EPB][N3] u_q, then wr_q
-    float* sB = sA + EPB * N3; // [EPB][N3] ws_q
-    float* sMax = sB + EPB * N3;
+    constexpr int N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB, R = lp_row(NX);
+    extern __shared__ __align__(16) float fsm[];
+    float* sD = fsm;                 // [NX][R]  rnd(D)[o][l]
+    float* sDT = sD + NX * R;        // [NX][R]  rnd(D)[l][o] at o*R + l
+    float* sU = sDT + NX * R;        // [EPB][N3] u_q, later the r+s part of w
+    float* sR = sU + EPB * N3;       // [EPB][N3] ur, then wr
+    float* sS = sR + EPB * N3;       // [EPB][N3] us, then ws
+    float* sMax = sS + EPB * N3;     // [EPB]
 
     const int tid = threadIdx.x;
     const int64_t e0 = (int64_t)blockIdx.x * EPB;
     const int ne = static_cast<int>(nelt - e0 < EPB ? nelt - e0 : EPB);
 
-    for (int q = tid; q < N2; q += NT) sD[q] = L::rnd((float)D[q]);
+    for (int q = tid; q < NX * R; q += NT) {
+        const int o = q / R, l = q - o * R;
+        sD[q] = l < NX ? L::rnd((float)D[o * NX + l]) : 0.f;
+        sDT[q] = l < NX ? L::rnd((float)D[l * NX + o]) : 0.f;
+    }
     for (int q = tid; q < EPB; q += NT) sMax[q] = 0.f;
     {
         const float* src = u + e0 * N3;
-        for (int q = tid; q < ne * N3; q += NT) sA[q] = __ldg(src + q);
+        for (int q = tid; q < ne * N3; q += NT) sU[q] = __ldg(src + q);
     }
     __syncthreads();
 
     const int el = tid / N2;
     const int q2 = tid - el * N2;
-    const int i = q2 % NX, j = q2 / NX;
+    const int a = q2 % NX, b = q2 / NX;
     const bool active = el < ne;
-    float* ue = sA + el * N3;
-    float* se = sB + el * N3;
+    float* ue = sU + el * N3;
+    float* re = sR + el * N3;
+    float* se = sS + el * N3;
     {
         float m = 0.f;
         if (active) {
 #pragma unroll
-            for (int l = 0; l < NX; l++) m = fmaxf(m, fabsf(ue[i + NX * (j + NX * l)]));
+            for (int l = 0; l < NX; l++) m = fmaxf(m, fabsf(ue[l * N2 + b * NX + a]));
         }
         segmented_max_to_smem(el, m, sMax);
     }
     __syncthreads();
-    for (int q = tid; q < ne * N3; q += NT) sA[q] = L::rnd(sA[q] * (1.f / pow2_ceil(sMax[q / N3])));
-    __syncthreads();
-
-    float ul[NX], wr[NX], wt[NX];
-    if (active) {
-#pragma unroll
-        for (int l = 0; l < NX; l++) ul[l] = ue[i + NX * (j + NX * l)];
-        const S* Ge = Glp + (e0 + el) * (int64_t)N3 * 6;
-#pragma unroll
-        for (int k = 0; k < NX; k++) {
-            const int p = i + NX * (j + NX * k);
-            float ar = 0.f, as = 0.f, at = 0.f;
+    const float su = pow2_ceil(sMax[el]);
+    {
+        const float inv = 1.f / su;  // a power of two: exact
+        if (active) {
 #pragma unroll
             for (int l = 0; l < NX; l++) {
-                ar = fmaf(sD[i * NX + l], ue[l + NX * (j + NX * k)], ar);
-                as = fmaf(sD[j * NX + l], ue[i + NX * (l + NX * k)], as);
-                at = fmaf(sD[k * NX + l], ul[l], at);
+                const int p = l * N2 + b * NX + a;
+                ue[p] = L::rnd(ue[p] * inv);
             }
-            const S* g = Ge + 6 * p;
-            const float g0 = L::to_f(g[0]), g1 = L::to_f(g[1]), g2 = L::to_f(g[2]), g3 = L::to_f(g[3]),
-                        g4 = L::to_f(g[4]), g5 = L::to_f(g[5]);
-            wr[k] = L::rnd(fmaf(g0, ar, fmaf(g1, as, g2 * at)));
-            se[p] = L::rnd(fmaf(g1, ar, fmaf(g3, as, g4 * at)));
-            wt[k] = L::rnd(fmaf(g2, ar, fmaf(g4, as, g5 * at)));
         }
     }
     __syncthreads();
+
+    // ---------------------------------------------------------------- phase 1
+    float ut[NX];
     if (active) {
+        float x[NX], y[NX];
 #pragma unroll
-        for (int k = 0; k < NX; k++) ue[i + NX * (j + NX * k)] = wr[k];
+        for (int l = 0; l < NX; l++) x[l] = ue[b * N2 + a * NX + l];  // r-line (j,k) = (a,b)
+        line_apply<NX>(sD, x, y);
+#pragma unroll
+        for (int o = 0; o < NX; o++) re[b * N2 + a * NX + o] = y[o];
+#pragma unroll
+        for (int l = 0; l < NX; l++) x[l] = ue[b * N2 + l * NX + a];  // s-line (i,k) = (a,b)
+        line_apply<NX>(sD, x, y);
+#pragma unroll
+        for (int o = 0; o < NX; o++) se[b * N2 + o * NX + a] = y[o];
+#pragma unroll
+        for (int l = 0; l < NX; l++) x[l] = ue[l * N2 + b * NX + a];  // t-line (i,j) = (a,b)
+        line_apply<NX>(sD, x, ut);
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- G product on the t-lines
+    float wt[NX];
+    if (active) {
+        const S* Ge = Glp + (e0 + el) * (int64_t)N3 * 6;
+        const bool al8 = (reinterpret_cast<uintptr_t>(Glp) & 7) == 0;
+#pragma unroll
+        for (int k = 0; k < NX; k++) {
+            const int p = k * N2 + b * NX + a;
+            const float ar = re[p], as = se[p], at = ut[k];
+            float g[6];
+            GLoad<S>::get(Ge + 6 * p, al8, g);
+            re[p] = L::rnd(fmaf(g[0], ar, fmaf(g[1], as, g[2] * at)));
+            se[p] = L::rnd(fmaf(g[1], ar, fmaf(g[3], as, g[4] * at)));
+            wt[k] = L::rnd(fmaf(g[2], ar, fmaf(g[4], as, g[5] * at)));
+        }
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- phase 2
+    float os[NX];
+    if (active) {
+        float x[NX], y[NX];
+#pragma unroll
+        for (int l = 0; l < NX; l++) x[l] = re[b * N2 + a * NX + l];  // r-line of wr
+        line_apply<NX>(sDT, x, y);
+#pragma unroll
+        for (int o = 0; o < NX; o++) ue[b * N2 + a * NX + o] = y[o];  // u is dead: reuse for w
+#pragma unroll
+        for (int l = 0; l < NX; l++) x[l] = se[b * N2 + l * NX + a];  // s-line of ws
+        line_apply<NX>(sDT, x, os);
     }
     __syncthreads();
     if (active) {
-        const float scale = pow2_ceil(sMax[el]) * gscale[e0 + el];
+#pragma unroll
+        for (int o = 0; o < NX; o++) ue[b * N2 + o * NX + a] += os[o];
+    }
+    __syncthreads();
+    if (active) {
+        float ot[NX];
+        line_apply<NX>(sDT, wt, ot);
+        const float scale = su * gscale[e0 + el];
         float* we = w + (e0 + el) * (int64_t)N3;
 #pragma unroll
         for (int k = 0; k < NX; k++) {
-            float s = 0.f;
-#pragma unroll
-            for (int l = 0; l < NX; l++) {
-                s = fmaf(sD[l * NX + i], ue[l + NX * (j + NX * k)], s);
-                s = fmaf(sD[l * NX + j], se[i + NX * (l + NX * k)], s);
-                s = fmaf(sD[l * NX + k], wt[l], s);
-            }
-            we[i + NX * (j + NX * k)] = s * scale;
+            const int p = k * N2 + b * NX + a;
+            we[p] = (ue[p] + ot[k]) * scale;
         }
     }
 }
