@@ -232,7 +232,7 @@ constexpr int ff_min_blocks()
 
 // Thread (e, i, j, g) computes the W-wide k-groups of planes [g*PPT, g*PPT + PPT)
 // of element e.
-template <int NX, int EPB>
+template <int NX, int EPB, bool GATHER>
 __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ff(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
             const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g)
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
         sDT[(q % NX) * NX + q / NX] = d;
     }
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
-    if (l2g) {
+    if constexpr (GATHER) {
         const int32_t* idx = l2g + e0 * N3;
         for (int q = tid; q < ne * N3; q += NT) sU[q] = split_double(__ldg(u + __ldg(idx + q)));
     } else {
@@ -438,7 +438,7 @@ constexpr size_t ffe_smem_bytes(int epb)
            sizeof(float2) * (size_t)epb * NX * NX * NX + sizeof(float) * (2 * NX + 4 * (size_t)epb + 4) + 16;
 }
 
-template <int NX, int EPB>
+template <int NX, int EPB, bool GATHER>
 __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ffe(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
              const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g)
@@ -476,11 +476,11 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
     {
         const double* src = u + e0 * N3;
-        const int32_t* idx = l2g ? l2g + e0 * N3 : nullptr;
+        const int32_t* idx = l2g + e0 * N3;  // used with GATHER only
         for (int q = tid; q < ne * N3; q += NT) {
             const int el = q / N3, p = q - el * N3;
             const int k = p / N2, ji = p - k * N2;
-            const float2 v = split_double(idx ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
+            const float2 v = split_double(GATHER ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
             float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
             dst[k & 1] = v.x;
             dst[2 + (k & 1)] = v.y;
@@ -641,9 +641,9 @@ constexpr size_t ff_variant_smem()
         return ff_smem_bytes<NX, EPB>();
 }
 
-template <int NX, int EPB>
-nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                                cudaStream_t s, const int32_t* l2g)
+template <int NX, int EPB, bool GATHER>
+nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
+                               cudaStream_t s, const int32_t* l2g)
 {
     constexpr size_t smem = ff_variant_smem<NX, EPB>();
     static bool configured = false;
@@ -651,24 +651,32 @@ nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff,
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
     if constexpr (ff_packed_layout<NX>()) {
         if (!configured) {
-            nek_status st = check_cuda(
-                cudaFuncSetAttribute(k_ax_ffe<NX, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            nek_status st = check_cuda(cudaFuncSetAttribute(k_ax_ffe<NX, EPB, GATHER>,
+                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             if (st != NEK_OK) return st;
             configured = true;
         }
-        k_ax_ffe<NX, EPB><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(nelt, D, reinterpret_cast<const float4*>(Gff),
-                                                                          u, w, l2g);
+        k_ax_ffe<NX, EPB, GATHER><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
+            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g);
     } else {
         if (!configured) {
-            nek_status st = check_cuda(
-                cudaFuncSetAttribute(k_ax_ff<NX, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            nek_status st = check_cuda(cudaFuncSetAttribute(k_ax_ff<NX, EPB, GATHER>,
+                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             if (st != NEK_OK) return st;
             configured = true;
         }
-        k_ax_ff<NX, EPB><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
+        k_ax_ff<NX, EPB, GATHER><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
             nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g);
     }
     return check_launch();
+}
+
+template <int NX, int EPB>
+nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
+                                cudaStream_t s, const int32_t* l2g)
+{
+    if (l2g) return launch_ax_ff_kernel<NX, EPB, true>(nelt, D, Gff, u, w, s, l2g);
+    return launch_ax_ff_kernel<NX, EPB, false>(nelt, D, Gff, u, w, s, nullptr);
 }
 
 template <int NX, int EPB>

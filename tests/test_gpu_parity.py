@@ -344,6 +344,42 @@ def test_cg_with_ff_operator(dims, nx):
     st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 1e-8, 2000)
     assert abs(res["iters"] - itr) <= 2, (res["iters"], itr)
     assert Pr.residual(f, x.cpu().numpy()) <= 1e-8 * (1 + 1e-3)
+    assert _rel(x.cpu().numpy(), xr) <= 1e-6
+
+
+@pytest.mark.parametrize("nx", [6, 8, 10, 12, 13])
+def test_cg_ff_fixed_iterations(nx):
+    """After a fixed number of iterations the float-float solve's iterate and
+    residual match the oracle's PCG."""
+    mesh = inputs.box_mesh(3, 2, 3, nx, perturb=0.1, seed=nx)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=5)
+    x = torch.empty((mesh.nelt, nx ** 3), dtype=torch.float64, device=DEV)
+    for its in (1, 2, 23):
+        res = P.cg(_t(f), x, tol=0.0, max_iter=its, ax_impl=nekax.AX_FF, time_ax=True)
+        assert res["status"] == nekax.OK and res["iters"] == its and res["ax_launches"] == its
+        # init, then AX, dssum, <p,w>, alpha, update, beta per iteration and the direction between iterations
+        assert res["kernel_launches"] == 2 + 6 * its + (its - 1)
+        st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 0.0, its)
+        assert _rel(x.cpu().numpy(), xr) <= 1e-9, its
+        assert abs(res["relres"] - rr) <= 1e-8 * rr
+        assert np.all(x.cpu().numpy()[mesh.mask == 0] == 0.0)
+
+
+def test_cg_ff_check_every_and_workspace_reuse():
+    mesh = inputs.box_mesh(3, 3, 2, 10, perturb=0.1, seed=6)
+    P = DeviceProblem(mesh, DEV)
+    f = _t(inputs.random_global_field(mesh, seed=1))
+    ws = torch.full((nekax.cg_workspace_bytes(mesh.nelt, 10, False) // 8 + 32,), float("nan"),
+                    dtype=torch.float64, device=DEV)
+    x1 = torch.empty_like(f)
+    x2 = torch.empty_like(f)
+    r1 = P.cg(f, x1, tol=1e-9, max_iter=1000, check_every=1, ax_impl=nekax.AX_FF, workspace=ws)
+    r2 = P.cg(f, x2, tol=1e-9, max_iter=1000, check_every=7, ax_impl=nekax.AX_FF, workspace=ws)
+    assert r1["status"] == r2["status"] == nekax.OK
+    assert r1["iters"] == r2["iters"]
+    assert torch.equal(x1, x2)
 
 
 # ------------------------------------------------------------------ elements-per-CTA variants
