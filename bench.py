@@ -359,6 +359,48 @@ def batch_block(torch, nprob, tol=1e-8):
             "gdofs_useful": pts_iters / dt / 1e9, "operator": "nek_ax_ff (FP64-accurate)"}
 
 
+def net_apply_rates(torch, theta, mesh, reps=20):
+    """One network application over every element of `mesh`: FP32 CUDA-core form against the BF16
+    tensor-core form (mma.sync), in points/s and useful TFLOP/s (16 416 flop per point)."""
+    import numpy as np
+
+    from paper_2011_04981_gb300 import nekax
+
+    n = mesh.nelt
+    rng = np.random.default_rng(0)
+    xin = torch.from_numpy(rng.normal(size=(n, 2, 512)).astype(np.float32)).to("cuda")
+    sc = torch.ones(n, dtype=torch.float32, device="cuda")
+    c = torch.ones((n, 512), dtype=torch.float64, device="cuda")
+    z = torch.empty_like(c)
+    flop_pt = 2 * (2 * 16 * 27 + 16 * 16 * 27 + 16 * 27)
+    _, bf16_peak = peaks_bf16()
+    out = {"elements": n, "flop_per_point": flop_pt}
+    for name, fn in (("fp32_cuda_cores", nekax.net_apply), ("bf16_tensor_cores", nekax.net_apply_bf16)):
+        fn(n, 8, theta, xin, sc, c, z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn(n, 8, theta, xin, sc, c, z)
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / reps / 1e3
+        tf = n * 512 * flop_pt / t / 1e12
+        out[name] = {"ms": t * 1e3, "gpts": n * 512 / t / 1e9, "tflops": tf}
+    out["bf16_tensor_cores"]["frac_of_bf16_peak"] = out["bf16_tensor_cores"]["tflops"] / bf16_peak
+    out["speedup"] = out["fp32_cuda_cores"]["ms"] / out["bf16_tensor_cores"]["ms"]
+    return out
+
+
+def peaks_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return "measured", float(p["bf16_tflops"])
+    except Exception:
+        return "fallback", 1900.0
+
+
 def learned_block(torch, n_meshes=200, epochs=30, eval_elems=24):
     """Configuration 5: pairs from the solver on n_meshes random meshes of the family, GPU training with the
     library's kernels, then time to 1e-8 on a held-out eval_elems^3 mesh with and without the network."""
@@ -378,6 +420,7 @@ def learned_block(torch, n_meshes=200, epochs=30, eval_elems=24):
     val0 = learned.validation_loss(theta0, val_data)
     mesh = learned.mesh_family(seed=777, e=eval_elems)
     cmp = learned.compare_on_mesh(theta, mesh, seed=3)
+    cmp["net_apply"] = net_apply_rates(torch, theta, mesh)
     return {"pairs": len(data), "data_seconds": t_data, "train_seconds": t_train, "epochs": epochs,
             "loss": "element energy norm", "train_loss_first_last": [hist[0], hist[-1]],
             "val_loss_untrained": val0, "val_loss_trained": val,

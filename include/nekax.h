@@ -326,6 +326,13 @@ nek_status nek_net_prep(int64_t nelt, int nx, const double* r, const double* min
 nek_status nek_net_apply(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
                          const double* c, double* z, void* stream);
 
+/* Same as nek_net_apply on the tensor cores: the network input and the two
+ * hidden activations are rounded to BF16 (nearest even) before each
+ * convolution, products are exact and sums FP32 (mma.sync m16n8k16, BF16 x
+ * BF16 -> FP32).  Same arguments and errors.  nek_fcg_solve uses this form. */
+nek_status nek_net_apply_bf16(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
+                              const double* c, double* z, void* stream);
+
 /* Training on a batch of `batch` samples (xin [batch][2][512], target
  * [batch][512]): loss = mean_b |y_b - t_b|^2/|t_b|^2 (device float, nullable)
  * and its gradient (grad: NPARAM floats, summed over the batch in a fixed
@@ -355,7 +362,7 @@ nek_status nek_adam_step(int n, float* theta, const float* grad, float* m, float
 
 /*
  * Flexible CG (Polak-Ribiere beta) preconditioned by the network,
- * M(r) = mask(dssum(nek_net_apply(r))), falling back to Jacobi (and restarting
+ * M(r) = mask(dssum(nek_net_apply_bf16(r))), falling back to Jacobi (and restarting
  * the direction) when the relative residual has not fallen by stag_factor
  * (0 < stag_factor < 1) in the last stag_window iterations.  theta NULL runs the
  * same loop with Jacobi throughout.  AX is nek_ax_ff when Gff is given, else

@@ -93,12 +93,27 @@ def gelu_grad(v):
     return 0.5 * (1.0 + erf(v / math.sqrt(2.0))) + v * np.exp(-0.5 * v * v) / math.sqrt(2.0 * math.pi)
 
 
-def forward(theta, x, keep=False):
+def bf16_round(v):
+    """Round to the nearest BF16 value (ties to even), via FP32: the FP32 bit
+    pattern plus 0x7FFF plus the lowest kept bit, truncated to the top 16 bits
+    (finite values)."""
+    f = np.asarray(v, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(theta, x, keep=False, act_round=None):
+    """act_round (optional): applied to the network input and to both hidden
+    activations before the convolution that reads them (the reduced-precision
+    inference form)."""
     P = unpack(theta)
+    rnd = act_round if act_round is not None else (lambda v: v)
+    x = rnd(x)
     h1 = conv(x, P["W1"], P["b1"])
-    a1 = gelu(h1)
+    a1 = rnd(gelu(h1))
     h2 = conv(a1, P["W2"], P["b2"])
-    a2 = gelu(h2)
+    a2 = rnd(gelu(h2))
     y = conv(a2, P["W3"], P["b3"])
     if keep:
         return y, (x, h1, a1, h2, a2)

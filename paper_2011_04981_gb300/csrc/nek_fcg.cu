@@ -19,6 +19,8 @@
 
 namespace nek {
 
+nek_status launch_net_apply_tc(int64_t nelt, const float* theta, const float* xin, const float* scale,
+                               const double* c, double* z, cudaStream_t s);
 nek_status launch_net_apply(int64_t nelt, const float* theta, const float* xin, const float* scale, const double* c,
                             double* z, cudaStream_t s);
 nek_status launch_net_prep(int64_t nelt, const double* r, const double* minv, float* xin, float* scale,
@@ -250,7 +252,7 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
         if (net) {
             cudaEventRecord(e0, s);
             nek_status sp = launch_net_prep(nelt, L.r, mv, L.xin, L.scale, s);
-            if (sp == NEK_OK) sp = launch_net_apply(nelt, theta, L.xin, L.scale, gs->d_c, L.z, s);
+            if (sp == NEK_OK) sp = launch_net_apply_tc(nelt, theta, L.xin, L.scale, gs->d_c, L.z, s);
             if (sp == NEK_OK) sp = pcg::dssum<double>(gs, L.z, s);
             cudaEventRecord(e1, s);
             if (sp != NEK_OK) return sp;

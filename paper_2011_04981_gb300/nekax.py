@@ -106,6 +106,7 @@ _SIGS = {
     "nek_net_param_count": ([], _I),
     "nek_net_prep": ([_I64, _I, _P, _P, _P, _P, _P], _I),
     "nek_net_apply": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
+    "nek_net_apply_bf16": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_train_workspace_bytes": ([_I], ctypes.c_size_t),
     "nek_net_forward_batch": ([_I, _P, _P, _P, _P, _P], _I),
     "nek_net_train_grad": ([_I, _P, _P, _P, _P, _P, _P, _P], _I),
@@ -398,6 +399,11 @@ def net_prep(nelt, nx, r, minv, xin, scale, stream=None):
 def net_apply(nelt, nx, theta, xin, scale, c, z, stream=None):
     _check("nek_net_apply", load().nek_net_apply(nelt, nx, _ptr(theta), _ptr(xin), _ptr(scale), _ptr(c), _ptr(z),
                                                  _stream(stream)))
+
+
+def net_apply_bf16(nelt, nx, theta, xin, scale, c, z, stream=None):
+    _check("nek_net_apply_bf16", load().nek_net_apply_bf16(nelt, nx, _ptr(theta), _ptr(xin), _ptr(scale), _ptr(c),
+                                                           _ptr(z), _stream(stream)))
 
 
 def net_train_workspace_bytes(batch):

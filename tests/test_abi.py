@@ -199,3 +199,11 @@ def test_lvec_entry_points_reject_bad_arguments(lib):
     assert L.nek_lvec_cg_solve(None, 1, 8, 0x100, 0x100, 0x100, 0x100, 0x200, 1e-8, 10, None, ctypes.byref(it),
                                ctypes.byref(rr), None, None) == nekax.ERR_INVALID_ARG
     assert it.value == 0 and rr.value == 0.0
+
+
+def test_net_apply_bf16_rejects_bad_arguments(lib):
+    L = lib
+    assert L.nek_net_apply_bf16(4, 10, 0x100, 0x100, 0x100, 0x100, 0x100, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_net_apply_bf16(-1, 8, 0x100, 0x100, 0x100, 0x100, 0x100, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_net_apply_bf16(4, 8, None, 0x100, 0x100, 0x100, 0x100, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_net_apply_bf16(0, 8, None, None, None, None, None, None) == nekax.OK

@@ -98,6 +98,39 @@ def test_prep_and_apply_match_oracle():
     assert _rel(z.cpu().numpy(), z_ref) <= 1e-4
 
 
+def test_apply_bf16_tensor_cores_match_oracle():
+    """The tensor-core inference rounds the input and both hidden activations to
+    BF16: against the oracle with the same rounding it agrees to FP32-sum level
+    (plus rare rounding ties decided differently), and against the unrounded
+    network within the BF16 bound."""
+    mesh = inputs.box_mesh(5, 3, 2, 8, perturb=0.15, seed=4)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    th = _theta(12)
+    r = inputs.random_local_field(mesh.nelt, 8, seed=3) * mesh.mask
+    rd = torch.from_numpy(r).to(DEV)
+    xin = torch.empty((mesh.nelt, 2, 512), dtype=torch.float32, device=DEV)
+    sc = torch.empty(mesh.nelt, dtype=torch.float32, device=DEV)
+    nekax.net_prep(mesh.nelt, 8, rd, P.minv, xin, sc)
+    c = torch.empty_like(rd)
+    P.gs.inv_multiplicity(c)
+    thd = torch.from_numpy(th.astype(np.float32)).to(DEV)
+    z = torch.full_like(rd, float("nan"))
+    nekax.net_apply_bf16(mesh.nelt, 8, thd, xin, sc, c, z)
+    z32 = torch.empty_like(rd)
+    nekax.net_apply(mesh.nelt, 8, thd, xin, sc, c, z32)
+    torch.cuda.synchronize()
+    xh = xin.cpu().numpy().astype(np.float64).reshape(mesh.nelt, 2, 8, 8, 8)
+    s = sc.cpu().numpy().astype(np.float64)[:, None] * Pr.c
+    yb = onet.forward(th, xh, act_round=onet.bf16_round)[:, 0].reshape(mesh.nelt, 512) * s
+    y = onet.forward(th, xh)[:, 0].reshape(mesh.nelt, 512) * s
+    zz = z.cpu().numpy()
+    assert np.all(np.isfinite(zz))
+    assert _rel(zz, yb) <= 5e-4
+    assert _rel(zz, y) <= 3e-2
+    assert _rel(z32.cpu().numpy(), y) <= 1e-4
+
+
 def test_adam_matches_oracle():
     rng = np.random.default_rng(5)
     n = 1000

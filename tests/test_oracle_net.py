@@ -133,3 +133,23 @@ def test_energy_loss_gradient_by_central_differences():
             fd = (net.energy_loss(theta + e, x, t, A) - net.energy_loss(theta - e, x, t, A)) / (2 * h)
             assert abs(fd - g[o + idx]) <= 1e-6 * max(1.0, abs(fd)), (name, idx)
         o += size
+
+
+def test_bf16_rounding_matches_torch_and_forward_rounds_activations():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    v = np.concatenate([rng.normal(scale=10.0 ** rng.uniform(-6, 6, 4000)), [0.0, -0.0, 1.0, -3.0, 65504.0],
+                        # halfway cases between neighbouring BF16 values: ties go to even
+                        [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8)]])
+    ref = torch.from_numpy(v.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(net.bf16_round(v), ref)
+    assert net.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert net.bf16_round(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    # with the identity as rounding, forward is unchanged; with BF16 it moves by a BF16-sized amount
+    th = rng.normal(scale=0.25, size=net.NPARAM)
+    x = rng.normal(size=(2, 2, 8, 8, 8))
+    y = net.forward(th, x)
+    assert np.array_equal(net.forward(th, x, act_round=lambda a: a), y)
+    yb = net.forward(th, x, act_round=net.bf16_round)
+    rel = np.linalg.norm(yb - y) / np.linalg.norm(y)
+    assert 1e-4 < rel < 3e-2
