@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--sweep", action="store_true", help="also time standalone AX at nx = 8, 10, 12, 16")
     ap.add_argument("--solve", action="store_true", help="also time one solve to 1e-8 relative residual")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=None,
+                    help="bound on the oracle's CPU time per sample (default: about 10-15 s for cpu_baseline, "
+                         "120 s spread over the steps of --impl reference)")
     ap.add_argument("--mixed", action="store_true",
                     help="also time FP64 defect correction with FP32/BF16/FP16 inner solves (to 1e-8 and 1e-10)")
     ap.add_argument("--batch", type=int, default=0,
@@ -176,6 +179,15 @@ def cpu_baseline(nx, iters_budget_s=15.0):
             "seconds": dt}
 
 
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum of a list of floats over all ranks (every rank gets it)."""
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     rank, world, _ = dist_env()
@@ -183,7 +195,7 @@ def run_reference(args):
         return 0
     cb = None
     steps_val = []
-    budget = max(3.0, 120.0 / max(1, args.steps + args.warmup))
+    budget = args.cpu_seconds if args.cpu_seconds else max(3.0, 120.0 / max(1, args.steps + args.warmup))
     for s in range(args.warmup + args.steps):
         r = cpu_baseline(args.nx, iters_budget_s=budget)
         if s >= args.warmup:
@@ -501,9 +513,7 @@ def run_native(args):
     barrier()
 
     if dist is not None:
-        tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev, t_e2e = float(tt[0]), float(tt[1])
+        t_dev, t_e2e = max_over_ranks(dist, [t_dev, t_e2e], "cuda")
 
     pts = mesh.npts
     value = pts * iters * args.steps * world / t_dev / 1e9
@@ -561,7 +571,7 @@ def run_native(args):
         del ws
         line["batch"] = batch_block(torch, args.batch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(nx)
+        cb = cpu_baseline(nx, iters_budget_s=args.cpu_seconds or 15.0)
         cb.pop("seconds", None)
         line["cpu_baseline"] = cb
     if rank == 0:
