@@ -49,6 +49,24 @@ __device__ __forceinline__ double cw(const V* __restrict__ c, int64_t q)
     return c ? (double)c[q] : 1.0;
 }
 
+// Point flags (optional, one byte per point): bit 0 = free (the mask), bit 1 =
+// owner (exactly one copy of every global node).  With flags the inner products
+// sum over owner copies, which is the 1/multiplicity-weighted sum over all
+// copies (copies hold bit-identical values) read from 1 byte instead of 8.
+constexpr uint8_t kFree = 1, kOwner = 2;
+
+template <class V>
+__device__ __forceinline__ double weight(const V* __restrict__ c, const uint8_t* __restrict__ flags, int64_t q)
+{
+    return flags ? ((flags[q] & kOwner) ? 1.0 : 0.0) : cw(c, q);
+}
+
+__device__ __forceinline__ bool is_free(const uint8_t* __restrict__ mask, const uint8_t* __restrict__ flags,
+                                        int64_t q)
+{
+    return flags ? (flags[q] & kFree) != 0 : mask[q] != 0;
+}
+
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 inline int stream_blocks(int64_t n)
@@ -89,19 +107,20 @@ template <class V>
 __global__ void __launch_bounds__(NT) k_init(int64_t n, const V* __restrict__ c, const uint8_t* __restrict__ mask,
                                               const V* __restrict__ minv, const V* __restrict__ f, V* __restrict__ x,
                                               V* __restrict__ r, V* __restrict__ z, V* __restrict__ p,
-                                              double* __restrict__ parts)
+                                              double* __restrict__ parts, const uint8_t* __restrict__ flags)
 {
     __shared__ double sh[NT / 32];
     double arz = 0.0, arr = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
-        const V rq = mask[q] ? f[q] : V(0);
+        const V rq = is_free(mask, flags, q) ? f[q] : V(0);
         const V zq = minv[q] * rq;
         x[q] = V(0);
         r[q] = rq;
         z[q] = zq;
         p[q] = zq;
-        arz += cw(c, q) * (double)rq * (double)zq;
-        arr += cw(c, q) * (double)rq * (double)rq;
+        const double wq = weight(c, flags, q);
+        arz += wq * (double)rq * (double)zq;
+        arr += wq * (double)rq * (double)rq;
     }
     double t = block_sum<NT>(arz, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -140,18 +159,18 @@ __global__ void __launch_bounds__(NT) k_init_finish(const double* __restrict__ p
 template <class V>
 __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, const uint8_t* __restrict__ mask,
                                             const V* __restrict__ p, V* __restrict__ w, double* __restrict__ parts,
-                                            const Scalars* __restrict__ sc)
+                                            const Scalars* __restrict__ sc, const uint8_t* __restrict__ flags)
 {
     __shared__ double sh[NT / 32];
     if (halted(sc)) return;
     double acc = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
         V wq = w[q];
-        if (!mask[q]) {
+        if (!is_free(mask, flags, q)) {
             wq = V(0);
             w[q] = V(0);
         }
-        acc += cw(c, q) * (double)p[q] * (double)wq;
+        acc += weight(c, flags, q) * (double)p[q] * (double)wq;
     }
     const double t = block_sum<NT>(acc, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -179,7 +198,7 @@ template <class V>
 __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ c, const V* __restrict__ minv,
                                                 const V* __restrict__ p, const V* __restrict__ w, V* __restrict__ x,
                                                 V* __restrict__ r, V* __restrict__ z, double* __restrict__ parts,
-                                                const Scalars* __restrict__ sc)
+                                                const Scalars* __restrict__ sc, const uint8_t* __restrict__ flags)
 {
     __shared__ double sh[NT / 32];
     if (halted(sc)) return;
@@ -191,8 +210,9 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
         const V zq = minv[q] * rq;
         r[q] = rq;
         z[q] = zq;
-        arr += cw(c, q) * (double)rq * (double)rq;
-        arz += cw(c, q) * (double)rq * (double)zq;
+        const double wq = weight(c, flags, q);
+        arr += wq * (double)rq * (double)rq;
+        arz += wq * (double)rq * (double)zq;
     }
     double t = block_sum<NT>(arr, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -248,6 +268,34 @@ struct Result {
     int ax_timed = 0;
 };
 
+namespace {
+
+// One flag byte per point of an E-vector plan: kFree from the mask; kOwner on
+// points in no group and on the first member of every group.
+__global__ void k_flags_init(int64_t n, const uint8_t* __restrict__ mask, uint8_t* __restrict__ flags)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        flags[q] = (mask[q] ? kFree : 0) | kOwner;
+}
+
+__global__ void k_flags_groups(int64_t ngroups, const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
+                               uint8_t* __restrict__ flags)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups; g += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t m = off[g] + 1; m < off[g + 1]; m++) flags[mem[m]] &= static_cast<uint8_t>(~kOwner);
+}
+
+}  // namespace
+
+// Fills flags (n bytes) for the plan gs and the mask.
+inline nek_status build_flags(const nek_gs* gs, int64_t n, const uint8_t* mask, uint8_t* flags, cudaStream_t s)
+{
+    k_flags_init<<<stream_blocks(n), 256, 0, s>>>(n, mask, flags);
+    if (gs && gs->ngroups > 0)
+        k_flags_groups<<<stream_blocks(gs->ngroups), 256, 0, s>>>(gs->ngroups, gs->d_offsets, gs->d_members, flags);
+    return check_launch();
+}
+
 // Runs PCG from x = 0.  `ax(p, w, stream)` applies the element operator, which
 // gs then sums over shared nodes; with gs null, ax applies the assembled
 // operator itself.  c null weights every entry by 1.
@@ -256,7 +304,7 @@ struct Result {
 template <class V, class AxFn>
 nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, const V* minv, const V* f, V* x,
                const Buffers<V>& b, double tol, int max_iter, int check_every, bool time_ax, AxFn&& ax,
-               cudaStream_t s, Result* res)
+               cudaStream_t s, Result* res, const uint8_t* flags = nullptr)
 {
     const int nb = reduce_blocks(n);
     const int sb = stream_blocks(n);
@@ -264,7 +312,7 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
     std::vector<cudaEvent_t> ev;
     Scalars h{};
     nek_status st = NEK_OK;
-    k_init<V><<<nb, NT, 0, s>>>(n, c, mask, minv, f, x, b.r, b.z, b.p, b.parts);
+    k_init<V><<<nb, NT, 0, s>>>(n, c, mask, minv, f, x, b.r, b.z, b.p, b.parts, flags);
     k_init_finish<<<1, NT, 0, s>>>(b.parts, nb, tol, b.sc);
     launches += 2;
     if ((st = check_launch()) != NEK_OK) goto done;
@@ -279,9 +327,9 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
         if ((st = ax(b.p, b.w, s)) != NEK_OK) goto done;
         if (timed) cudaEventRecord(ev[2 * (it - 1) + 1], s);
         if ((st = dssum<V>(gs, b.w, s)) != NEK_OK) goto done;
-        k_pw<V><<<nb, NT, 0, s>>>(n, c, mask, b.p, b.w, b.parts, b.sc);
+        k_pw<V><<<nb, NT, 0, s>>>(n, c, mask, b.p, b.w, b.parts, b.sc, flags);
         k_alpha<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
-        k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.p, b.w, x, b.r, b.z, b.parts, b.sc);
+        k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.p, b.w, x, b.r, b.z, b.parts, b.sc, flags);
         k_beta<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
         launches += 6;
         if ((st = check_launch()) != NEK_OK) goto done;
