@@ -332,6 +332,17 @@ def mixed_block(torch, P, f, x, ws_bytes_hint=None):
         bpp = 8 + 6 * (4 if prec == nekax.PREC_F32 else 2)
         rec = {"ax_rel_err_vs_fp64": err, "ax_gdofs": P.npts / t_ax / 1e9, "ax_bytes_per_point": bpp,
                "ax_hbm_frac": P.npts * bpp / t_ax / 1e9 / hbm}
+        if prec != nekax.PREC_F32:  # the same operator with the D-contractions on the tensor cores
+            w2 = torch.empty_like(w32)
+            nekax.ax_lowp_tc(nelt, nx, prec, P.D, Glp, gsc, u32, w2)
+            e0.record()
+            for _ in range(10):
+                nekax.ax_lowp_tc(nelt, nx, prec, P.D, Glp, gsc, u32, w2)
+            e1.record()
+            e1.synchronize()
+            t_tc = e0.elapsed_time(e1) / 10 / 1e3
+            rec["tensor_core_form"] = {"ax_gdofs": P.npts / t_tc / 1e9,
+                                       "ax_rel_err_vs_fp64": float((w2.double() - w64).abs().max() / w64.abs().max())}
         for tol in (1e-8, 1e-10):
             torch.cuda.synchronize()
             t0 = time.perf_counter()

@@ -166,6 +166,15 @@ nek_status nek_geom_lowp(int64_t nelt, int nx, int precision, const double* G, v
 nek_status nek_ax_lowp(int64_t nelt, int nx, int precision, const double* D, const void* Glp, const float* gscale,
                        const float* u, float* w, void* stream);
 
+/* Same operator with the D-contractions on the tensor cores (precision
+ * NEK_PREC_BF16 or NEK_PREC_F16 only, else NEK_ERR_INVALID_ARG): each
+ * contraction is a 16 x 16 x 16 product per plane of the element (nx padded
+ * with zeros), mma.sync m16n8k16 with FP32 accumulation.  Same rounding points
+ * and the same error bound as nek_ax_lowp; only the order of the FP32
+ * additions inside a contraction differs.  Arguments as nek_ax_lowp. */
+nek_status nek_ax_lowp_tc(int64_t nelt, int nx, int precision, const double* D, const void* Glp,
+                          const float* gscale, const float* u, float* w, void* stream);
+
 /* Defect correction (iterative refinement) to FP64 accuracy: the residual
  * r = mask(f - dssum(AX x)), its norm, inner products and the update x += d are
  * FP64 on the GPU (AX through nek_ax_ff when Gff is given, else nek_ax); each

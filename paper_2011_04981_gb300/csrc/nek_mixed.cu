@@ -336,6 +336,9 @@ nek_status launch_lowp_t(int64_t nelt, int nx, const double* D, const void* Glp,
 
 }  // namespace
 
+nek_status launch_ax_lowp_tc(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
+                             const float* u, float* w, cudaStream_t s);
+
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
                           const float* u, float* w, cudaStream_t s)
 {
@@ -519,6 +522,19 @@ nek_status nek_geom_lowp(int64_t nelt, int nx, int precision, const double* G, v
         default: k_geom_lowp<__half><<<blocks, 256, 0, s>>>(nelt, n6, G, static_cast<__half*>(Glp), gscale); break;
     }
     return check_launch();
+}
+
+nek_status nek_ax_lowp_tc(int64_t nelt, int nx, int precision, const double* D, const void* Glp,
+                          const float* gscale, const float* u, float* w, void* stream)
+{
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt < 0 || (precision != NEK_PREC_BF16 && precision != NEK_PREC_F16)) return NEK_ERR_INVALID_ARG;
+    if (nelt == 0) return NEK_OK;
+    if (!D || !Glp || !gscale || !u || !w) return NEK_ERR_INVALID_ARG;
+    if (!is_aligned(D, 8) || !is_aligned(Glp, 4) || !is_aligned(u, 4) || !is_aligned(w, 4)) return NEK_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(float) * (size_t)nelt * nx * nx * nx;
+    if (ranges_overlap(u, bytes, w, bytes)) return NEK_ERR_INVALID_ARG;
+    return launch_ax_lowp_tc(precision, nelt, nx, D, Glp, gscale, u, w, static_cast<cudaStream_t>(stream));
 }
 
 nek_status nek_ax_lowp(int64_t nelt, int nx, int precision, const double* D, const void* Glp, const float* gscale,

@@ -207,3 +207,14 @@ def test_net_apply_bf16_rejects_bad_arguments(lib):
     assert L.nek_net_apply_bf16(-1, 8, 0x100, 0x100, 0x100, 0x100, 0x100, None) == nekax.ERR_INVALID_ARG
     assert L.nek_net_apply_bf16(4, 8, None, 0x100, 0x100, 0x100, 0x100, None) == nekax.ERR_INVALID_ARG
     assert L.nek_net_apply_bf16(0, 8, None, None, None, None, None, None) == nekax.OK
+
+
+def test_ax_lowp_tc_rejects_bad_arguments(lib):
+    L = lib
+    A = 0x1000
+    assert L.nek_ax_lowp_tc(4, 8, nekax.PREC_F32, A, A, A, A, A + 0x100000, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_lowp_tc(4, 17, nekax.PREC_BF16, A, A, A, A, A + 0x100000, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_ax_lowp_tc(-1, 8, nekax.PREC_BF16, A, A, A, A, A + 0x100000, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_lowp_tc(4, 8, nekax.PREC_F16, A, A, A, A, A, None) == nekax.ERR_INVALID_ARG  # u and w overlap
+    assert L.nek_ax_lowp_tc(4, 8, nekax.PREC_F16, A + 2, A, A, A, A + 0x100000, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_lowp_tc(0, 8, nekax.PREC_BF16, None, None, None, None, None, None) == nekax.OK

@@ -413,9 +413,10 @@ def test_epb_variants_bit_identical_and_tuner(impl, nx):
 UNIT_IN = {nekax.PREC_F32: 2.0 ** -24, nekax.PREC_BF16: 2.0 ** -8, nekax.PREC_F16: 2.0 ** -11}
 
 
-@pytest.mark.parametrize("prec", [nekax.PREC_F32, nekax.PREC_BF16, nekax.PREC_F16])
-@pytest.mark.parametrize("nx", [4, 8, 10, 13, 16])
-def test_ax_lowp_componentwise_bound(prec, nx):
+@pytest.mark.parametrize("prec,tc", [(nekax.PREC_F32, False), (nekax.PREC_BF16, False), (nekax.PREC_F16, False),
+                                     (nekax.PREC_BF16, True), (nekax.PREC_F16, True)])
+@pytest.mark.parametrize("nx", [2, 3, 4, 8, 10, 13, 16])
+def test_ax_lowp_componentwise_bound(prec, tc, nx):
     """|w - w_ref| <= C (u_in + (2 nx + 3) u_acc) w_abs with w_abs = AX(|D|, |G|, |u|) from the oracle, C = 4."""
     mesh = inputs.box_mesh(3, 2, 2, nx, perturb=0.15, seed=nx)
     xi, rho, D = ref.gll(nx)
@@ -428,9 +429,10 @@ def test_ax_lowp_componentwise_bound(prec, nx):
     nekax.geom_lowp(mesh.nelt, nx, prec, _t(G), Glp, gsc)
     ud = torch.from_numpy(u.astype(np.float32)).to(DEV)
     wd = torch.full_like(ud, float("nan"))
-    nekax.ax_lowp(mesh.nelt, nx, prec, _t(D), Glp, gsc, ud, wd)
+    (nekax.ax_lowp_tc if tc else nekax.ax_lowp)(mesh.nelt, nx, prec, _t(D), Glp, gsc, ud, wd)
     torch.cuda.synchronize()
     w = wd.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(w))
     u32 = u.astype(np.float32).astype(np.float64)
     w_ref = ref.ax(D, G, u32)
     w_abs = ref.ax(np.abs(D), np.abs(G), np.abs(u32))
