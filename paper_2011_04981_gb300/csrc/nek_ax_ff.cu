@@ -232,10 +232,31 @@ constexpr int ff_min_blocks()
 
 // Thread (e, i, j, g) computes the W-wide k-groups of planes [g*PPT, g*PPT + PPT)
 // of element e.
-template <int NX, int EPB, bool GATHER>
+// Load modes of the float-float kernels: plain w = AX u; GATHER: u is a
+// unique-node vector read through l2g (element point p reads u[l2g[p]]); SKIP:
+// a CTA whose elements all belong to finished problems (eprob: problem of each
+// element, pdone: one byte per problem) returns at once (batched solves).
+constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2;
+
+// True when every element of the CTA belongs to a finished problem.
+template <int MODE>
+__device__ __forceinline__ bool cta_skipped(const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone,
+                                            int64_t e0, int ne)
+{
+    if constexpr (MODE != kModeSkip) {
+        return false;
+    } else {
+        bool all_done = true;
+        for (int q = 0; q < ne; q++) all_done = all_done && pdone[eprob[e0 + q]] != 0;
+        return all_done;
+    }
+}
+
+template <int NX, int EPB, int MODE>
 __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ff(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
-            const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g)
+            const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g,
+            const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone)
 {
     using T = typename std::conditional<(NX % 2 == 0), float2, float>::type;
     using L = Lanes<T>;
@@ -257,6 +278,7 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
     const int tid = threadIdx.x;
     const int64_t e0 = (int64_t)blockIdx.x * EPB;
     const int ne = static_cast<int>(nelt - e0 < EPB ? nelt - e0 : EPB);
+    if (cta_skipped<MODE>(eprob, pdone, e0, ne)) return;  // uniform over the CTA, before any barrier
 
     for (int q = tid; q < N2; q += NT) {
         const float2 d = split_double(D[q]);
@@ -264,7 +286,7 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
         sDT[(q % NX) * NX + q / NX] = d;
     }
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
-    if constexpr (GATHER) {
+    if constexpr (MODE == kModeGather) {
         const int32_t* idx = l2g + e0 * N3;
         for (int q = tid; q < ne * N3; q += NT) sU[q] = split_double(__ldg(u + __ldg(idx + q)));
     } else {
@@ -438,10 +460,11 @@ constexpr size_t ffe_smem_bytes(int epb)
            sizeof(float2) * (size_t)epb * NX * NX * NX + sizeof(float) * (2 * NX + 4 * (size_t)epb + 4) + 16;
 }
 
-template <int NX, int EPB, bool GATHER>
+template <int NX, int EPB, int MODE>
 __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ffe(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
-             const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g)
+             const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g,
+             const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone)
 {
     static_assert(NX % 2 == 0 && NX <= 12, "even nx up to 12");
     using T = float2;
@@ -461,6 +484,7 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     const int tid = threadIdx.x;
     const int64_t e0 = (int64_t)blockIdx.x * EPB;
     const int ne = static_cast<int>(nelt - e0 < EPB ? nelt - e0 : EPB);
+    if (cta_skipped<MODE>(eprob, pdone, e0, ne)) return;  // uniform over the CTA, before any barrier
 
     for (int q = tid; q < N2; q += NT) {
         const int a = q / NX, b = q % NX;
@@ -476,11 +500,11 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
     {
         const double* src = u + e0 * N3;
-        const int32_t* idx = l2g + e0 * N3;  // used with GATHER only
+        const int32_t* idx = l2g + e0 * N3;  // used in the gather mode only
         for (int q = tid; q < ne * N3; q += NT) {
             const int el = q / N3, p = q - el * N3;
             const int k = p / N2, ji = p - k * N2;
-            const float2 v = split_double(GATHER ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
+            const float2 v = split_double(MODE == kModeGather ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
             float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
             dst[k & 1] = v.x;
             dst[2 + (k & 1)] = v.y;
@@ -641,9 +665,9 @@ constexpr size_t ff_variant_smem()
         return ff_smem_bytes<NX, EPB>();
 }
 
-template <int NX, int EPB, bool GATHER>
+template <int NX, int EPB, int MODE>
 nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                               cudaStream_t s, const int32_t* l2g)
+                               cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
 {
     constexpr size_t smem = ff_variant_smem<NX, EPB>();
     static bool configured = false;
@@ -651,32 +675,33 @@ nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, 
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
     if constexpr (ff_packed_layout<NX>()) {
         if (!configured) {
-            nek_status st = check_cuda(cudaFuncSetAttribute(k_ax_ffe<NX, EPB, GATHER>,
+            nek_status st = check_cuda(cudaFuncSetAttribute(k_ax_ffe<NX, EPB, MODE>,
                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             if (st != NEK_OK) return st;
             configured = true;
         }
-        k_ax_ffe<NX, EPB, GATHER><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
-            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g);
+        k_ax_ffe<NX, EPB, MODE><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
+            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone);
     } else {
         if (!configured) {
-            nek_status st = check_cuda(cudaFuncSetAttribute(k_ax_ff<NX, EPB, GATHER>,
+            nek_status st = check_cuda(cudaFuncSetAttribute(k_ax_ff<NX, EPB, MODE>,
                                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             if (st != NEK_OK) return st;
             configured = true;
         }
-        k_ax_ff<NX, EPB, GATHER><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
-            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g);
+        k_ax_ff<NX, EPB, MODE><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
+            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone);
     }
     return check_launch();
 }
 
 template <int NX, int EPB>
 nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                                cudaStream_t s, const int32_t* l2g)
+                                cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
 {
-    if (l2g) return launch_ax_ff_kernel<NX, EPB, true>(nelt, D, Gff, u, w, s, l2g);
-    return launch_ax_ff_kernel<NX, EPB, false>(nelt, D, Gff, u, w, s, nullptr);
+    if (l2g) return launch_ax_ff_kernel<NX, EPB, kModeGather>(nelt, D, Gff, u, w, s, l2g, nullptr, nullptr);
+    if (eprob && pdone) return launch_ax_ff_kernel<NX, EPB, kModeSkip>(nelt, D, Gff, u, w, s, nullptr, eprob, pdone);
+    return launch_ax_ff_kernel<NX, EPB, kModePlain>(nelt, D, Gff, u, w, s, nullptr, nullptr, nullptr);
 }
 
 template <int NX, int EPB>
@@ -687,24 +712,27 @@ constexpr bool ff_fits()
 
 template <int NX>
 nek_status launch_ax_ff_nx(int epb, int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                           cudaStream_t s, const int32_t* l2g)
+                           cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
 {
     if (epb <= 0) epb = ff_epb<NX>();
     switch (epb) {
         case 1:
-            if constexpr (ff_fits<NX, 1>()) return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s, l2g);
+            if constexpr (ff_fits<NX, 1>())
+                return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s, l2g, eprob, pdone);
             break;
         case 2:
-            if constexpr (ff_fits<NX, 2>()) return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s, l2g);
+            if constexpr (ff_fits<NX, 2>())
+                return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s, l2g, eprob, pdone);
             break;
         case 4:
-            if constexpr (ff_fits<NX, 4>()) return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s, l2g);
+            if constexpr (ff_fits<NX, 4>())
+                return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s, l2g, eprob, pdone);
             break;
         default:
             break;
     }
     if constexpr (ff_epb<NX>() != 1 && ff_epb<NX>() != 2 && ff_epb<NX>() != 4)
-        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s, l2g);
+        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s, l2g, eprob, pdone);
     return NEK_ERR_INVALID_ARG;
 }
 
@@ -719,24 +747,25 @@ __global__ void k_g_to_ff(int64_t npts, const double* __restrict__ G, float2* __
 }  // namespace
 
 nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
-                            double* w, cudaStream_t s, const int32_t* l2g)
+                            double* w, cudaStream_t s, const int32_t* l2g, const int32_t* eprob,
+                            const uint8_t* pdone)
 {
     switch (nx) {
-        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s, l2g);
-        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s, l2g);
+        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
 }
@@ -772,9 +801,9 @@ bool ax_ff_epb_fits(int nx, int epb)
 }
 
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
-                        cudaStream_t s, const int32_t* l2g)
+                        cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
 {
-    return launch_ax_ff_epb(tuned_epb(NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s, l2g);
+    return launch_ax_ff_epb(tuned_epb(NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s, l2g, eprob, pdone);
 }
 
 }  // namespace nek

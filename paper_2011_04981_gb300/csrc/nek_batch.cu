@@ -3,7 +3,9 @@
 // The problems (any element counts, nx in [2,16]) are laid out back to back in
 // one E-vector space, sorted by nx, so that
 //   - AX is one launch per nx group (elements are independent, the operator does
-//     not care which problem an element belongs to);
+//     not care which problem an element belongs to); with the float-float
+//     operator, CTAs whose elements all belong to finished problems return at
+//     once, so the operator's work follows the problems still iterating;
 //   - gather-scatter is one plan over all problems (each problem's global ids
 //     are offset past the previous problem's);
 //   - vector updates and inner products run over fixed-size chunks that never
@@ -219,18 +221,20 @@ __global__ void kb_beta(int nprob, const int* __restrict__ pch, const double* __
 }
 
 // per-problem convergence test, kept separate from kb_beta so the tolerance is
-// a kernel argument of the captured graph
-__global__ void kb_test(int nprob, double tol, BScal* __restrict__ sc, int* __restrict__ active)
+// a kernel argument of the captured graph; pdone[p] = 1 once p has finished
+// (the operator then skips p's elements)
+__global__ void kb_test(int nprob, double tol, BScal* __restrict__ sc, int* __restrict__ active,
+                        uint8_t* __restrict__ pdone)
 {
     const int pid = blockIdx.x * blockDim.x + threadIdx.x;
     if (pid >= nprob) return;
     BScal& s = sc[pid];
-    if (bhalted(s)) return;
-    if (tol > 0.0 && s.relres <= tol && s.it > 0) {
+    if (!bhalted(s) && tol > 0.0 && s.relres <= tol && s.it > 0) {
         s.done = 1;
         s.iters = s.it;
         atomicSub(active, 1);
     }
+    pdone[pid] = bhalted(s) ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(BT) kb_p(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
@@ -288,6 +292,7 @@ struct nek_batch {
     int64_t* d_ch_begin;  // nchunks+1
     int32_t* d_ch_prob;   // nchunks
     int* d_pch;           // nprob+1: chunk range of each problem
+    int32_t* d_elem_prob; // nelt_total: problem of each element
 };
 
 using namespace nek;
@@ -300,6 +305,7 @@ struct BLayout {
     double *r, *z, *p, *w, *minv, *parts;
     BScal* sc;
     int* active;
+    uint8_t* pdone;  // nprob: 1 once a problem has finished (converged or broken down)
     size_t bytes;
 };
 
@@ -321,6 +327,7 @@ BLayout b_layout(char* base, const nek_batch* b, bool need_minv)
     L.parts = reinterpret_cast<double*>(take(sizeof(double) * 2 * (size_t)b->nchunks));
     L.sc = reinterpret_cast<BScal*>(take(sizeof(BScal) * (size_t)b->nprob));
     L.active = reinterpret_cast<int*>(take(sizeof(int) * 4));
+    L.pdone = reinterpret_cast<uint8_t*>(take(static_cast<size_t>(b->nprob)));
     L.bytes = off;
     return L;
 }
@@ -353,6 +360,7 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
     b->d_ch_begin = nullptr;
     b->d_ch_prob = nullptr;
     b->d_pch = nullptr;
+    b->d_elem_prob = nullptr;
     nek_status st = NEK_OK;
     try {
         // global ids of all problems in one space: problem q's ids are offset by
@@ -361,6 +369,7 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
         std::vector<int64_t> ch_begin;
         std::vector<int32_t> ch_prob;
         std::vector<int> pch(1, 0);
+        std::vector<int32_t> elem_prob(static_cast<size_t>(nel));
         b->prob_pt0.assign(1, 0);
         int64_t pt = 0, goff = 0, el = 0;
         for (int q = 0; q < nprob; q++) {
@@ -377,6 +386,7 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
                 ch_prob.push_back(q);
             }
             pch.push_back(static_cast<int>(ch_begin.size()));
+            for (int64_t k = 0; k < nelt[q]; k++) elem_prob[el + k] = q;
             if (b->groups.empty() || b->groups.back().nx != nx[q]) b->groups.push_back(Group{nx[q], el, 0, pt, nullptr});
             b->groups.back().nelt += nelt[q];
             goff += gmax + 1;
@@ -390,6 +400,10 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
         if ((st = check_cuda(cudaMalloc(&b->d_ch_begin, sizeof(int64_t) * ch_begin.size()))) != NEK_OK) throw 3;
         if ((st = check_cuda(cudaMalloc(&b->d_ch_prob, sizeof(int32_t) * ch_prob.size()))) != NEK_OK) throw 3;
         if ((st = check_cuda(cudaMalloc(&b->d_pch, sizeof(int) * pch.size()))) != NEK_OK) throw 3;
+        if ((st = check_cuda(cudaMalloc(&b->d_elem_prob, sizeof(int32_t) * elem_prob.size()))) != NEK_OK) throw 3;
+        if ((st = check_cuda(cudaMemcpy(b->d_elem_prob, elem_prob.data(), sizeof(int32_t) * elem_prob.size(),
+                                        cudaMemcpyHostToDevice))) != NEK_OK)
+            throw 3;
         cudaMemcpy(b->d_ch_begin, ch_begin.data(), sizeof(int64_t) * ch_begin.size(), cudaMemcpyHostToDevice);
         cudaMemcpy(b->d_ch_prob, ch_prob.data(), sizeof(int32_t) * ch_prob.size(), cudaMemcpyHostToDevice);
         if ((st = check_cuda(cudaMemcpy(b->d_pch, pch.data(), sizeof(int) * pch.size(), cudaMemcpyHostToDevice))) !=
@@ -423,6 +437,7 @@ nek_status nek_batch_destroy(nek_batch* b)
     cudaFree(b->d_ch_begin);
     cudaFree(b->d_ch_prob);
     cudaFree(b->d_pch);
+    cudaFree(b->d_elem_prob);
     for (auto& g : b->groups) cudaFree(g.D);
     delete b;
     return NEK_OK;
@@ -492,7 +507,8 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
         for (const auto& g : b->groups) {
             const double* pg = L.p + g.pt0;
             double* wg = L.w + g.pt0;
-            nek_status sa = Gff ? launch_ax_ff(g.nelt, g.nx, g.D, Gff + g.pt0 * 12, pg, wg, ss)
+            nek_status sa = Gff ? launch_ax_ff(g.nelt, g.nx, g.D, Gff + g.pt0 * 12, pg, wg, ss, nullptr,
+                                               b->d_elem_prob + g.elem0, L.pdone)
                                 : launch_ax_fp64(g.nelt, g.nx, g.D, G + g.pt0 * 6, pg, wg, ss);
             if (sa != NEK_OK) return sa;
         }
@@ -503,7 +519,7 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
         kb_update<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, b->gs->d_c, mv, L.p, L.w, x, L.r, L.z, L.parts,
                                      L.sc);
         kb_beta<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, nc, L.sc, L.active);
-        kb_test<<<(np + 255) / 256, 256, 0, ss>>>(np, tol_rel, L.sc, L.active);
+        kb_test<<<(np + 255) / 256, 256, 0, ss>>>(np, tol_rel, L.sc, L.active, L.pdone);
         kb_p<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, L.z, L.p, L.sc);
         return check_launch();
     };
@@ -517,7 +533,8 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
     cudaMemsetAsync(L.active, 0, sizeof(int), s);
     kb_init<<<nc, BT, 0, s>>>(b->d_ch_begin, b->d_ch_prob, nc, b->gs->d_c, mask, mv, f, x, L.r, L.z, L.p, L.parts);
     kb_init_finish<<<wblocks, 256, 0, s>>>(np, b->d_pch, L.parts, nc, tol_rel, L.sc, L.active);
-    launches += 2;
+    kb_test<<<(np + 255) / 256, 256, 0, s>>>(np, tol_rel, L.sc, L.active, L.pdone);  // initial pdone
+    launches += 3;
     if ((st = check_launch()) != NEK_OK) goto done;
     // first iteration eagerly (configures every kernel before any capture)
     if (max_iter > 0) {
