@@ -126,13 +126,9 @@ nek_status launch_ax_variant(int64_t nelt, const double* D, const double* G, con
                              cudaStream_t s)
 {
     constexpr size_t smem = ax_smem_bytes<NX, EPB>();
-    static bool configured = false;
-    if (!configured) {
-        nek_status st = check_cuda(
-            cudaFuncSetAttribute(k_ax_fp64<NX, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (st != NEK_OK) return st;
-        configured = true;
-    }
+    static std::atomic<uint64_t> configured{0};
+    nek_status st = ensure_dyn_smem(k_ax_fp64<NX, EPB>, smem, configured);
+    if (st != NEK_OK) return st;
     const int64_t blocks = (nelt + EPB - 1) / EPB;
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
     k_ax_fp64<NX, EPB><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(nelt, D, G, u, w);

@@ -670,25 +670,17 @@ nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, 
                                cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
 {
     constexpr size_t smem = ff_variant_smem<NX, EPB>();
-    static bool configured = false;
+    static std::atomic<uint64_t> configured{0};
     const int64_t blocks = (nelt + EPB - 1) / EPB;
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
     if constexpr (ff_packed_layout<NX>()) {
-        if (!configured) {
-            nek_status st = check_cuda(cudaFuncSetAttribute(k_ax_ffe<NX, EPB, MODE>,
-                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            if (st != NEK_OK) return st;
-            configured = true;
-        }
+        nek_status st = ensure_dyn_smem(k_ax_ffe<NX, EPB, MODE>, smem, configured);
+        if (st != NEK_OK) return st;
         k_ax_ffe<NX, EPB, MODE><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
             nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone);
     } else {
-        if (!configured) {
-            nek_status st = check_cuda(cudaFuncSetAttribute(k_ax_ff<NX, EPB, MODE>,
-                                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            if (st != NEK_OK) return st;
-            configured = true;
-        }
+        nek_status st = ensure_dyn_smem(k_ax_ff<NX, EPB, MODE>, smem, configured);
+        if (st != NEK_OK) return st;
         k_ax_ff<NX, EPB, MODE><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
             nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone);
     }

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libnekax.so.
 #pragma once
 
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -17,6 +18,23 @@ inline nek_status check_cuda(cudaError_t e) { return e == cudaSuccess ? NEK_OK :
 inline nek_status check_launch() { return check_cuda(cudaGetLastError()); }
 
 inline bool is_aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device (the attribute belongs to the device's context: set
+// on one GPU only, a launch with more than 48 KB on another would fail).
+// done_mask: one bit per device ordinal (< 64), static storage of the caller.
+template <class K>
+nek_status ensure_dyn_smem(K kernel, size_t bytes, std::atomic<uint64_t>& done_mask)
+{
+    int dev = 0;
+    nek_status st = check_cuda(cudaGetDevice(&dev));
+    if (st != NEK_OK) return st;
+    const uint64_t bit = dev >= 0 && dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (bit && (done_mask.load(std::memory_order_acquire) & bit)) return NEK_OK;
+    st = check_cuda(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (st == NEK_OK && bit) done_mask.fetch_or(bit, std::memory_order_release);
+    return st;
+}
 inline bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb)
 {
     uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);

@@ -296,13 +296,9 @@ nek_status launch_lowp_nx(int64_t nelt, const double* D, const void* Glp, const 
 {
     constexpr int EPB = lp_epb(NX);
     constexpr size_t smem = lp_smem_bytes<NX, EPB>();
-    static bool configured = false;
-    if (!configured) {
-        nek_status st = check_cuda(
-            cudaFuncSetAttribute(k_ax_lowp<S, NX, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (st != NEK_OK) return st;
-        configured = true;
-    }
+    static std::atomic<uint64_t> configured{0};
+    nek_status st = ensure_dyn_smem(k_ax_lowp<S, NX, EPB>, smem, configured);
+    if (st != NEK_OK) return st;
     const int64_t blocks = (nelt + EPB - 1) / EPB;
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
     k_ax_lowp<S, NX, EPB><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(nelt, D, static_cast<const S*>(Glp),

@@ -275,14 +275,17 @@ nek_status launch_tc_nx(int64_t nelt, const double* D, const void* Glp, const fl
                         cudaStream_t s)
 {
     constexpr size_t smem = sizeof(TcSmemLp<S, NX>);
-    static int per_sm = 0;
+    static std::atomic<uint64_t> configured{0};
+    nek_status st0 = ensure_dyn_smem(k_ax_lowp_tc<S, NX>, smem, configured);
+    if (st0 != NEK_OK) return st0;
+    static std::atomic<int> per_sm_cache{0};  // resident CTAs per SM (the same on every GB300)
+    int per_sm = per_sm_cache.load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        nek_status st = check_cuda(
-            cudaFuncSetAttribute(k_ax_lowp_tc<S, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (st == NEK_OK)
-            st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_lowp_tc<S, NX>, 32 * TCW, smem));
-        if (st != NEK_OK) return st;
+        nek_status so =
+            check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ax_lowp_tc<S, NX>, 32 * TCW, smem));
+        if (so != NEK_OK) return so;
         if (per_sm < 1) per_sm = 1;
+        per_sm_cache.store(per_sm, std::memory_order_relaxed);
     }
     int dev = 0, sms = 0;
     nek_status st = check_cuda(cudaGetDevice(&dev));

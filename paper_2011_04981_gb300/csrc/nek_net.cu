@@ -509,11 +509,7 @@ __global__ void k_adam(int n, float* __restrict__ th, const float* __restrict__ 
     th[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
 }
 
-template <class K>
-nek_status set_smem(K kern, size_t bytes)
-{
-    return check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-}
+std::atomic<uint64_t> g_apply_conf{0}, g_fwd_conf{0}, g_bwd_conf{0};
 
 int grid_for(int64_t n) { return static_cast<int>(n < 152 * 2 ? n : 152 * 2); }
 
@@ -522,12 +518,8 @@ int grid_for(int64_t n) { return static_cast<int>(n < 152 * 2 ? n : 152 * 2); }
 nek_status launch_net_apply(int64_t nelt, const float* theta, const float* xin, const float* scale, const double* c,
                             double* z, cudaStream_t s)
 {
-    static bool conf = false;
-    if (!conf) {
-        nek_status st = set_smem(k_net_apply, sizeof(ApplySmem));
-        if (st != NEK_OK) return st;
-        conf = true;
-    }
+    nek_status st = ensure_dyn_smem(k_net_apply, sizeof(ApplySmem), g_apply_conf);
+    if (st != NEK_OK) return st;
     k_net_apply<<<static_cast<int>(nelt < 152 * 2 ? nelt : 152 * 2), NT_APPLY, sizeof(ApplySmem), s>>>(nelt, theta,
                                                                                                   xin, scale, c, z);
     return check_launch();
@@ -609,12 +601,8 @@ nek_status nek_net_forward_batch(int batch, const float* theta, const float* xin
     if (batch <= 0 || !theta || !xin || !y || !workspace || !is_aligned(workspace, 256)) return NEK_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TrainLayout L = train_layout(static_cast<char*>(workspace), batch);
-    static bool conf = false;
-    if (!conf) {
-        nek_status st = set_smem(k_net_fwd_train, sizeof(ApplySmem));
-        if (st != NEK_OK) return st;
-        conf = true;
-    }
+    nek_status st = ensure_dyn_smem(k_net_fwd_train, sizeof(ApplySmem), g_fwd_conf);
+    if (st != NEK_OK) return st;
     k_net_fwd_train<<<grid_for(batch), NP, sizeof(ApplySmem), s>>>(batch, theta, xin, L.h1, L.h2, y);
     return check_launch();
 }
@@ -626,13 +614,9 @@ nek_status nek_net_train_grad(int batch, const float* theta, const float* xin, c
         return NEK_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TrainLayout L = train_layout(static_cast<char*>(workspace), batch);
-    static bool conf = false;
-    if (!conf) {
-        nek_status st = set_smem(k_net_fwd_train, sizeof(ApplySmem));
-        if (st == NEK_OK) st = set_smem(k_net_bwd, sizeof(BwdSmem));
-        if (st != NEK_OK) return st;
-        conf = true;
-    }
+    nek_status st0 = ensure_dyn_smem(k_net_fwd_train, sizeof(ApplySmem), g_fwd_conf);
+    if (st0 == NEK_OK) st0 = ensure_dyn_smem(k_net_bwd, sizeof(BwdSmem), g_bwd_conf);
+    if (st0 != NEK_OK) return st0;
     k_net_fwd_train<<<grid_for(batch), NP, sizeof(ApplySmem), s>>>(batch, theta, xin, L.h1, L.h2, L.y);
     k_net_loss<<<grid_for(batch), NP, 0, s>>>(batch, L.y, target, L.dy, L.lossb);
     k_net_bwd<<<grid_for(batch), NP, sizeof(BwdSmem), s>>>(batch, theta, xin, L.h1, L.h2, L.dy, L.gs);
@@ -649,13 +633,9 @@ nek_status nek_net_train_grad_energy(int batch, const float* theta, const float*
         return NEK_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     TrainLayout L = train_layout(static_cast<char*>(workspace), batch);
-    static bool conf = false;
-    if (!conf) {
-        nek_status st = set_smem(k_net_fwd_train, sizeof(ApplySmem));
-        if (st == NEK_OK) st = set_smem(k_net_bwd, sizeof(BwdSmem));
-        if (st != NEK_OK) return st;
-        conf = true;
-    }
+    nek_status st0 = ensure_dyn_smem(k_net_fwd_train, sizeof(ApplySmem), g_fwd_conf);
+    if (st0 == NEK_OK) st0 = ensure_dyn_smem(k_net_bwd, sizeof(BwdSmem), g_bwd_conf);
+    if (st0 != NEK_OK) return st0;
     const int64_t n = (int64_t)batch * NP;
     k_net_fwd_train<<<grid_for(batch), NP, sizeof(ApplySmem), s>>>(batch, theta, xin, L.h1, L.h2, L.y);
     k_net_diff<<<pcg::stream_blocks(n), 256, 0, s>>>(n, L.y, target, L.d);

@@ -224,13 +224,9 @@ __global__ void __launch_bounds__(NT_TC, 2) k_net_apply_tc(int64_t nelt, const f
 nek_status launch_net_apply_tc(int64_t nelt, const float* theta, const float* xin, const float* scale,
                                const double* c, double* z, cudaStream_t s)
 {
-    static bool conf = false;
-    if (!conf) {
-        nek_status st = check_cuda(
-            cudaFuncSetAttribute(k_net_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem)));
-        if (st != NEK_OK) return st;
-        conf = true;
-    }
+    static std::atomic<uint64_t> configured{0};
+    nek_status st = ensure_dyn_smem(k_net_apply_tc, sizeof(TcSmem), configured);
+    if (st != NEK_OK) return st;
     const int grid = static_cast<int>(nelt < 152 * 2 ? nelt : 152 * 2);
     k_net_apply_tc<<<grid, NT_TC, sizeof(TcSmem), s>>>(nelt, theta, xin, scale, c, z);
     return check_launch();
