@@ -89,9 +89,12 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
+        import tempfile
+
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+        # raw samples go to a private temporary file; their summary goes into the JSON line
+        self.path = os.path.join(tempfile.mkdtemp(prefix="nek_clocks_"), "clocks_%d.csv" % gpu_index)
 
     def start(self):
         try:
