@@ -243,18 +243,27 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
     std::vector<double> hist;
     bool net = theta != nullptr;
     int it = 0, fell_back = 0, net_apps = 0, launches = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // one event pair per network application, read once at the end (no host
+    // synchronisation inside the loop for the timing)
+    std::vector<cudaEvent_t> nev;
     double net_ms = 0.0;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
 
     auto precondition = [&](int restart) -> nek_status {
         if (net) {
-            cudaEventRecord(e0, s);
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            const bool timed = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+            if (timed) {
+                nev.push_back(e0);
+                nev.push_back(e1);
+            } else {
+                if (e0) cudaEventDestroy(e0);
+                if (e1) cudaEventDestroy(e1);
+            }
+            if (timed) cudaEventRecord(e0, s);
             nek_status sp = launch_net_prep(nelt, L.r, mv, L.xin, L.scale, s);
             if (sp == NEK_OK) sp = launch_net_apply_tc(nelt, theta, L.xin, L.scale, gs->d_c, L.z, s);
             if (sp == NEK_OK) sp = pcg::dssum<double>(gs, L.z, s);
-            cudaEventRecord(e1, s);
+            if (timed) cudaEventRecord(e1, s);
             if (sp != NEK_OK) return sp;
             net_apps++;
             launches += 3;
@@ -265,15 +274,7 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
         kf_zdots<<<nb, NT, 0, s>>>(n, gs->d_c, mask, L.r, L.r_old, L.z, L.parts);
         kf_beta<<<1, NT, 0, s>>>(L.parts, nb, restart, L.sc);
         launches += 2;
-        nek_status sp = check_launch();
-        if (sp == NEK_OK && net) {
-            if ((sp = check_cuda(cudaEventSynchronize(e1))) == NEK_OK) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                net_ms += ms;
-            }
-        }
-        return sp;
+        return check_launch();
     };
 
     if (!minv) {
@@ -328,6 +329,13 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
         st = NEK_ERR_NOT_CONVERGED;
     }
 done:
+    if (!nev.empty() && cudaStreamSynchronize(s) == cudaSuccess) {
+        for (size_t q = 0; q + 1 < nev.size(); q += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, nev[q], nev[q + 1]) == cudaSuccess) net_ms += ms;
+        }
+    }
+    for (auto& e : nev) cudaEventDestroy(e);
     if (info) {
         info->iters = it;
         info->relres = h.relres;
@@ -336,8 +344,6 @@ done:
         info->net_ms = net_ms;
         info->kernel_launches = launches;
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
     if (!workspace) {
         cudaFreeAsync(ws, s);
         nek_status st2 = check_cuda(cudaStreamSynchronize(s));

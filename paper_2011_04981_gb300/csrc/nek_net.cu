@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(NP) k_net_prep(int64_t nelt, const double* __r
                                                  float* __restrict__ scale)
 {
     __shared__ double sh[2][NP / 32];
-    const int p = threadIdx.x;
+    __shared__ double sinv[2];
+    const int p = threadIdx.x, lane = p & 31;
     for (int64_t e = blockIdx.x; e < nelt; e += gridDim.x) {
         const double rv = r[e * NP + p];
         const double jv = minv[e * NP + p] * rv;
@@ -114,21 +115,31 @@ __global__ void __launch_bounds__(NP) k_net_prep(int64_t nelt, const double* __r
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
         }
-        if ((p & 31) == 0) {
+        if (lane == 0) {
             sh[0][p >> 5] = a;
             sh[1][p >> 5] = b;
         }
         __syncthreads();
-        double sa = 0.0, sb = 0.0;
-        for (int q = 0; q < NP / 32; q++) {
-            sa += sh[0][q];
-            sb += sh[1][q];
+        // one warp finishes the sums, the square roots and the reciprocals (FP64
+        // division and square root are long sequences on GB300's FP64 pipe)
+        if (p < 32) {
+            double sa = lane < NP / 32 ? sh[0][lane] : 0.0, sb = lane < NP / 32 ? sh[1][lane] : 0.0;
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            }
+            if (lane == 0) {
+                const double ra = sqrt(sa / NP), rb = sqrt(sb / NP);
+                sinv[0] = ra > 0.0 ? 1.0 / ra : 0.0;
+                sinv[1] = rb > 0.0 ? 1.0 / rb : 0.0;
+                scale[e] = (float)rb;
+            }
         }
         __syncthreads();
-        const double ra = sqrt(sa / NP), rb = sqrt(sb / NP);
-        xin[(e * CIN + 0) * NP + p] = ra > 0.0 ? (float)(rv / ra) : 0.f;
-        xin[(e * CIN + 1) * NP + p] = rb > 0.0 ? (float)(jv / rb) : 0.f;
-        if (p == 0) scale[e] = (float)rb;
+        xin[(e * CIN + 0) * NP + p] = (float)(rv * sinv[0]);
+        xin[(e * CIN + 1) * NP + p] = (float)(jv * sinv[1]);
+        __syncthreads();  // sh and sinv are reused by the next element
     }
 }
 

@@ -438,6 +438,7 @@ def test_ax_lowp_componentwise_bound(prec, tc, nx):
     w_abs = ref.ax(np.abs(D), np.abs(G), np.abs(u32))
     bound = 4.0 * (UNIT_IN[prec] + (2 * nx + 3) * 2.0 ** -24) * w_abs
     ratio = np.max(np.abs(w - w_ref) / bound)
+    print("lowp bound ratio: precision %d tensor-core %d nx %d: %.3f" % (prec, tc, nx, ratio))
     assert ratio <= 1.0, ratio
 
 
