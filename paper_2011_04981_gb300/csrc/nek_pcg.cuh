@@ -164,13 +164,28 @@ __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, c
     __shared__ double sh[NT / 32];
     if (halted(sc)) return;
     double acc = 0.0;
-    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
-        V wq = w[q];
-        if (!is_free(mask, flags, q)) {
-            wq = V(0);
-            w[q] = V(0);
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    if (flags) {
+        // unrolled: more loads in flight per thread for this memory-bound loop
+#pragma unroll 4
+        for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
+            const uint8_t fq = flags[q];
+            V wq = w[q];
+            if (!(fq & kFree)) {
+                wq = V(0);
+                w[q] = V(0);
+            }
+            if (fq & kOwner) acc += (double)p[q] * (double)wq;
         }
-        acc += weight(c, flags, q) * (double)p[q] * (double)wq;
+    } else {
+        for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
+            V wq = w[q];
+            if (!mask[q]) {
+                wq = V(0);
+                w[q] = V(0);
+            }
+            acc += cw(c, q) * (double)p[q] * (double)wq;
+        }
     }
     const double t = block_sum<NT>(acc, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -204,15 +219,31 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
     if (halted(sc)) return;
     const V alpha = (V)sc->alpha;
     double arr = 0.0, arz = 0.0;
-    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
-        x[q] = fma(alpha, p[q], x[q]);
-        const V rq = fma(-alpha, w[q], r[q]);
-        const V zq = minv[q] * rq;
-        r[q] = rq;
-        z[q] = zq;
-        const double wq = weight(c, flags, q);
-        arr += wq * (double)rq * (double)rq;
-        arz += wq * (double)rq * (double)zq;
+    const int64_t stride = (int64_t)gridDim.x * NT;
+    if (flags) {
+#pragma unroll 2
+        for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
+            x[q] = fma(alpha, p[q], x[q]);
+            const V rq = fma(-alpha, w[q], r[q]);
+            const V zq = minv[q] * rq;
+            r[q] = rq;
+            z[q] = zq;
+            if (flags[q] & kOwner) {
+                arr += (double)rq * (double)rq;
+                arz += (double)rq * (double)zq;
+            }
+        }
+    } else {
+        for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
+            x[q] = fma(alpha, p[q], x[q]);
+            const V rq = fma(-alpha, w[q], r[q]);
+            const V zq = minv[q] * rq;
+            r[q] = rq;
+            z[q] = zq;
+            const double wq = cw(c, q);
+            arr += wq * (double)rq * (double)rq;
+            arz += wq * (double)rq * (double)zq;
+        }
     }
     double t = block_sum<NT>(arr, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -247,6 +278,7 @@ __global__ void k_p(int64_t n, const V* __restrict__ z, V* __restrict__ p, const
 {
     if (halted(sc)) return;
     const V beta = (V)sc->beta;
+#pragma unroll 4
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
         p[q] = fma(beta, p[q], z[q]);
 }
