@@ -449,6 +449,7 @@ __global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict
 struct MixLayout {
     double *r, *w, *minv64;
     float *d, *minv, *c;
+    uint8_t* flags;  // owner / free byte per point for the inner solve's inner products
     pcg::Buffers<float> b;
     double* parts;
     MixScalars* ms;
@@ -474,6 +475,7 @@ MixLayout mix_layout(void* base_, int64_t n, bool need_minv)
     L.d = reinterpret_cast<float*>(take(v4));
     L.minv = reinterpret_cast<float*>(take(v4));
     L.c = reinterpret_cast<float*>(take(v4));
+    L.flags = reinterpret_cast<uint8_t*>(take(align256(std::max<int64_t>(n, 1))));
     L.b.r = reinterpret_cast<float*>(take(v4));
     L.b.z = reinterpret_cast<float*>(take(v4));
     L.b.p = reinterpret_cast<float*>(take(v4));
@@ -598,6 +600,8 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
     }
     k_d2f<<<sb, 256, 0, s>>>(n, mv, L.minv);
     k_d2f<<<sb, 256, 0, s>>>(n, gs->d_c, L.c);
+    if ((st = pcg::build_flags(gs, n, mask, L.flags, s)) != NEK_OK) goto done;
+    launches += gs->ngroups > 0 ? 2 : 1;
     k_mix_init<<<nb, NT, 0, s>>>(n, gs->d_c, mask, f, x, L.r, L.parts);
     k_mix_norm<<<1, NT, 0, s>>>(L.parts, nb, 1, L.ms);
     launches += 4;
@@ -621,7 +625,7 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
         {
             pcg::Result res;
             nek_status si = pcg::run<float>(gs, n, L.c, mask, L.minv, L.b.w, L.d, L.b, inner_tol, max_inner, 10,
-                                           false, ax_lo, s, &res);
+                                           false, ax_lo, s, &res, L.flags);
             inner_total += res.iters;
             launches += res.launches;
             if (si == NEK_ERR_BREAKDOWN || si == NEK_ERR_CUDA) {
