@@ -76,8 +76,8 @@ __device__ __forceinline__ void chunk_reduce(double (&acc)[NA], double* parts, i
 
 // x = 0; r = mask.f; z = minv r; p = z; partials <r,z>, <r,r>
 __global__ void __launch_bounds__(BT) kb_init(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
-                                              int nchunks, const double* __restrict__ c,
-                                              const uint8_t* __restrict__ mask, const double* __restrict__ minv,
+                                              int nchunks, const uint8_t* __restrict__ flags,
+                                              const double* __restrict__ minv,
                                               const double* __restrict__ f, double* __restrict__ x,
                                               double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
                                               double* __restrict__ parts)
@@ -85,14 +85,17 @@ __global__ void __launch_bounds__(BT) kb_init(const int64_t* __restrict__ ch_beg
     const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
     double acc[2] = {0.0, 0.0};
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
-        const double rq = mask[q] ? f[q] : 0.0;
+        const uint8_t fq = flags[q];
+        const double rq = (fq & pcg::kFree) ? f[q] : 0.0;
         const double zq = minv[q] * rq;
         x[q] = 0.0;
         r[q] = rq;
         z[q] = zq;
         p[q] = zq;
-        acc[0] += c[q] * rq * zq;
-        acc[1] += c[q] * rq * rq;
+        if (fq & pcg::kOwner) {  // owner copies: the 1/multiplicity-weighted sums
+            acc[0] += rq * zq;
+            acc[1] += rq * rq;
+        }
     }
     chunk_reduce<2>(acc, parts, nchunks);
 }
@@ -133,8 +136,8 @@ __global__ void kb_init_finish(int nprob, const int* __restrict__ pch, const dou
 
 // w <- mask.w ; partial <p,w>
 __global__ void __launch_bounds__(BT) kb_pw(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
-                                            int nchunks, const double* __restrict__ c,
-                                            const uint8_t* __restrict__ mask, const double* __restrict__ p,
+                                            int nchunks, const uint8_t* __restrict__ flags,
+                                            const double* __restrict__ p,
                                             double* __restrict__ w, double* __restrict__ parts,
                                             const BScal* __restrict__ sc)
 {
@@ -142,12 +145,13 @@ __global__ void __launch_bounds__(BT) kb_pw(const int64_t* __restrict__ ch_begin
     const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
     double acc[1] = {0.0};
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
+        const uint8_t fq = flags[q];
         double wq = w[q];
-        if (!mask[q]) {
+        if (!(fq & pcg::kFree)) {
             wq = 0.0;
             w[q] = 0.0;
         }
-        acc[0] += c[q] * p[q] * wq;
+        if (fq & pcg::kOwner) acc[0] += p[q] * wq;
     }
     chunk_reduce<1>(acc, parts, nchunks);
 }
@@ -175,7 +179,7 @@ __global__ void kb_alpha(int nprob, const int* __restrict__ pch, const double* _
 // x += alpha p; r -= alpha w; z = minv r; partials <r,r>, <r,z>
 __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_begin,
                                                 const int32_t* __restrict__ ch_prob, int nchunks,
-                                                const double* __restrict__ c, const double* __restrict__ minv,
+                                                const uint8_t* __restrict__ flags, const double* __restrict__ minv,
                                                 const double* __restrict__ p, const double* __restrict__ w,
                                                 double* __restrict__ x, double* __restrict__ r,
                                                 double* __restrict__ z, double* __restrict__ parts,
@@ -192,8 +196,10 @@ __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_b
         const double zq = minv[q] * rq;
         r[q] = rq;
         z[q] = zq;
-        acc[0] += c[q] * rq * rq;
-        acc[1] += c[q] * rq * zq;
+        if (flags[q] & pcg::kOwner) {
+            acc[0] += rq * rq;
+            acc[1] += rq * zq;
+        }
     }
     chunk_reduce<2>(acc, parts, nchunks);
 }
@@ -306,6 +312,7 @@ struct BLayout {
     BScal* sc;
     int* active;
     uint8_t* pdone;  // nprob: 1 once a problem has finished (converged or broken down)
+    uint8_t* flags;  // npts: owner / free byte per point (inner-product weights and the mask)
     size_t bytes;
 };
 
@@ -328,6 +335,7 @@ BLayout b_layout(char* base, const nek_batch* b, bool need_minv)
     L.sc = reinterpret_cast<BScal*>(take(sizeof(BScal) * (size_t)b->nprob));
     L.active = reinterpret_cast<int*>(take(sizeof(int) * 4));
     L.pdone = reinterpret_cast<uint8_t*>(take(static_cast<size_t>(b->nprob)));
+    L.flags = reinterpret_cast<uint8_t*>(take(static_cast<size_t>(b->npts)));
     L.bytes = off;
     return L;
 }
@@ -514,9 +522,9 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
         }
         nek_status sd = pcg::dssum<double>(b->gs, L.w, ss);
         if (sd != NEK_OK) return sd;
-        kb_pw<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, b->gs->d_c, mask, L.p, L.w, L.parts, L.sc);
+        kb_pw<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, L.p, L.w, L.parts, L.sc);
         kb_alpha<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, L.sc, L.active);
-        kb_update<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, b->gs->d_c, mv, L.p, L.w, x, L.r, L.z, L.parts,
+        kb_update<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, L.p, L.w, x, L.r, L.z, L.parts,
                                      L.sc);
         kb_beta<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, nc, L.sc, L.active);
         kb_test<<<(np + 255) / 256, 256, 0, ss>>>(np, tol_rel, L.sc, L.active, L.pdone);
@@ -531,7 +539,9 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
         launches += static_cast<int>(b->groups.size()) + 2;
     }
     cudaMemsetAsync(L.active, 0, sizeof(int), s);
-    kb_init<<<nc, BT, 0, s>>>(b->d_ch_begin, b->d_ch_prob, nc, b->gs->d_c, mask, mv, f, x, L.r, L.z, L.p, L.parts);
+    if ((st = pcg::build_flags(b->gs, b->npts, mask, L.flags, s)) != NEK_OK) goto done;
+    launches += b->gs->ngroups > 0 ? 2 : 1;
+    kb_init<<<nc, BT, 0, s>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, f, x, L.r, L.z, L.p, L.parts);
     kb_init_finish<<<wblocks, 256, 0, s>>>(np, b->d_pch, L.parts, nc, tol_rel, L.sc, L.active);
     kb_test<<<(np + 255) / 256, 256, 0, s>>>(np, tol_rel, L.sc, L.active, L.pdone);  // initial pdone
     launches += 3;
