@@ -234,8 +234,8 @@ nek_status nek_gs_inv_multiplicity(const nek_gs* gs, double* c, void* stream);
 nek_status nek_mask(int64_t n, const uint8_t* mask, double* v, void* stream);
 
 /* ----------------------------------------------------- Jacobi / vectors ---
- * Jacobi preconditioner (the "simple preconditioner" of Section II-B read as
- * the inverse assembled diagonal): minv = mask ? 1/dssum(diag_e(A)) : 0.
+ * Jacobi preconditioner (Section II-B's basic preconditioner, read as the
+ * inverse assembled diagonal): minv = mask ? 1/dssum(diag_e(A)) : 0.
  * All pointers device; async. */
 nek_status nek_jacobi_minv(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
                            const uint8_t* mask, double* minv, void* stream);

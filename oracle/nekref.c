@@ -11,7 +11,7 @@
  * architectures" (arXiv 2011.04981).  Section II-B, Listing 1 gives the
  * element operator ax / ax_e / local_grad3; the same section states that the
  * CG iteration is vector operations + this operator + nearest-neighbour
- * exchange + global reductions, with a "simple preconditioner".  Everything
+ * exchange + global reductions, with a basic preconditioner.  Everything
  * the paper leaves open is read as the standard spectral-element definition;
  * each function says which reading it takes.
  *
@@ -147,7 +147,7 @@ int ref_ax(int64_t nelt, int nx, const double* D, const double* G, const double*
     return REF_OK;
 }
 
-/* ---- gather-scatter (the "nearest-neighbour communication" of Section II-B) ----
+/* ---- gather-scatter (the exchange with neighbouring elements of Section II-B) ----
  * Reading: direct stiffness summation.  Every local node whose global id is
  * shared by m >= 2 local nodes belongs to one group; dssum replaces each member
  * by the group sum.  Groups are listed by ascending global id and members by
@@ -252,7 +252,7 @@ void ref_diag_local(int64_t nelt, int nx, const double* D, const double* G, doub
     }
 }
 
-/* Jacobi preconditioner ("simple preconditioner" of Section II-B, read as the
+/* Jacobi preconditioner (the basic preconditioner of Section II-B, read as the
  * inverse of the assembled diagonal): minv = 1/dssum(diag_local), 0 on masked
  * nodes. */
 int ref_jacobi_minv(int64_t nelt, int nx, const double* D, const double* G, int64_t ngroups,

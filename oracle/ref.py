@@ -12,7 +12,7 @@ Functions and the passages they follow (arXiv 2011.04981):
 * ``ax``             -- ax / ax_e / local_grad3 / local_grad3_t, Section II-B, Listing 1
 * ``element_matrix`` -- dense element operator from the bilinear form (brute force of Listing 1)
 * ``gs_build``/``dssum`` -- nearest-neighbour exchange of Section II-B read as direct stiffness summation
-* ``jacobi_minv``    -- "simple preconditioner" of Section II-B read as Jacobi
+* ``jacobi_minv``    -- the basic preconditioner of Section II-B, read as Jacobi
 * ``pcg``            -- the CG solve of Section II-B
 """
 from __future__ import annotations

@@ -9,8 +9,8 @@
 // Kernel layout: a CTA owns EPB elements and has nx*nx*EPB threads; thread
 // (e, i, j) keeps the k-line u(i,j,:) and the t-results wt(i,j,:) in registers
 // and walks the k planes.  The u block of every element is staged in shared
-// memory once (one coalesced read of u, the paper's "read each grid point of u
-// only once" on the FPGA becomes one pass through HBM here) so that the r- and
+// memory once (one coalesced read of u: the FPGA design's single read of every
+// grid point of u becomes one pass through HBM here) so that the r- and
 // s-contractions read it from shared memory in their own order, which is what
 // the per-matmul reorder buffers of the FPGA design (Section III) achieve.
 // ws goes to shared memory as it is produced; wr is kept in registers until
