@@ -220,7 +220,9 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ native arm
-def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10, tune=False):
+def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=20, tune=False):
+    """Standalone AX at each nx on a 32^3-element box: median over `reps` launches, each timed with its own
+    CUDA events (inputs far above L2, so no flush is needed)."""
     from paper_2011_04981_gb300 import inputs, nekax, perfmodel
     from paper_2011_04981_gb300.problem import DeviceProblem
 
@@ -241,14 +243,15 @@ def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=10, tune=False):
                 epb, _ = nekax.tune_ax(impl, mesh.nelt, nx, P.D, P.Gff if name == "ff" else P.G, u, w)
             for _ in range(3):
                 fn(u, w)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(reps)]
             torch.cuda.synchronize()
-            e0.record(s)
-            for _ in range(reps):
+            for a, b in evs:
+                a.record(s)
                 fn(u, w)
-            e1.record(s)
-            e1.synchronize()
-            t = e0.elapsed_time(e1) / reps / 1e3
+                b.record(s)
+            evs[-1][1].synchronize()
+            t = statistics.median(a.elapsed_time(b) for a, b in evs) / 1e3
             g = mesh.npts / t / 1e9
             res[name] = {"gdofs": g, "ms": t * 1e3, "gflops": g * perfmodel.ax_flops_per_point(nx),
                          "hbm_frac": g * 64 / hbm,
