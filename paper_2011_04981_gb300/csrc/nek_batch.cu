@@ -35,6 +35,7 @@ constexpr int BT = 256;       // threads per chunk block
 struct BScal {
     double rz, pw, alpha, beta, rr, bnorm, relres;
     int done, status, iters, it;
+    int xpend;  // this iteration's x += alpha p is still to be applied (kb_p)
 };
 
 struct Group {
@@ -74,12 +75,12 @@ __device__ __forceinline__ void chunk_reduce(double (&acc)[NA], double* parts, i
     }
 }
 
-// x = 0; r = mask.f; z = minv r; p = z; partials <r,z>, <r,r>
+// x = 0; r = mask.f; p = z = minv r; partials <r,z>, <r,r>
 __global__ void __launch_bounds__(BT) kb_init(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
                                               int nchunks, const uint8_t* __restrict__ flags,
                                               const double* __restrict__ minv,
                                               const double* __restrict__ f, double* __restrict__ x,
-                                              double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
+                                              double* __restrict__ r, double* __restrict__ p,
                                               double* __restrict__ parts)
 {
     const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
@@ -90,7 +91,6 @@ __global__ void __launch_bounds__(BT) kb_init(const int64_t* __restrict__ ch_beg
         const double zq = minv[q] * rq;
         x[q] = 0.0;
         r[q] = rq;
-        z[q] = zq;
         p[q] = zq;
         if (fq & pcg::kOwner) {  // owner copies: the 1/multiplicity-weighted sums
             acc[0] += rq * zq;
@@ -146,12 +146,13 @@ __global__ void __launch_bounds__(BT) kb_pw(const int64_t* __restrict__ ch_begin
     double acc[1] = {0.0};
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
         const uint8_t fq = flags[q];
+        const double pq = p[q];  // loaded whatever the flags say, so it is not held back behind them
         double wq = w[q];
         if (!(fq & pcg::kFree)) {
             wq = 0.0;
             w[q] = 0.0;
         }
-        if (fq & pcg::kOwner) acc[0] += p[q] * wq;
+        if (fq & pcg::kOwner) acc[0] += pq * wq;
     }
     chunk_reduce<1>(acc, parts, nchunks);
 }
@@ -160,7 +161,11 @@ __global__ void kb_alpha(int nprob, const int* __restrict__ pch, const double* _
                          BScal* __restrict__ sc, int* __restrict__ active)
 {
     const int pid = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (pid >= nprob || bhalted(sc[pid])) return;
+    if (pid >= nprob) return;
+    if (bhalted(sc[pid])) {
+        if ((threadIdx.x & 31) == 0) sc[pid].xpend = 0;
+        return;
+    }
     const double pw = prob_sum(parts, pch[pid], pch[pid + 1]);
     if ((threadIdx.x & 31) == 0) {
         BScal& s = sc[pid];
@@ -169,21 +174,23 @@ __global__ void kb_alpha(int nprob, const int* __restrict__ pch, const double* _
         if (!(pw > 0.0) || !isfinite(pw)) {
             s.status = NEK_ERR_BREAKDOWN;
             s.iters = s.it;
+            s.xpend = 0;
             atomicSub(active, 1);
         } else {
             s.alpha = s.rz / pw;
+            s.xpend = 1;
         }
     }
 }
 
-// x += alpha p; r -= alpha w; z = minv r; partials <r,r>, <r,z>
+// r -= alpha w; partials <r,r>, <r,z> with z = minv r (not stored); x and p
+// are updated by kb_p, so p is read by one vector kernel only (the same split
+// as the single-problem solve, with the same results)
 __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_begin,
                                                 const int32_t* __restrict__ ch_prob, int nchunks,
                                                 const uint8_t* __restrict__ flags, const double* __restrict__ minv,
-                                                const double* __restrict__ p, const double* __restrict__ w,
-                                                double* __restrict__ x, double* __restrict__ r,
-                                                double* __restrict__ z, double* __restrict__ parts,
-                                                const BScal* __restrict__ sc)
+                                                const double* __restrict__ w, double* __restrict__ r,
+                                                double* __restrict__ parts, const BScal* __restrict__ sc)
 {
     const BScal& s = sc[ch_prob[blockIdx.x]];
     if (bhalted(s)) return;
@@ -191,11 +198,9 @@ __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_b
     const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
     double acc[2] = {0.0, 0.0};
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
-        x[q] = fma(alpha, p[q], x[q]);
         const double rq = fma(-alpha, w[q], r[q]);
         const double zq = minv[q] * rq;
         r[q] = rq;
-        z[q] = zq;
         if (flags[q] & pcg::kOwner) {
             acc[0] += rq * rq;
             acc[1] += rq * zq;
@@ -243,15 +248,26 @@ __global__ void kb_test(int nprob, double tol, BScal* __restrict__ sc, int* __re
     pdone[pid] = bhalted(s) ? 1 : 0;
 }
 
+// x += alpha p (old p) while the problem's x update is pending; p = minv r +
+// beta p while it goes on
 __global__ void __launch_bounds__(BT) kb_p(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
-                                           const double* __restrict__ z, double* __restrict__ p,
+                                           const double* __restrict__ minv, const double* __restrict__ r,
+                                           double* __restrict__ x, double* __restrict__ p,
                                            const BScal* __restrict__ sc)
 {
     const BScal& s = sc[ch_prob[blockIdx.x]];
-    if (bhalted(s)) return;
-    const double beta = s.beta;
+    const bool do_x = s.xpend != 0, do_p = !bhalted(s);
+    const double alpha = s.alpha, beta = s.beta;
     const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
-    for (int64_t q = a + threadIdx.x; q < b; q += BT) p[q] = fma(beta, p[q], z[q]);
+    if (do_x && do_p) {
+        for (int64_t q = a + threadIdx.x; q < b; q += BT) {
+            const double pq = p[q];
+            x[q] = fma(alpha, pq, x[q]);
+            p[q] = fma(beta, pq, minv[q] * r[q]);
+        }
+    } else if (do_x) {
+        for (int64_t q = a + threadIdx.x; q < b; q += BT) x[q] = fma(alpha, p[q], x[q]);
+    }
 }
 
 __global__ void k_bdiag_local(int64_t nelt, int nx, const double* __restrict__ D, const double* __restrict__ G,
@@ -308,7 +324,7 @@ namespace {
 inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct BLayout {
-    double *r, *z, *p, *w, *minv, *parts;
+    double *r, *p, *w, *minv, *parts;
     BScal* sc;
     int* active;
     uint8_t* pdone;  // nprob: 1 once a problem has finished (converged or broken down)
@@ -327,7 +343,6 @@ BLayout b_layout(char* base, const nek_batch* b, bool need_minv)
     };
     const size_t v = sizeof(double) * std::max<int64_t>(b->npts, 1);
     L.r = reinterpret_cast<double*>(take(v));
-    L.z = reinterpret_cast<double*>(take(v));
     L.p = reinterpret_cast<double*>(take(v));
     L.w = reinterpret_cast<double*>(take(v));
     L.minv = need_minv ? reinterpret_cast<double*>(take(v)) : nullptr;
@@ -524,11 +539,10 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
         if (sd != NEK_OK) return sd;
         kb_pw<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, L.p, L.w, L.parts, L.sc);
         kb_alpha<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, L.sc, L.active);
-        kb_update<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, L.p, L.w, x, L.r, L.z, L.parts,
-                                     L.sc);
+        kb_update<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, L.w, L.r, L.parts, L.sc);
         kb_beta<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, nc, L.sc, L.active);
         kb_test<<<(np + 255) / 256, 256, 0, ss>>>(np, tol_rel, L.sc, L.active, L.pdone);
-        kb_p<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, L.z, L.p, L.sc);
+        kb_p<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, mv, L.r, x, L.p, L.sc);
         return check_launch();
     };
     const int per_iter_launches = static_cast<int>(b->groups.size()) + 7;
@@ -541,7 +555,7 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
     cudaMemsetAsync(L.active, 0, sizeof(int), s);
     if ((st = pcg::build_flags(b->gs, b->npts, mask, L.flags, s)) != NEK_OK) goto done;
     launches += b->gs->ngroups > 0 ? 2 : 1;
-    kb_init<<<nc, BT, 0, s>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, f, x, L.r, L.z, L.p, L.parts);
+    kb_init<<<nc, BT, 0, s>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, f, x, L.r, L.p, L.parts);
     kb_init_finish<<<wblocks, 256, 0, s>>>(np, b->d_pch, L.parts, nc, tol_rel, L.sc, L.active);
     kb_test<<<(np + 255) / 256, 256, 0, s>>>(np, tol_rel, L.sc, L.active, L.pdone);  // initial pdone
     launches += 3;

@@ -90,8 +90,8 @@ size_t nek_cg_workspace_bytes(int64_t nelt, int nx, int need_minv)
     if (nelt < 0 || nx < kMinNx || nx > kMaxNx) return 0;
     const size_t n = (size_t)nelt * nx * nx * nx;
     const size_t vec = pcg::align256(sizeof(double) * std::max<size_t>(n, 1));
-    // r, z, p, w, [minv], point flags (1 byte each), reduction partials, scalars
-    return vec * (need_minv ? 5 : 4) + pcg::align256(std::max<size_t>(n, 1)) +
+    // r, p, w, [minv], point flags (1 byte each), reduction partials, scalars
+    return vec * (need_minv ? 4 : 3) + pcg::align256(std::max<size_t>(n, 1)) +
            pcg::align256(sizeof(double) * 2 * kMaxReduceBlocks) + pcg::align256(sizeof(pcg::Scalars));
 }
 
@@ -134,10 +134,9 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
     char* base = static_cast<char*>(ws);
     pcg::Buffers<double> b;
     b.r = reinterpret_cast<double*>(base);
-    b.z = reinterpret_cast<double*>(base + vec);
-    b.p = reinterpret_cast<double*>(base + 2 * vec);
-    b.w = reinterpret_cast<double*>(base + 3 * vec);
-    size_t off = 4 * vec;
+    b.p = reinterpret_cast<double*>(base + vec);
+    b.w = reinterpret_cast<double*>(base + 2 * vec);
+    size_t off = 3 * vec;
     double* mv = const_cast<double*>(minv);
     if (!minv) {
         mv = reinterpret_cast<double*>(base + off);

@@ -257,7 +257,7 @@ size_t nek_lvec_cg_workspace_bytes(const nek_lvec* lv)
 {
     if (!lv) return 0;
     const size_t vec = pcg::align256(sizeof(double) * std::max<int64_t>(lv->nl, 1));
-    return 4 * vec + pcg::align256(sizeof(double) * std::max<int64_t>(lv->npts, 1)) +
+    return 3 * vec + pcg::align256(sizeof(double) * std::max<int64_t>(lv->npts, 1)) +
            pcg::align256(sizeof(double) * 2 * kMaxReduceBlocks) + pcg::align256(sizeof(pcg::Scalars));
 }
 
@@ -293,11 +293,10 @@ nek_status nek_lvec_cg_solve(const nek_lvec* lv, int64_t nelt, int nx, const dou
     char* base = static_cast<char*>(ws);
     pcg::Buffers<double> b;
     b.r = reinterpret_cast<double*>(base);
-    b.z = reinterpret_cast<double*>(base + vec);
-    b.p = reinterpret_cast<double*>(base + 2 * vec);
-    b.w = reinterpret_cast<double*>(base + 3 * vec);
-    double* wE = reinterpret_cast<double*>(base + 4 * vec);
-    size_t off = 4 * vec + pcg::align256(sizeof(double) * lv->npts);
+    b.p = reinterpret_cast<double*>(base + vec);
+    b.w = reinterpret_cast<double*>(base + 2 * vec);
+    double* wE = reinterpret_cast<double*>(base + 3 * vec);
+    size_t off = 3 * vec + pcg::align256(sizeof(double) * lv->npts);
     b.parts = reinterpret_cast<double*>(base + off);
     off += pcg::align256(sizeof(double) * 2 * kMaxReduceBlocks);
     b.sc = reinterpret_cast<pcg::Scalars*>(base + off);

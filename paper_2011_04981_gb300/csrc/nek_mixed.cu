@@ -477,7 +477,6 @@ MixLayout mix_layout(void* base_, int64_t n, bool need_minv)
     L.c = reinterpret_cast<float*>(take(v4));
     L.flags = reinterpret_cast<uint8_t*>(take(align256(std::max<int64_t>(n, 1))));
     L.b.r = reinterpret_cast<float*>(take(v4));
-    L.b.z = reinterpret_cast<float*>(take(v4));
     L.b.p = reinterpret_cast<float*>(take(v4));
     L.b.w = reinterpret_cast<float*>(take(v4));
     L.b.parts = reinterpret_cast<double*>(take(align256(sizeof(double) * 2 * kMaxReduceBlocks)));

@@ -7,6 +7,13 @@
 //   w = AX p (caller's operator) ; w = dssum(w) ; w = mask.w ; pw = <p,w>_c
 //   alpha = rz/pw ; x += alpha p ; r -= alpha w ; z = minv r ; rr = <r,r>_c ;
 //   rz' = <r,z>_c ; stop if sqrt(rr)/||b|| <= tol ; beta = rz'/rz ; p = z + beta p
+// The kernels split this so that p is read by one vector kernel only:
+// k_update does r -= alpha w and the two sums (z = minv r formed on the fly,
+// never stored); k_p then does x += alpha p with the old p and p = minv r +
+// beta p.  Every value is computed by the same operations as in the order
+// above, so the split changes no result, and it saves 8 bytes per point and
+// iteration (the second read of p; z's write and read become reads of minv
+// and r).
 // Reductions use a fixed grid per length and a fixed shuffle tree, so results
 // are deterministic.  Once the residual test passes, or a breakdown is seen, a
 // device flag makes every later update kernel of the call return at once.
@@ -35,6 +42,7 @@ struct Scalars {
     int status;     // NEK_OK or NEK_ERR_BREAKDOWN
     int iters;      // iterations completed when done/status was set
     int it;         // iterations executed so far
+    int xpend;      // this iteration's x += alpha p is still to be applied (k_p)
 };
 
 constexpr int NT = kReduceThreads;
@@ -102,12 +110,12 @@ nek_status dssum(const nek_gs* gs, V* v, cudaStream_t s)
     return check_launch();
 }
 
-// x = 0, r = mask.f, z = minv r, p = z; partials of <r,z>_c and <r,r>_c.
+// x = 0, r = mask.f, p = z = minv r; partials of <r,z>_c and <r,r>_c.
 template <class V>
 __global__ void __launch_bounds__(NT) k_init(int64_t n, const V* __restrict__ c, const uint8_t* __restrict__ mask,
                                               const V* __restrict__ minv, const V* __restrict__ f, V* __restrict__ x,
-                                              V* __restrict__ r, V* __restrict__ z, V* __restrict__ p,
-                                              double* __restrict__ parts, const uint8_t* __restrict__ flags)
+                                              V* __restrict__ r, V* __restrict__ p, double* __restrict__ parts,
+                                              const uint8_t* __restrict__ flags)
 {
     __shared__ double sh[NT / 32];
     double arz = 0.0, arr = 0.0;
@@ -116,7 +124,6 @@ __global__ void __launch_bounds__(NT) k_init(int64_t n, const V* __restrict__ c,
         const V zq = minv[q] * rq;
         x[q] = V(0);
         r[q] = rq;
-        z[q] = zq;
         p[q] = zq;
         const double wq = weight(c, flags, q);
         arz += wq * (double)rq * (double)zq;
@@ -142,6 +149,7 @@ __global__ void __launch_bounds__(NT) k_init_finish(const double* __restrict__ p
         sc->it = 0;
         sc->iters = 0;
         sc->alpha = sc->beta = sc->pw = 0.0;
+        sc->xpend = 0;
         sc->status = NEK_OK;
         sc->done = 0;
         sc->relres = 0.0;
@@ -170,12 +178,13 @@ __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, c
 #pragma unroll 4
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
             const uint8_t fq = flags[q];
+            const V pq = p[q];  // loaded whatever the flags say, so it is not held back behind them
             V wq = w[q];
             if (!(fq & kFree)) {
                 wq = V(0);
                 w[q] = V(0);
             }
-            if (fq & kOwner) acc += (double)p[q] * (double)wq;
+            if (fq & kOwner) acc += (double)pq * (double)wq;
         }
     } else {
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
@@ -194,7 +203,10 @@ __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, c
 __global__ void __launch_bounds__(NT) k_alpha(const double* __restrict__ parts, int nb, Scalars* sc)
 {
     __shared__ double sh[NT / 32];
-    if (halted(sc)) return;
+    if (halted(sc)) {
+        if (threadIdx.x == 0) sc->xpend = 0;
+        return;
+    }
     const double pw = sum_partials<NT>(parts, nb, sh);
     if (threadIdx.x == 0) {
         sc->it += 1;
@@ -202,17 +214,18 @@ __global__ void __launch_bounds__(NT) k_alpha(const double* __restrict__ parts, 
         if (!(pw > 0.0) || !isfinite(pw)) {
             sc->status = NEK_ERR_BREAKDOWN;
             sc->iters = sc->it;
+            sc->xpend = 0;
         } else {
             sc->alpha = sc->rz / pw;
+            sc->xpend = 1;
         }
     }
 }
 
-// x += alpha p; r -= alpha w; z = minv r; partials of <r,r>_c and <r,z>_c
+// r -= alpha w; partials of <r,r>_c and <r,z>_c with z = minv r (not stored)
 template <class V>
 __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ c, const V* __restrict__ minv,
-                                                const V* __restrict__ p, const V* __restrict__ w, V* __restrict__ x,
-                                                V* __restrict__ r, V* __restrict__ z, double* __restrict__ parts,
+                                                const V* __restrict__ w, V* __restrict__ r, double* __restrict__ parts,
                                                 const Scalars* __restrict__ sc, const uint8_t* __restrict__ flags)
 {
     __shared__ double sh[NT / 32];
@@ -221,13 +234,11 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
     double arr = 0.0, arz = 0.0;
     const int64_t stride = (int64_t)gridDim.x * NT;
     if (flags) {
-#pragma unroll 2
+#pragma unroll 4
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
-            x[q] = fma(alpha, p[q], x[q]);
             const V rq = fma(-alpha, w[q], r[q]);
             const V zq = minv[q] * rq;
             r[q] = rq;
-            z[q] = zq;
             if (flags[q] & kOwner) {
                 arr += (double)rq * (double)rq;
                 arz += (double)rq * (double)zq;
@@ -235,11 +246,9 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
         }
     } else {
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
-            x[q] = fma(alpha, p[q], x[q]);
             const V rq = fma(-alpha, w[q], r[q]);
             const V zq = minv[q] * rq;
             r[q] = rq;
-            z[q] = zq;
             const double wq = cw(c, q);
             arr += wq * (double)rq * (double)rq;
             arz += wq * (double)rq * (double)zq;
@@ -273,21 +282,39 @@ __global__ void __launch_bounds__(NT) k_beta(const double* __restrict__ parts, i
     }
 }
 
+// x += alpha p (old p) while xpend is set; then, when the iteration goes on and
+// update_p is set, p = minv r + beta p.
 template <class V>
-__global__ void k_p(int64_t n, const V* __restrict__ z, V* __restrict__ p, const Scalars* __restrict__ sc)
+__global__ void k_p(int64_t n, const V* __restrict__ minv, const V* __restrict__ r, V* __restrict__ x,
+                    V* __restrict__ p, const Scalars* __restrict__ sc, int update_p)
 {
-    if (halted(sc)) return;
-    const V beta = (V)sc->beta;
+    const bool do_x = sc->xpend != 0;
+    const bool do_p = update_p && !halted(sc);
+    const V alpha = (V)sc->alpha, beta = (V)sc->beta;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (do_x && do_p) {
 #pragma unroll 4
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        p[q] = fma(beta, p[q], z[q]);
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) {
+            const V pq = p[q];
+            x[q] = fma(alpha, pq, x[q]);
+            p[q] = fma(beta, pq, minv[q] * r[q]);
+        }
+    } else if (do_x) {
+#pragma unroll 4
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride)
+            x[q] = fma(alpha, p[q], x[q]);
+    } else if (do_p) {  // not reached: an iteration that goes on has a pending x update
+#pragma unroll 4
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride)
+            p[q] = fma(beta, p[q], minv[q] * r[q]);
+    }
 }
 
 }  // namespace
 
 template <class V>
 struct Buffers {
-    V *r, *z, *p, *w;
+    V *r, *p, *w;
     double* parts;  // 2 * kMaxReduceBlocks
     Scalars* sc;
 };
@@ -344,7 +371,7 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
     std::vector<cudaEvent_t> ev;
     Scalars h{};
     nek_status st = NEK_OK;
-    k_init<V><<<nb, NT, 0, s>>>(n, c, mask, minv, f, x, b.r, b.z, b.p, b.parts, flags);
+    k_init<V><<<nb, NT, 0, s>>>(n, c, mask, minv, f, x, b.r, b.p, b.parts, flags);
     k_init_finish<<<1, NT, 0, s>>>(b.parts, nb, tol, b.sc);
     launches += 2;
     if ((st = check_launch()) != NEK_OK) goto done;
@@ -361,18 +388,15 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
         if ((st = dssum<V>(gs, b.w, s)) != NEK_OK) goto done;
         k_pw<V><<<nb, NT, 0, s>>>(n, c, mask, b.p, b.w, b.parts, b.sc, flags);
         k_alpha<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
-        k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.p, b.w, x, b.r, b.z, b.parts, b.sc, flags);
+        k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.w, b.r, b.parts, b.sc, flags);
         k_beta<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
-        launches += 6;
+        k_p<V><<<sb, 256, 0, s>>>(n, minv, b.r, x, b.p, b.sc, it < max_iter ? 1 : 0);
+        launches += 7;
         if ((st = check_launch()) != NEK_OK) goto done;
         if (tol > 0.0 && (it % check_every == 0 || it == max_iter)) {
             if ((st = check_cuda(cudaMemcpyAsync(&h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) != NEK_OK) goto done;
             if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
             if (h.done || h.status != NEK_OK) break;
-        }
-        if (it < max_iter) {
-            k_p<V><<<sb, 256, 0, s>>>(n, b.z, b.p, b.sc);
-            launches += 1;
         }
     }
     if ((st = check_cuda(cudaMemcpyAsync(&h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) != NEK_OK) goto done;
