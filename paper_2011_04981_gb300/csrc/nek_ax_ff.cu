@@ -235,8 +235,39 @@ constexpr int ff_min_blocks()
 // Load modes of the float-float kernels: plain w = AX u; GATHER: u is a
 // unique-node vector read through l2g (element point p reads u[l2g[p]]); SKIP:
 // a CTA whose elements all belong to finished problems (eprob: problem of each
-// element, pdone: one byte per problem) returns at once (batched solves).
-constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2;
+// element, pdone: one byte per problem) returns at once (batched solves); DOT:
+// plain, and each element's energy u_e . (A_e u_e) is written to edot[e] (the
+// CG's <p, Ap> is their sum, see the solve).
+constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3;
+
+// out[e] = sum of the values v of element e's threads (thread t belongs to
+// element t / TPE).  Each element's TPE values are summed in a fixed order
+// (lane-strided, then a shuffle tree), so the result depends on nx only, not on
+// the number of elements per CTA.  sh: blockDim doubles of shared memory that
+// no thread reads any more.
+template <int TPE, int EPB>
+__device__ __forceinline__ void element_sums(double v, double* sh, double* __restrict__ out, int ne)
+{
+    __syncthreads();
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    if constexpr (TPE >= 32) {
+        if (threadIdx.x < EPB * 32) {  // whole warps: the block has EPB * TPE >= EPB * 32 threads
+            const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            double t = 0.0;
+            for (int q = lane; q < TPE; q += 32) t += sh[e * TPE + q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0 && e < ne) out[e] = t;
+        }
+    } else {
+        if (threadIdx.x < EPB) {
+            double t = 0.0;
+            for (int q = 0; q < TPE; q++) t += sh[threadIdx.x * TPE + q];
+            if ((int)threadIdx.x < ne) out[threadIdx.x] = t;
+        }
+    }
+}
 
 // True when every element of the CTA belongs to a finished problem.
 template <int MODE>
@@ -256,7 +287,7 @@ template <int NX, int EPB, int MODE>
 __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ff(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
             const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g,
-            const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone)
+            const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot)
 {
     using T = typename std::conditional<(NX % 2 == 0), float2, float>::type;
     using L = Lanes<T>;
@@ -397,10 +428,12 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
     __syncthreads();
 
     // ------------------------------------------------------------- phase 2
+    double energy = 0.0;  // kModeDot: sum of u . w over this thread's points
     if (active) {
         const float2* wre = sWr + el * N3;
         const float2* wse = sWs + el * N3;
         const float2* wte = sWt + el * N3;
+        const double* ug = u + (e0 + el) * (int64_t)N3;
         const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
                     mwt = sMax[4 * el + 3] * 1.0001f;
         const float bij = sCol[i] * mwr + sCol[j] * mws;
@@ -437,10 +470,13 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
 #pragma unroll
             for (int q = 0; q < W; q++) {
                 const int p = i + NX * (j + NX * (k0 + q));
-                we[p] = join_pair(L::get(hi, q), L::get(lo, q));
+                const double wv = join_pair(L::get(hi, q), L::get(lo, q));
+                we[p] = wv;
+                if constexpr (MODE == kModeDot) energy = fma(__ldg(ug + p), wv, energy);
             }
         }
     }
+    if constexpr (MODE == kModeDot) element_sums<TPE, EPB>(energy, reinterpret_cast<double*>(sU), edot + e0, ne);
 }
 
 // ------------------------------------------------------------------------
@@ -464,7 +500,7 @@ template <int NX, int EPB, int MODE>
 __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ffe(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
              const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g,
-             const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone)
+             const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot)
 {
     static_assert(NX % 2 == 0 && NX <= 12, "even nx up to 12");
     using T = float2;
@@ -610,9 +646,11 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     __syncthreads();
 
     // ------------------------------------------------------------- phase 2
+    double energy = 0.0;  // kModeDot: sum of u . w over this thread's points
     if (active) {
         const float4* wre = WR4 + el * PB;
         const float4* wse = WS4 + el * PB;
+        const double* ug = u + (e0 + el) * (int64_t)N3 + i + NX * j;  // u(i, j, k) at ug[k * N2]
         const float2* wte = WT2 + el * N3 + i + NX * j;  // wt(i, j, l) at wte[l * N2]
         const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
                     mwt = sMax[4 * el + 3] * 1.0001f;
@@ -621,6 +659,11 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
 #pragma unroll 1
         for (int kp = 0; kp < NP; kp++) {
             const int k0 = 2 * kp;
+            double u0 = 0.0, u1 = 0.0;
+            if constexpr (MODE == kModeDot) {  // issued here, used after the contraction
+                u0 = __ldg(ug + k0 * N2);
+                u1 = __ldg(ug + (k0 + 1) * N2);
+            }
             OffsetAcc<T> acc;
             acc.init(make_float2(offset_for(bij + sCol[k0] * mwt), offset_for(bij + sCol[k0 + 1] * mwt)));
             const float4* rr = wre + kp * N2 + j * NX;  // wr(l, j, k0..k0+1) at rr[l]
@@ -640,10 +683,13 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
             T hi, lo;
             acc.finish(hi, lo);
             const int p0 = i + NX * (j + NX * k0);
-            we[p0] = join_pair(hi.x, lo.x);
-            we[p0 + N2] = join_pair(hi.y, lo.y);
+            const double w0 = join_pair(hi.x, lo.x), w1 = join_pair(hi.y, lo.y);
+            we[p0] = w0;
+            we[p0 + N2] = w1;
+            if constexpr (MODE == kModeDot) energy = fma(u1, w1, fma(u0, w0, energy));
         }
     }
+    if constexpr (MODE == kModeDot) element_sums<N2, EPB>(energy, reinterpret_cast<double*>(U4), edot + e0, ne);
 }
 
 // The k-pair layout is used where it measured faster than the column walk on
@@ -667,7 +713,8 @@ constexpr size_t ff_variant_smem()
 
 template <int NX, int EPB, int MODE>
 nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                               cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
+                               cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
+                               double* edot)
 {
     constexpr size_t smem = ff_variant_smem<NX, EPB>();
     static std::atomic<uint64_t> configured{0};
@@ -677,23 +724,27 @@ nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, 
         nek_status st = ensure_dyn_smem(k_ax_ffe<NX, EPB, MODE>, smem, configured);
         if (st != NEK_OK) return st;
         k_ax_ffe<NX, EPB, MODE><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
-            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone);
+            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot);
     } else {
         nek_status st = ensure_dyn_smem(k_ax_ff<NX, EPB, MODE>, smem, configured);
         if (st != NEK_OK) return st;
         k_ax_ff<NX, EPB, MODE><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
-            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone);
+            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot);
     }
     return check_launch();
 }
 
 template <int NX, int EPB>
 nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                                cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
+                                cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
+                                double* edot)
 {
-    if (l2g) return launch_ax_ff_kernel<NX, EPB, kModeGather>(nelt, D, Gff, u, w, s, l2g, nullptr, nullptr);
-    if (eprob && pdone) return launch_ax_ff_kernel<NX, EPB, kModeSkip>(nelt, D, Gff, u, w, s, nullptr, eprob, pdone);
-    return launch_ax_ff_kernel<NX, EPB, kModePlain>(nelt, D, Gff, u, w, s, nullptr, nullptr, nullptr);
+    if (l2g)
+        return launch_ax_ff_kernel<NX, EPB, kModeGather>(nelt, D, Gff, u, w, s, l2g, nullptr, nullptr, nullptr);
+    if (eprob && pdone)
+        return launch_ax_ff_kernel<NX, EPB, kModeSkip>(nelt, D, Gff, u, w, s, nullptr, eprob, pdone, nullptr);
+    if (edot) return launch_ax_ff_kernel<NX, EPB, kModeDot>(nelt, D, Gff, u, w, s, nullptr, nullptr, nullptr, edot);
+    return launch_ax_ff_kernel<NX, EPB, kModePlain>(nelt, D, Gff, u, w, s, nullptr, nullptr, nullptr, nullptr);
 }
 
 template <int NX, int EPB>
@@ -704,27 +755,28 @@ constexpr bool ff_fits()
 
 template <int NX>
 nek_status launch_ax_ff_nx(int epb, int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
-                           cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
+                           cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
+                           double* edot)
 {
     if (epb <= 0) epb = ff_epb<NX>();
     switch (epb) {
         case 1:
             if constexpr (ff_fits<NX, 1>())
-                return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+                return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
             break;
         case 2:
             if constexpr (ff_fits<NX, 2>())
-                return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+                return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
             break;
         case 4:
             if constexpr (ff_fits<NX, 4>())
-                return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+                return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
             break;
         default:
             break;
     }
     if constexpr (ff_epb<NX>() != 1 && ff_epb<NX>() != 2 && ff_epb<NX>() != 4)
-        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
     return NEK_ERR_INVALID_ARG;
 }
 
@@ -740,24 +792,24 @@ __global__ void k_g_to_ff(int64_t npts, const double* __restrict__ G, float2* __
 
 nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
                             double* w, cudaStream_t s, const int32_t* l2g, const int32_t* eprob,
-                            const uint8_t* pdone)
+                            const uint8_t* pdone, double* edot)
 {
     switch (nx) {
-        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
-        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone);
+        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
 }
@@ -793,9 +845,10 @@ bool ax_ff_epb_fits(int nx, int epb)
 }
 
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
-                        cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone)
+                        cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
+                        double* edot)
 {
-    return launch_ax_ff_epb(tuned_epb(NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s, l2g, eprob, pdone);
+    return launch_ax_ff_epb(tuned_epb(NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s, l2g, eprob, pdone, edot);
 }
 
 }  // namespace nek

@@ -90,8 +90,10 @@ size_t nek_cg_workspace_bytes(int64_t nelt, int nx, int need_minv)
     if (nelt < 0 || nx < kMinNx || nx > kMaxNx) return 0;
     const size_t n = (size_t)nelt * nx * nx * nx;
     const size_t vec = pcg::align256(sizeof(double) * std::max<size_t>(n, 1));
-    // r, p, w, [minv], point flags (1 byte each), reduction partials, scalars
+    // r, p, w, [minv], point flags (1 byte each), element energies, reduction
+    // partials, scalars
     return vec * (need_minv ? 4 : 3) + pcg::align256(std::max<size_t>(n, 1)) +
+           pcg::align256(sizeof(double) * std::max<int64_t>(nelt, 1)) +
            pcg::align256(sizeof(double) * 2 * kMaxReduceBlocks) + pcg::align256(sizeof(pcg::Scalars));
 }
 
@@ -144,6 +146,8 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
     }
     uint8_t* flags = reinterpret_cast<uint8_t*>(base + off);
     off += pcg::align256(n);
+    double* edot = reinterpret_cast<double*>(base + off);
+    off += pcg::align256(sizeof(double) * nelt);
     b.parts = reinterpret_cast<double*>(base + off);
     off += pcg::align256(sizeof(double) * 2 * kMaxReduceBlocks);
     b.sc = reinterpret_cast<pcg::Scalars*>(base + off);
@@ -158,13 +162,17 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
         st = pcg::build_flags(gs, n, mask, flags, s);
         extra += gs->ngroups > 0 ? 2 : 1;
     }
+    // The float-float operator also writes element energies, which replace the
+    // solve's <p,w> pass.
+    const bool energies = ax_impl == NEK_AX_FF;
+    pcg::ElementEnergies ee{edot, nelt};
     if (st == NEK_OK) {
-        auto ax = [&](const double* p, double* w, cudaStream_t ss) {
-            return ax_impl == NEK_AX_FF ? launch_ax_ff(nelt, nx, D, Gff, p, w, ss)
+        auto ax = [&](const double* p, double* w, double* ed, cudaStream_t ss) {
+            return ax_impl == NEK_AX_FF ? launch_ax_ff(nelt, nx, D, Gff, p, w, ss, nullptr, nullptr, nullptr, ed)
                                         : launch_ax_fp64(nelt, nx, D, G, p, w, ss);
         };
         st = pcg::run<double>(gs, n, gs->d_c, mask, mv, f, x, b, tol_rel, max_iter, check_every, time_ax, ax, s,
-                              &res, flags);
+                              &res, flags, energies ? &ee : nullptr);
         if (iters_out) *iters_out = res.iters;
         if (relres_out) *relres_out = res.relres;
         if (opts) {

@@ -302,7 +302,9 @@ nek_status nek_lvec_cg_solve(const nek_lvec* lv, int64_t nelt, int nx, const dou
     b.sc = reinterpret_cast<pcg::Scalars*>(base + off);
 
     pcg::Result res;
-    auto ax = [&](const double* p, double* w, cudaStream_t ss) { return lvec_ax(lv, nelt, nx, D, Gff, p, w, wE, ss); };
+    auto ax = [&](const double* p, double* w, double*, cudaStream_t ss) {
+        return lvec_ax(lv, nelt, nx, D, Gff, p, w, wE, ss);
+    };
     st = pcg::run<double>(nullptr, lv->nl, static_cast<const double*>(nullptr), lv->d_mask, minvL, fL, xL, b, tol_rel,
                           max_iter, check_every, time_ax, ax, s, &res);
     if (iters_out) *iters_out = res.iters;

@@ -14,6 +14,14 @@
 // above, so the split changes no result, and it saves 8 bytes per point and
 // iteration (the second read of p; z's write and read become reads of minv
 // and r).
+// With point flags the mask is applied where w is used (k_update, and the flag
+// test of <p,w>), so nothing writes w after the operator and dssum.
+//
+// Operators that report element energies (ElementEnergies) save the <p,w>
+// pass: <p, mask.dssum(A_L p)>_c = sum over elements of p_e . (A_e p_e),
+// because p holds the same value in every copy of a node and is zero on masked
+// nodes (z = minv r and r vanish there).  The operator writes those energies
+// and k_alpha sums them.
 // Reductions use a fixed grid per length and a fixed shuffle tree, so results
 // are deterministic.  Once the residual test passes, or a breakdown is seen, a
 // device flag makes every later update kernel of the call return at once.
@@ -174,17 +182,14 @@ __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, c
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * NT;
     if (flags) {
-        // unrolled: more loads in flight per thread for this memory-bound loop
+        // read-only (the mask is applied by k_update), so the unrolled loads of
+        // consecutive iterations can all be in flight
 #pragma unroll 4
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
             const uint8_t fq = flags[q];
             const V pq = p[q];  // loaded whatever the flags say, so it is not held back behind them
-            V wq = w[q];
-            if (!(fq & kFree)) {
-                wq = V(0);
-                w[q] = V(0);
-            }
-            if (fq & kOwner) acc += (double)pq * (double)wq;
+            const V wq = w[q];
+            if ((fq & (kFree | kOwner)) == (kFree | kOwner)) acc += (double)pq * (double)wq;
         }
     } else {
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
@@ -236,10 +241,13 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
     if (flags) {
 #pragma unroll 4
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
-            const V rq = fma(-alpha, w[q], r[q]);
+            const uint8_t fq = flags[q];
+            V wq = w[q];
+            if (!(fq & kFree)) wq = V(0);  // the mask
+            const V rq = fma(-alpha, wq, r[q]);
             const V zq = minv[q] * rq;
             r[q] = rq;
-            if (flags[q] & kOwner) {
+            if (fq & kOwner) {
                 arr += (double)rq * (double)rq;
                 arz += (double)rq * (double)zq;
             }
@@ -327,6 +335,13 @@ struct Result {
     int ax_timed = 0;
 };
 
+// The element-energy path (see the top of this file): the operator writes
+// edot[e] = p_e . (A_e p_e) for its nelt elements.  Requires point flags.
+struct ElementEnergies {
+    double* edot;
+    int64_t nelt;
+};
+
 namespace {
 
 // One flag byte per point of an E-vector plan: kFree from the mask; kOwner on
@@ -355,15 +370,16 @@ inline nek_status build_flags(const nek_gs* gs, int64_t n, const uint8_t* mask, 
     return check_launch();
 }
 
-// Runs PCG from x = 0.  `ax(p, w, stream)` applies the element operator, which
-// gs then sums over shared nodes; with gs null, ax applies the assembled
-// operator itself.  c null weights every entry by 1.
+// Runs PCG from x = 0.  `ax(p, w, edot, stream)` applies the element operator,
+// which gs then sums over shared nodes; with gs null, ax applies the assembled
+// operator itself.  edot is ee->edot on the element-energy path (ee non-null),
+// else null.  c null weights every entry by 1.
 // tol > 0: stop at convergence (NEK_ERR_NOT_CONVERGED after max_iter);
 // tol == 0: exactly max_iter iterations.  Leaves the stream synchronised.
 template <class V, class AxFn>
 nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, const V* minv, const V* f, V* x,
                const Buffers<V>& b, double tol, int max_iter, int check_every, bool time_ax, AxFn&& ax,
-               cudaStream_t s, Result* res, const uint8_t* flags = nullptr)
+               cudaStream_t s, Result* res, const uint8_t* flags = nullptr, const ElementEnergies* ee = nullptr)
 {
     const int nb = reduce_blocks(n);
     const int sb = stream_blocks(n);
@@ -383,15 +399,20 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
     for (int it = 1; it <= max_iter; it++) {
         const bool timed = time_ax && (size_t)(2 * it) <= ev.size();
         if (timed) cudaEventRecord(ev[2 * (it - 1)], s);
-        if ((st = ax(b.p, b.w, s)) != NEK_OK) goto done;
+        if ((st = ax(b.p, b.w, ee ? ee->edot : nullptr, s)) != NEK_OK) goto done;
         if (timed) cudaEventRecord(ev[2 * (it - 1) + 1], s);
         if ((st = dssum<V>(gs, b.w, s)) != NEK_OK) goto done;
-        k_pw<V><<<nb, NT, 0, s>>>(n, c, mask, b.p, b.w, b.parts, b.sc, flags);
-        k_alpha<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
+        if (ee) {
+            k_alpha<<<1, NT, 0, s>>>(ee->edot, static_cast<int>(ee->nelt), b.sc);
+        } else {
+            k_pw<V><<<nb, NT, 0, s>>>(n, c, mask, b.p, b.w, b.parts, b.sc, flags);
+            k_alpha<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
+            launches += 1;
+        }
         k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.w, b.r, b.parts, b.sc, flags);
         k_beta<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
         k_p<V><<<sb, 256, 0, s>>>(n, minv, b.r, x, b.p, b.sc, it < max_iter ? 1 : 0);
-        launches += 7;
+        launches += 6;  // the operator, dssum, k_alpha, k_update, k_beta, k_p
         if ((st = check_launch()) != NEK_OK) goto done;
         if (tol > 0.0 && (it % check_every == 0 || it == max_iter)) {
             if ((st = check_cuda(cudaMemcpyAsync(&h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) != NEK_OK) goto done;
