@@ -129,7 +129,9 @@ nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, co
  * the given data (synchronously; u, G/Gff, w as for nek_ax / nek_ax_ff with
  * impl = NEK_AX_FP64 / NEK_AX_FF, 16-byte aligned) and keeps the fastest for
  * all later launches of that (impl, nx) in this process; *epb_out and *ms_out
- * (nullable) receive it and its time per launch.  nek_set_ax_epb sets the size
+ * (nullable) receive it and its time per launch.  For NEK_AX_FF the form with
+ * element energies that nek_cg_solve_ex uses is tuned too (kept on its own,
+ * not reported).  nek_set_ax_epb sets the size
  * directly (0 restores the built-in default; a size that does not fit the
  * kernel's thread or shared-memory limits for that nx is NEK_ERR_INVALID_ARG);
  * nek_get_ax_epb reads it back.

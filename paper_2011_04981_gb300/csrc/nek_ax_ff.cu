@@ -848,7 +848,8 @@ nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff,
                         cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
                         double* edot)
 {
-    return launch_ax_ff_epb(tuned_epb(NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+    return launch_ax_ff_epb(tuned_epb(edot ? kAxFfEnergy : NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s, l2g, eprob,
+                            pdone, edot);
 }
 
 }  // namespace nek

@@ -48,7 +48,9 @@ nek_status gs_create_flat(int64_t n, const int64_t* glo, nek_gs** out);
 void gll_host(int nx, double* xi, double* rho, double* D);
 
 // Elements per CTA of the AX kernels: 0 = built-in default, else the value chosen
-// by nek_tune_ax for (impl, nx).
+// by nek_tune_ax for (impl, nx); impl kAxFfEnergy is the float-float kernel in
+// its element-energy form.
+constexpr int kAxFfEnergy = 2;
 int tuned_epb(int impl, int nx);
 bool ax_fp64_epb_fits(int nx, int epb);
 bool ax_ff_epb_fits(int nx, int epb);

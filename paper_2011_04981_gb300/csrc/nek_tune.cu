@@ -5,7 +5,9 @@
 // elements are grouped into CTAs, never the arithmetic on an element, so all
 // variants give bit-identical results; it trades occupancy against how much of
 // a CTA's load phase overlaps other CTAs' compute.  nek_tune_ax times the
-// variants on the caller's data and keeps the fastest for later launches.
+// variants on the caller's data and keeps the fastest for later launches.  The
+// float-float kernel has two forms (plain, and with element energies for the
+// solve), each tuned on its own: their register allocations differ.
 #include <atomic>
 
 #include "nek_internal.h"
@@ -13,12 +15,12 @@
 namespace nek {
 
 namespace {
-std::atomic<int> g_epb[2][kMaxNx + 1];
+std::atomic<int> g_epb[3][kMaxNx + 1];  // NEK_AX_FP64, NEK_AX_FF, kAxFfEnergy
 }
 
 int tuned_epb(int impl, int nx)
 {
-    if (impl < 0 || impl > 1 || nx < 0 || nx > kMaxNx) return 0;
+    if (impl < 0 || impl > kAxFfEnergy || nx < 0 || nx > kMaxNx) return 0;
     return g_epb[impl][nx].load(std::memory_order_relaxed);
 }
 
@@ -35,6 +37,7 @@ nek_status nek_set_ax_epb(int impl, int nx, int epb)
     if (epb != 0 && !(impl == NEK_AX_FF ? ax_ff_epb_fits(nx, epb) : ax_fp64_epb_fits(nx, epb)))
         return NEK_ERR_INVALID_ARG;  // not one of the compiled counts, or too many threads / too much smem
     g_epb[impl][nx].store(epb, std::memory_order_relaxed);
+    if (impl == NEK_AX_FF) g_epb[kAxFfEnergy][nx].store(epb, std::memory_order_relaxed);
     return NEK_OK;
 }
 
@@ -51,44 +54,59 @@ nek_status nek_tune_ax(int impl, int64_t nelt, int nx, const double* D, const vo
     if (ranges_overlap(u, bytes, w, bytes)) return NEK_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double* edot = nullptr;  // element energies of the float-float solve form
     nek_status st = check_cuda(cudaEventCreate(&e0));
     if (st == NEK_OK) st = check_cuda(cudaEventCreate(&e1));
-    int best = 0;
-    float best_ms = 0.f;
-    const int cand[3] = {1, 2, 4};
-    for (int c = 0; c < 3 && st == NEK_OK; c++) {
-        auto run = [&]() {
-            return impl == NEK_AX_FF
-                       ? launch_ax_ff_epb(cand[c], nelt, nx, D, static_cast<const float*>(Gx), u, w, s)
-                       : launch_ax_fp64_epb(cand[c], nelt, nx, D, static_cast<const double*>(Gx), u, w, s);
-        };
-        nek_status sv = run();
-        if (sv == NEK_ERR_INVALID_ARG) continue;  // this count does not fit this nx
-        if (sv != NEK_OK) {
-            st = sv;
-            break;
+    if (st == NEK_OK && impl == NEK_AX_FF)
+        if (check_cuda(cudaMalloc(&edot, sizeof(double) * (size_t)nelt)) != NEK_OK) st = NEK_ERR_NOMEM;
+    int best_plain = 0;
+    float best_plain_ms = 0.f;
+    const int nforms = impl == NEK_AX_FF ? 2 : 1;
+    for (int form = 0; form < nforms && st == NEK_OK; form++) {
+        int best = 0;
+        float best_ms = 0.f;
+        const int cand[3] = {1, 2, 4};
+        for (int c = 0; c < 3 && st == NEK_OK; c++) {
+            auto run = [&]() {
+                return impl == NEK_AX_FF
+                           ? launch_ax_ff_epb(cand[c], nelt, nx, D, static_cast<const float*>(Gx), u, w, s, nullptr,
+                                              nullptr, nullptr, form ? edot : nullptr)
+                           : launch_ax_fp64_epb(cand[c], nelt, nx, D, static_cast<const double*>(Gx), u, w, s);
+            };
+            nek_status sv = run();
+            if (sv == NEK_ERR_INVALID_ARG) continue;  // this count does not fit this nx
+            if (sv != NEK_OK) {
+                st = sv;
+                break;
+            }
+            if ((st = run()) != NEK_OK) break;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && st == NEK_OK; r++) st = run();
+            cudaEventRecord(e1, s);
+            if (st != NEK_OK) break;
+            if ((st = check_cuda(cudaEventSynchronize(e1))) != NEK_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= 3.f;
+            if (best == 0 || ms < best_ms) {
+                best = cand[c];
+                best_ms = ms;
+            }
         }
-        if ((st = run()) != NEK_OK) break;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < 3 && st == NEK_OK; r++) st = run();
-        cudaEventRecord(e1, s);
+        if (st == NEK_OK && best == 0) st = NEK_ERR_INVALID_ARG;
         if (st != NEK_OK) break;
-        if ((st = check_cuda(cudaEventSynchronize(e1))) != NEK_OK) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= 3.f;
-        if (best == 0 || ms < best_ms) {
-            best = cand[c];
-            best_ms = ms;
+        g_epb[form ? kAxFfEnergy : impl][nx].store(best, std::memory_order_relaxed);
+        if (form == 0) {
+            best_plain = best;
+            best_plain_ms = best_ms;
         }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    if (edot) cudaFree(edot);
     if (st != NEK_OK) return st;
-    if (best == 0) return NEK_ERR_INVALID_ARG;
-    g_epb[impl][nx].store(best, std::memory_order_relaxed);
-    if (epb_out) *epb_out = best;
-    if (ms_out) *ms_out = best_ms;
+    if (epb_out) *epb_out = best_plain;
+    if (ms_out) *ms_out = best_plain_ms;
     return NEK_OK;
 }
 
