@@ -237,8 +237,10 @@ constexpr int ff_min_blocks()
 // a CTA whose elements all belong to finished problems (eprob: problem of each
 // element, pdone: one byte per problem) returns at once (batched solves); DOT:
 // plain, and each element's energy u_e . (A_e u_e) is written to edot[e] (the
-// CG's <p, Ap> is their sum, see the solve).
-constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3;
+// CG's <p, Ap> is their sum, see the solve); SKIP_DOT: both (batched solves).
+constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3, kModeSkipDot = 4;
+constexpr bool mode_skips(int m) { return m == kModeSkip || m == kModeSkipDot; }
+constexpr bool mode_energies(int m) { return m == kModeDot || m == kModeSkipDot; }
 
 // out[e] = sum of the values v of element e's threads (thread t belongs to
 // element t / TPE).  Each element's TPE values are summed in a fixed order
@@ -274,7 +276,7 @@ template <int MODE>
 __device__ __forceinline__ bool cta_skipped(const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone,
                                             int64_t e0, int ne)
 {
-    if constexpr (MODE != kModeSkip) {
+    if constexpr (!mode_skips(MODE)) {
         return false;
     } else {
         bool all_done = true;
@@ -472,11 +474,11 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
                 const int p = i + NX * (j + NX * (k0 + q));
                 const double wv = join_pair(L::get(hi, q), L::get(lo, q));
                 we[p] = wv;
-                if constexpr (MODE == kModeDot) energy = fma(__ldg(ug + p), wv, energy);
+                if constexpr (mode_energies(MODE)) energy = fma(__ldg(ug + p), wv, energy);
             }
         }
     }
-    if constexpr (MODE == kModeDot) element_sums<TPE, EPB>(energy, reinterpret_cast<double*>(sU), edot + e0, ne);
+    if constexpr (mode_energies(MODE)) element_sums<TPE, EPB>(energy, reinterpret_cast<double*>(sU), edot + e0, ne);
 }
 
 // ------------------------------------------------------------------------
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
         for (int kp = 0; kp < NP; kp++) {
             const int k0 = 2 * kp;
             double u0 = 0.0, u1 = 0.0;
-            if constexpr (MODE == kModeDot) {  // issued here, used after the contraction
+            if constexpr (mode_energies(MODE)) {  // issued here, used after the contraction
                 u0 = __ldg(ug + k0 * N2);
                 u1 = __ldg(ug + (k0 + 1) * N2);
             }
@@ -686,10 +688,10 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
             const double w0 = join_pair(hi.x, lo.x), w1 = join_pair(hi.y, lo.y);
             we[p0] = w0;
             we[p0 + N2] = w1;
-            if constexpr (MODE == kModeDot) energy = fma(u1, w1, fma(u0, w0, energy));
+            if constexpr (mode_energies(MODE)) energy = fma(u1, w1, fma(u0, w0, energy));
         }
     }
-    if constexpr (MODE == kModeDot) element_sums<N2, EPB>(energy, reinterpret_cast<double*>(U4), edot + e0, ne);
+    if constexpr (mode_energies(MODE)) element_sums<N2, EPB>(energy, reinterpret_cast<double*>(U4), edot + e0, ne);
 }
 
 // The k-pair layout is used where it measured faster than the column walk on
@@ -741,6 +743,8 @@ nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff,
 {
     if (l2g)
         return launch_ax_ff_kernel<NX, EPB, kModeGather>(nelt, D, Gff, u, w, s, l2g, nullptr, nullptr, nullptr);
+    if (eprob && pdone && edot)
+        return launch_ax_ff_kernel<NX, EPB, kModeSkipDot>(nelt, D, Gff, u, w, s, nullptr, eprob, pdone, edot);
     if (eprob && pdone)
         return launch_ax_ff_kernel<NX, EPB, kModeSkip>(nelt, D, Gff, u, w, s, nullptr, eprob, pdone, nullptr);
     if (edot) return launch_ax_ff_kernel<NX, EPB, kModeDot>(nelt, D, Gff, u, w, s, nullptr, nullptr, nullptr, edot);

@@ -100,12 +100,14 @@ __global__ void __launch_bounds__(BT) kb_init(const int64_t* __restrict__ ch_beg
     chunk_reduce<2>(acc, parts, nchunks);
 }
 
-// one warp per problem: sums its chunk partials in order
-__device__ __forceinline__ double prob_sum(const double* parts, int c0, int c1)
+// one warp per problem: sums its partials [c0, c1) in order
+template <class I>
+__device__ __forceinline__ double prob_sum(const double* __restrict__ parts, I c0, I c1)
 {
     const int lane = threadIdx.x & 31;
     double v = 0.0;
-    for (int q = c0 + lane; q < c1; q += 32) v += parts[q];
+#pragma unroll 4
+    for (I q = c0 + lane; q < c1; q += 32) v += parts[q];
     return warp_sum(v);
 }
 
@@ -147,18 +149,17 @@ __global__ void __launch_bounds__(BT) kb_pw(const int64_t* __restrict__ ch_begin
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
         const uint8_t fq = flags[q];
         const double pq = p[q];  // loaded whatever the flags say, so it is not held back behind them
-        double wq = w[q];
-        if (!(fq & pcg::kFree)) {
-            wq = 0.0;
-            w[q] = 0.0;
-        }
-        if (fq & pcg::kOwner) acc[0] += pq * wq;
+        const double wq = w[q];  // read-only: kb_update applies the mask
+        if ((fq & (pcg::kFree | pcg::kOwner)) == (pcg::kFree | pcg::kOwner)) acc[0] += pq * wq;
     }
     chunk_reduce<1>(acc, parts, nchunks);
 }
 
+// pw from the chunk partials of kb_pw or, with edot, from the element energies
+// of the float-float operator (problem p's elements are [pel[p], pel[p+1]))
 __global__ void kb_alpha(int nprob, const int* __restrict__ pch, const double* __restrict__ parts,
-                         BScal* __restrict__ sc, int* __restrict__ active)
+                         BScal* __restrict__ sc, int* __restrict__ active, const int64_t* __restrict__ pel,
+                         const double* __restrict__ edot)
 {
     const int pid = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (pid >= nprob) return;
@@ -166,7 +167,7 @@ __global__ void kb_alpha(int nprob, const int* __restrict__ pch, const double* _
         if ((threadIdx.x & 31) == 0) sc[pid].xpend = 0;
         return;
     }
-    const double pw = prob_sum(parts, pch[pid], pch[pid + 1]);
+    const double pw = edot ? prob_sum(edot, pel[pid], pel[pid + 1]) : prob_sum(parts, pch[pid], pch[pid + 1]);
     if ((threadIdx.x & 31) == 0) {
         BScal& s = sc[pid];
         s.it += 1;
@@ -198,10 +199,13 @@ __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_b
     const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
     double acc[2] = {0.0, 0.0};
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
-        const double rq = fma(-alpha, w[q], r[q]);
+        const uint8_t fq = flags[q];
+        double wq = w[q];  // loaded whatever the flags say
+        if (!(fq & pcg::kFree)) wq = 0.0;  // the mask
+        const double rq = fma(-alpha, wq, r[q]);
         const double zq = minv[q] * rq;
         r[q] = rq;
-        if (flags[q] & pcg::kOwner) {
+        if (fq & pcg::kOwner) {
             acc[0] += rq * rq;
             acc[1] += rq * zq;
         }
@@ -315,6 +319,7 @@ struct nek_batch {
     int32_t* d_ch_prob;   // nchunks
     int* d_pch;           // nprob+1: chunk range of each problem
     int32_t* d_elem_prob; // nelt_total: problem of each element
+    int64_t* d_pel;       // nprob+1: element range of each problem
 };
 
 using namespace nek;
@@ -324,7 +329,7 @@ namespace {
 inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct BLayout {
-    double *r, *p, *w, *minv, *parts;
+    double *r, *p, *w, *minv, *parts, *edot;
     BScal* sc;
     int* active;
     uint8_t* pdone;  // nprob: 1 once a problem has finished (converged or broken down)
@@ -347,6 +352,7 @@ BLayout b_layout(char* base, const nek_batch* b, bool need_minv)
     L.w = reinterpret_cast<double*>(take(v));
     L.minv = need_minv ? reinterpret_cast<double*>(take(v)) : nullptr;
     L.parts = reinterpret_cast<double*>(take(sizeof(double) * 2 * (size_t)b->nchunks));
+    L.edot = reinterpret_cast<double*>(take(sizeof(double) * std::max<int64_t>(b->nelt_total, 1)));
     L.sc = reinterpret_cast<BScal*>(take(sizeof(BScal) * (size_t)b->nprob));
     L.active = reinterpret_cast<int*>(take(sizeof(int) * 4));
     L.pdone = reinterpret_cast<uint8_t*>(take(static_cast<size_t>(b->nprob)));
@@ -384,6 +390,7 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
     b->d_ch_prob = nullptr;
     b->d_pch = nullptr;
     b->d_elem_prob = nullptr;
+    b->d_pel = nullptr;
     nek_status st = NEK_OK;
     try {
         // global ids of all problems in one space: problem q's ids are offset by
@@ -393,6 +400,7 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
         std::vector<int32_t> ch_prob;
         std::vector<int> pch(1, 0);
         std::vector<int32_t> elem_prob(static_cast<size_t>(nel));
+        std::vector<int64_t> pel(1, 0);
         b->prob_pt0.assign(1, 0);
         int64_t pt = 0, goff = 0, el = 0;
         for (int q = 0; q < nprob; q++) {
@@ -410,6 +418,7 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
             }
             pch.push_back(static_cast<int>(ch_begin.size()));
             for (int64_t k = 0; k < nelt[q]; k++) elem_prob[el + k] = q;
+            pel.push_back(el + nelt[q]);
             if (b->groups.empty() || b->groups.back().nx != nx[q]) b->groups.push_back(Group{nx[q], el, 0, pt, nullptr});
             b->groups.back().nelt += nelt[q];
             goff += gmax + 1;
@@ -424,6 +433,10 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
         if ((st = check_cuda(cudaMalloc(&b->d_ch_prob, sizeof(int32_t) * ch_prob.size()))) != NEK_OK) throw 3;
         if ((st = check_cuda(cudaMalloc(&b->d_pch, sizeof(int) * pch.size()))) != NEK_OK) throw 3;
         if ((st = check_cuda(cudaMalloc(&b->d_elem_prob, sizeof(int32_t) * elem_prob.size()))) != NEK_OK) throw 3;
+        if ((st = check_cuda(cudaMalloc(&b->d_pel, sizeof(int64_t) * pel.size()))) != NEK_OK) throw 3;
+        if ((st = check_cuda(cudaMemcpy(b->d_pel, pel.data(), sizeof(int64_t) * pel.size(), cudaMemcpyHostToDevice))) !=
+            NEK_OK)
+            throw 3;
         if ((st = check_cuda(cudaMemcpy(b->d_elem_prob, elem_prob.data(), sizeof(int32_t) * elem_prob.size(),
                                         cudaMemcpyHostToDevice))) != NEK_OK)
             throw 3;
@@ -461,6 +474,7 @@ nek_status nek_batch_destroy(nek_batch* b)
     cudaFree(b->d_ch_prob);
     cudaFree(b->d_pch);
     cudaFree(b->d_elem_prob);
+    cudaFree(b->d_pel);
     for (auto& g : b->groups) cudaFree(g.D);
     delete b;
     return NEK_OK;
@@ -531,21 +545,22 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
             const double* pg = L.p + g.pt0;
             double* wg = L.w + g.pt0;
             nek_status sa = Gff ? launch_ax_ff(g.nelt, g.nx, g.D, Gff + g.pt0 * 12, pg, wg, ss, nullptr,
-                                               b->d_elem_prob + g.elem0, L.pdone)
+                                               b->d_elem_prob + g.elem0, L.pdone, L.edot + g.elem0)
                                 : launch_ax_fp64(g.nelt, g.nx, g.D, G + g.pt0 * 6, pg, wg, ss);
             if (sa != NEK_OK) return sa;
         }
         nek_status sd = pcg::dssum<double>(b->gs, L.w, ss);
         if (sd != NEK_OK) return sd;
-        kb_pw<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, L.p, L.w, L.parts, L.sc);
-        kb_alpha<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, L.sc, L.active);
+        // the float-float operator writes element energies, which give <p,w> (no kb_pw pass)
+        if (!Gff) kb_pw<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, L.p, L.w, L.parts, L.sc);
+        kb_alpha<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, L.sc, L.active, b->d_pel, Gff ? L.edot : nullptr);
         kb_update<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, L.w, L.r, L.parts, L.sc);
         kb_beta<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, nc, L.sc, L.active);
         kb_test<<<(np + 255) / 256, 256, 0, ss>>>(np, tol_rel, L.sc, L.active, L.pdone);
         kb_p<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, mv, L.r, x, L.p, L.sc);
         return check_launch();
     };
-    const int per_iter_launches = static_cast<int>(b->groups.size()) + 7;
+    const int per_iter_launches = static_cast<int>(b->groups.size()) + (Gff ? 6 : 7);
 
     if (!minv) {
         if ((st = nek_batch_jacobi_minv(b, G, mask, L.minv, stream)) != NEK_OK) goto done;

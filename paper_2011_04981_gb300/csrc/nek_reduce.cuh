@@ -25,11 +25,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh /* NT/32 double
     return t;  // valid in thread 0
 }
 
-// Sum of nparts partials (in a fixed order) by one block of NT threads.
+// Sum of nparts partials (in a fixed order) by one block of NT threads.  The
+// unrolled loop issues a thread's loads together; the adds stay in order.
 template <int NT>
-__device__ __forceinline__ double sum_partials(const double* parts, int nparts, double* sh)
+__device__ __forceinline__ double sum_partials(const double* __restrict__ parts, int nparts, double* sh)
 {
     double v = 0.0;
+#pragma unroll 8
     for (int q = threadIdx.x; q < nparts; q += NT) v += parts[q];
     return block_sum<NT>(v, sh);
 }
