@@ -57,12 +57,40 @@ constexpr int NT = kReduceThreads;
 
 __device__ __forceinline__ bool halted(const Scalars* sc) { return sc->done || sc->status != NEK_OK; }
 
+// (double)x with integer operations only, exact for every float (normal,
+// subnormal, zero, inf, nan).  The FP32 -> FP64 conversion instruction runs on
+// the FP64 pipe, which the double-precision dot products of the float solve
+// already load; this keeps it to the DFMA of each product.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned sgn = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+    unsigned hi, lo;
+    if (e != 0u && e != 0xFFu) {  // normal: exponent rebiased 127 -> 1023, mantissa 23 -> 52 bits
+        hi = sgn | ((e + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    } else if (e == 0xFFu) {  // inf, nan (payload kept)
+        hi = sgn | 0x7FF00000u | (m >> 3);
+        lo = m << 29;
+    } else if (m == 0u) {  // signed zero
+        hi = sgn;
+        lo = 0u;
+    } else {  // subnormal m * 2^-149 = 1.f * 2^(p-149) with the leading one at bit p
+        const int p = 31 - __clz(m);
+        const unsigned long long f = static_cast<unsigned long long>(m ^ (1u << p)) << (52 - p);
+        hi = sgn | (static_cast<unsigned>(p + 874) << 20) | static_cast<unsigned>(f >> 32);
+        lo = static_cast<unsigned>(f);
+    }
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
 // Inner-product weight of entry q: 1/multiplicity on E-vectors, 1 when c is
 // null (unique-node vectors, where every node is stored once).
 template <class V>
 __device__ __forceinline__ double cw(const V* __restrict__ c, int64_t q)
 {
-    return c ? (double)c[q] : 1.0;
+    return c ? to_f64(c[q]) : 1.0;
 }
 
 // Point flags (optional, one byte per point): bit 0 = free (the mask), bit 1 =
@@ -134,8 +162,8 @@ __global__ void __launch_bounds__(NT) k_init(int64_t n, const V* __restrict__ c,
         r[q] = rq;
         p[q] = zq;
         const double wq = weight(c, flags, q);
-        arz += wq * (double)rq * (double)zq;
-        arr += wq * (double)rq * (double)rq;
+        arz += wq * to_f64(rq) * to_f64(zq);
+        arr += wq * to_f64(rq) * to_f64(rq);
     }
     double t = block_sum<NT>(arz, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -189,7 +217,7 @@ __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, c
             const uint8_t fq = flags[q];
             const V pq = p[q];  // loaded whatever the flags say, so it is not held back behind them
             const V wq = w[q];
-            if ((fq & (kFree | kOwner)) == (kFree | kOwner)) acc += (double)pq * (double)wq;
+            if ((fq & (kFree | kOwner)) == (kFree | kOwner)) acc += to_f64(pq) * to_f64(wq);
         }
     } else {
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
@@ -198,7 +226,7 @@ __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, c
                 wq = V(0);
                 w[q] = V(0);
             }
-            acc += cw(c, q) * (double)p[q] * (double)wq;
+            acc += cw(c, q) * to_f64(p[q]) * to_f64(wq);
         }
     }
     const double t = block_sum<NT>(acc, sh);
@@ -248,8 +276,9 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
             const V zq = minv[q] * rq;
             r[q] = rq;
             if (fq & kOwner) {
-                arr += (double)rq * (double)rq;
-                arz += (double)rq * (double)zq;
+                const double rd = to_f64(rq);
+                arr += rd * rd;
+                arz += rd * to_f64(zq);
             }
         }
     } else {
@@ -258,8 +287,8 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
             const V zq = minv[q] * rq;
             r[q] = rq;
             const double wq = cw(c, q);
-            arr += wq * (double)rq * (double)rq;
-            arz += wq * (double)rq * (double)zq;
+            arr += wq * to_f64(rq) * to_f64(rq);
+            arz += wq * to_f64(rq) * to_f64(zq);
         }
     }
     double t = block_sum<NT>(arr, sh);
