@@ -27,6 +27,7 @@
 #include <type_traits>
 
 #include "nek_internal.h"
+#include "nek_reduce.cuh"
 
 namespace nek {
 
@@ -241,35 +242,6 @@ constexpr int ff_min_blocks()
 constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3, kModeSkipDot = 4;
 constexpr bool mode_skips(int m) { return m == kModeSkip || m == kModeSkipDot; }
 constexpr bool mode_energies(int m) { return m == kModeDot || m == kModeSkipDot; }
-
-// out[e] = sum of the values v of element e's threads (thread t belongs to
-// element t / TPE).  Each element's TPE values are summed in a fixed order
-// (lane-strided, then a shuffle tree), so the result depends on nx only, not on
-// the number of elements per CTA.  sh: blockDim doubles of shared memory that
-// no thread reads any more.
-template <int TPE, int EPB>
-__device__ __forceinline__ void element_sums(double v, double* sh, double* __restrict__ out, int ne)
-{
-    __syncthreads();
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    if constexpr (TPE >= 32) {
-        if (threadIdx.x < EPB * 32) {  // whole warps: the block has EPB * TPE >= EPB * 32 threads
-            const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
-            double t = 0.0;
-            for (int q = lane; q < TPE; q += 32) t += sh[e * TPE + q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0 && e < ne) out[e] = t;
-        }
-    } else {
-        if (threadIdx.x < EPB) {
-            double t = 0.0;
-            for (int q = 0; q < TPE; q++) t += sh[threadIdx.x * TPE + q];
-            if ((int)threadIdx.x < ne) out[threadIdx.x] = t;
-        }
-    }
-}
 
 // True when every element of the CTA belongs to a finished problem.
 template <int MODE>

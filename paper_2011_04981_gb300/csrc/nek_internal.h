@@ -74,8 +74,9 @@ nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                         cudaStream_t s, const int32_t* l2g = nullptr, const int32_t* eprob = nullptr,
                         const uint8_t* pdone = nullptr, double* edot = nullptr);
+// edot (optional, nelt doubles): per-element energies u_e . w_e in FP64.
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
-                          const float* u, float* w, cudaStream_t s);
+                          const float* u, float* w, cudaStream_t s, double* edot = nullptr);
 nek_status launch_mask(int64_t n, const uint8_t* mask, double* v, cudaStream_t s);
 // Diagonal of the element operators (before summation over shared nodes).
 nek_status launch_diag_local(int64_t nelt, int nx, const double* D, const double* G, double* d, cudaStream_t s);

@@ -159,11 +159,14 @@ __device__ __forceinline__ void line_apply(const float* __restrict__ M, const fl
 // registers; the pointwise G product runs on the t-lines; phase 2 sums the
 // r- and s-contributions through shared memory and adds the t-contribution in
 // registers before the store.
-template <class S, int NX, int EPB>
+// ENERGY: edot[e] = sum over the element's points of u w (products and sums in
+// FP64), which the inner solve uses for <p,w> (see nek_pcg.cuh).
+template <class S, int NX, int EPB, bool ENERGY>
 __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const double* __restrict__ D,
                                                           const S* __restrict__ Glp,
                                                           const float* __restrict__ gscale,
-                                                          const float* __restrict__ u, float* __restrict__ w)
+                                                          const float* __restrict__ u, float* __restrict__ w,
+                                                          double* __restrict__ edot)
 {
     using L = Lp<S>;
     constexpr int N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB, R = lp_row(NX);
@@ -277,55 +280,68 @@ __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const dou
         for (int o = 0; o < NX; o++) ue[b * N2 + o * NX + a] += os[o];
     }
     __syncthreads();
+    double energy = 0.0;
     if (active) {
         float ot[NX];
         line_apply<NX>(sDT, wt, ot);
         const float scale = su * gscale[e0 + el];
         float* we = w + (e0 + el) * (int64_t)N3;
+        const float* ug = u + (e0 + el) * (int64_t)N3;
 #pragma unroll
         for (int k = 0; k < NX; k++) {
             const int p = k * N2 + b * NX + a;
-            we[p] = (ue[p] + ot[k]) * scale;
+            const float wv = (ue[p] + ot[k]) * scale;
+            we[p] = wv;
+            if constexpr (ENERGY) energy = fma(pcg::to_f64(__ldg(ug + p)), pcg::to_f64(wv), energy);
         }
     }
+    if constexpr (ENERGY) element_sums<N2, EPB>(energy, reinterpret_cast<double*>(sR), edot + e0, ne);
 }
 
-template <class S, int NX>
-nek_status launch_lowp_nx(int64_t nelt, const double* D, const void* Glp, const float* gscale, const float* u,
-                          float* w, cudaStream_t s)
+template <class S, int NX, bool ENERGY>
+nek_status launch_lowp_kernel(int64_t nelt, const double* D, const void* Glp, const float* gscale, const float* u,
+                              float* w, double* edot, cudaStream_t s)
 {
     constexpr int EPB = lp_epb(NX);
     constexpr size_t smem = lp_smem_bytes<NX, EPB>();
     static std::atomic<uint64_t> configured{0};
-    nek_status st = ensure_dyn_smem(k_ax_lowp<S, NX, EPB>, smem, configured);
+    nek_status st = ensure_dyn_smem(k_ax_lowp<S, NX, EPB, ENERGY>, smem, configured);
     if (st != NEK_OK) return st;
     const int64_t blocks = (nelt + EPB - 1) / EPB;
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
-    k_ax_lowp<S, NX, EPB><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(nelt, D, static_cast<const S*>(Glp),
-                                                                          gscale, u, w);
+    k_ax_lowp<S, NX, EPB, ENERGY><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
+        nelt, D, static_cast<const S*>(Glp), gscale, u, w, edot);
     return check_launch();
+}
+
+template <class S, int NX>
+nek_status launch_lowp_nx(int64_t nelt, const double* D, const void* Glp, const float* gscale, const float* u,
+                          float* w, double* edot, cudaStream_t s)
+{
+    return edot ? launch_lowp_kernel<S, NX, true>(nelt, D, Glp, gscale, u, w, edot, s)
+                : launch_lowp_kernel<S, NX, false>(nelt, D, Glp, gscale, u, w, nullptr, s);
 }
 
 template <class S>
 nek_status launch_lowp_t(int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
-                         const float* u, float* w, cudaStream_t s)
+                         const float* u, float* w, double* edot, cudaStream_t s)
 {
     switch (nx) {
-        case 2: return launch_lowp_nx<S, 2>(nelt, D, Glp, gscale, u, w, s);
-        case 3: return launch_lowp_nx<S, 3>(nelt, D, Glp, gscale, u, w, s);
-        case 4: return launch_lowp_nx<S, 4>(nelt, D, Glp, gscale, u, w, s);
-        case 5: return launch_lowp_nx<S, 5>(nelt, D, Glp, gscale, u, w, s);
-        case 6: return launch_lowp_nx<S, 6>(nelt, D, Glp, gscale, u, w, s);
-        case 7: return launch_lowp_nx<S, 7>(nelt, D, Glp, gscale, u, w, s);
-        case 8: return launch_lowp_nx<S, 8>(nelt, D, Glp, gscale, u, w, s);
-        case 9: return launch_lowp_nx<S, 9>(nelt, D, Glp, gscale, u, w, s);
-        case 10: return launch_lowp_nx<S, 10>(nelt, D, Glp, gscale, u, w, s);
-        case 11: return launch_lowp_nx<S, 11>(nelt, D, Glp, gscale, u, w, s);
-        case 12: return launch_lowp_nx<S, 12>(nelt, D, Glp, gscale, u, w, s);
-        case 13: return launch_lowp_nx<S, 13>(nelt, D, Glp, gscale, u, w, s);
-        case 14: return launch_lowp_nx<S, 14>(nelt, D, Glp, gscale, u, w, s);
-        case 15: return launch_lowp_nx<S, 15>(nelt, D, Glp, gscale, u, w, s);
-        case 16: return launch_lowp_nx<S, 16>(nelt, D, Glp, gscale, u, w, s);
+        case 2: return launch_lowp_nx<S, 2>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 3: return launch_lowp_nx<S, 3>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 4: return launch_lowp_nx<S, 4>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 5: return launch_lowp_nx<S, 5>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 6: return launch_lowp_nx<S, 6>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 7: return launch_lowp_nx<S, 7>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 8: return launch_lowp_nx<S, 8>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 9: return launch_lowp_nx<S, 9>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 10: return launch_lowp_nx<S, 10>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 11: return launch_lowp_nx<S, 11>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 12: return launch_lowp_nx<S, 12>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 13: return launch_lowp_nx<S, 13>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 14: return launch_lowp_nx<S, 14>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 15: return launch_lowp_nx<S, 15>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 16: return launch_lowp_nx<S, 16>(nelt, D, Glp, gscale, u, w, edot, s);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
 }
@@ -336,12 +352,12 @@ nek_status launch_ax_lowp_tc(int prec, int64_t nelt, int nx, const double* D, co
                              const float* u, float* w, cudaStream_t s);
 
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
-                          const float* u, float* w, cudaStream_t s)
+                          const float* u, float* w, cudaStream_t s, double* edot)
 {
     switch (prec) {
-        case NEK_PREC_F32: return launch_lowp_t<float>(nelt, nx, D, Glp, gscale, u, w, s);
-        case NEK_PREC_BF16: return launch_lowp_t<__nv_bfloat16>(nelt, nx, D, Glp, gscale, u, w, s);
-        case NEK_PREC_F16: return launch_lowp_t<__half>(nelt, nx, D, Glp, gscale, u, w, s);
+        case NEK_PREC_F32: return launch_lowp_t<float>(nelt, nx, D, Glp, gscale, u, w, edot, s);
+        case NEK_PREC_BF16: return launch_lowp_t<__nv_bfloat16>(nelt, nx, D, Glp, gscale, u, w, edot, s);
+        case NEK_PREC_F16: return launch_lowp_t<__half>(nelt, nx, D, Glp, gscale, u, w, edot, s);
         default: return NEK_ERR_INVALID_ARG;
     }
 }
@@ -451,12 +467,13 @@ struct MixLayout {
     float *d, *minv, *c;
     uint8_t* flags;  // owner / free byte per point for the inner solve's inner products
     pcg::Buffers<float> b;
+    double* edot;  // element energies of the inner operator (its <p,w>)
     double* parts;
     MixScalars* ms;
     size_t bytes;
 };
 
-MixLayout mix_layout(void* base_, int64_t n, bool need_minv)
+MixLayout mix_layout(void* base_, int64_t nelt, int64_t n, bool need_minv)
 {
     using pcg::align256;
     MixLayout L{};
@@ -481,6 +498,7 @@ MixLayout mix_layout(void* base_, int64_t n, bool need_minv)
     L.b.w = reinterpret_cast<float*>(take(v4));
     L.b.parts = reinterpret_cast<double*>(take(align256(sizeof(double) * 2 * kMaxReduceBlocks)));
     L.b.sc = reinterpret_cast<pcg::Scalars*>(take(align256(sizeof(pcg::Scalars))));
+    L.edot = reinterpret_cast<double*>(take(align256(sizeof(double) * std::max<int64_t>(nelt, 1))));
     L.parts = reinterpret_cast<double*>(take(align256(sizeof(double) * kMaxReduceBlocks)));
     L.ms = reinterpret_cast<MixScalars*>(take(align256(sizeof(MixScalars))));
     L.bytes = off;
@@ -550,7 +568,7 @@ nek_status nek_ax_lowp(int64_t nelt, int nx, int precision, const double* D, con
 size_t nek_cg_mixed_workspace_bytes(int64_t nelt, int nx, int need_minv)
 {
     if (nelt < 0 || nx < kMinNx || nx > kMaxNx) return 0;
-    return mix_layout(nullptr, nelt * (int64_t)nx * nx * nx, need_minv != 0).bytes;
+    return mix_layout(nullptr, nelt, nelt * (int64_t)nx * nx * nx, need_minv != 0).bytes;
 }
 
 nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
@@ -579,7 +597,7 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
     if (!ws) {
         if (check_cuda(cudaMallocAsync(&ws, bytes, s)) != NEK_OK) return NEK_ERR_NOMEM;
     }
-    MixLayout L = mix_layout(ws, n, minv == nullptr);
+    MixLayout L = mix_layout(ws, nelt, n, minv == nullptr);
     const double* mv = minv;
     const int nb = reduce_blocks(n);
     const int sb = pcg::stream_blocks(n);
@@ -588,8 +606,8 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
     auto ax64 = [&](const double* p, double* w) {
         return Gff ? launch_ax_ff(nelt, nx, D, Gff, p, w, s) : launch_ax_fp64(nelt, nx, D, G, p, w, s);
     };
-    auto ax_lo = [&](const float* p, float* w, double*, cudaStream_t ss) {
-        return launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss);
+    auto ax_lo = [&](const float* p, float* w, double* ed, cudaStream_t ss) {
+        return launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed);
     };
 
     if (!minv) {
@@ -623,8 +641,9 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
         launches += 1;
         {
             pcg::Result res;
+            const pcg::ElementEnergies ee{L.edot, nelt};  // the operator's energies give <p,w>
             nek_status si = pcg::run<float>(gs, n, L.c, mask, L.minv, L.b.w, L.d, L.b, inner_tol, max_inner, 10,
-                                           false, ax_lo, s, &res, L.flags);
+                                           false, ax_lo, s, &res, L.flags, &ee);
             inner_total += res.iters;
             launches += res.launches;
             if (si == NEK_ERR_BREAKDOWN || si == NEK_ERR_CUDA) {
