@@ -127,9 +127,10 @@ nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, co
  * per CTA where threads and shared memory allow) changes only occupancy, never
  * the arithmetic, so results are bit-identical.  nek_tune_ax times each size on
  * the given data (synchronously; u, G/Gff, w as for nek_ax / nek_ax_ff with
- * impl = NEK_AX_FP64 / NEK_AX_FF, 16-byte aligned) and keeps the fastest for
- * all later launches of that (impl, nx) in this process; *epb_out and *ms_out
- * (nullable) receive it and its time per launch.  For NEK_AX_FF the form with
+ * impl = NEK_AX_FP64 / NEK_AX_FF, 16-byte aligned; the median of 7
+ * individually timed launches) and keeps the fastest for all later launches of
+ * that (impl, nx) in this process; *epb_out and *ms_out (nullable) receive it
+ * and its time per launch.  For NEK_AX_FF the form with
  * element energies that nek_cg_solve_ex uses is tuned too (kept on its own,
  * not reported).  nek_set_ax_epb sets the size
  * directly (0 restores the built-in default; a size that does not fit the

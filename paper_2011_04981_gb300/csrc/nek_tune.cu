@@ -8,6 +8,7 @@
 // variants on the caller's data and keeps the fastest for later launches.  The
 // float-float kernel has two forms (plain, and with element energies for the
 // solve), each tuned on its own: their register allocations differ.
+#include <algorithm>
 #include <atomic>
 
 #include "nek_internal.h"
@@ -53,10 +54,11 @@ nek_status nek_tune_ax(int impl, int64_t nelt, int nx, const double* D, const vo
     const size_t bytes = sizeof(double) * (size_t)nelt * nx * nx * nx;
     if (ranges_overlap(u, bytes, w, bytes)) return NEK_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    constexpr int kReps = 7;  // individually timed launches per candidate; the median is kept
+    cudaEvent_t ev[kReps + 1] = {};
     double* edot = nullptr;  // element energies of the float-float solve form
-    nek_status st = check_cuda(cudaEventCreate(&e0));
-    if (st == NEK_OK) st = check_cuda(cudaEventCreate(&e1));
+    nek_status st = NEK_OK;
+    for (int r = 0; r <= kReps && st == NEK_OK; r++) st = check_cuda(cudaEventCreate(&ev[r]));
     if (st == NEK_OK && impl == NEK_AX_FF)
         if (check_cuda(cudaMalloc(&edot, sizeof(double) * (size_t)nelt)) != NEK_OK) st = NEK_ERR_NOMEM;
     int best_plain = 0;
@@ -80,14 +82,17 @@ nek_status nek_tune_ax(int impl, int64_t nelt, int nx, const double* D, const vo
                 break;
             }
             if ((st = run()) != NEK_OK) break;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 3 && st == NEK_OK; r++) st = run();
-            cudaEventRecord(e1, s);
+            cudaEventRecord(ev[0], s);
+            for (int r = 0; r < kReps && st == NEK_OK; r++) {
+                st = run();
+                cudaEventRecord(ev[r + 1], s);
+            }
             if (st != NEK_OK) break;
-            if ((st = check_cuda(cudaEventSynchronize(e1))) != NEK_OK) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= 3.f;
+            if ((st = check_cuda(cudaEventSynchronize(ev[kReps]))) != NEK_OK) break;
+            float t[kReps];
+            for (int r = 0; r < kReps; r++) cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+            std::sort(t, t + kReps);
+            const float ms = t[kReps / 2];
             if (best == 0 || ms < best_ms) {
                 best = cand[c];
                 best_ms = ms;
@@ -101,8 +106,8 @@ nek_status nek_tune_ax(int impl, int64_t nelt, int nx, const double* D, const vo
             best_plain_ms = best_ms;
         }
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
     if (edot) cudaFree(edot);
     if (st != NEK_OK) return st;
     if (epb_out) *epb_out = best_plain;
