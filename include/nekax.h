@@ -122,6 +122,19 @@ nek_status nek_geom_ff(int64_t nelt, int nx, const double* G, float* Gff, void* 
 nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                      void* stream);
 
+/*
+ * nek_ax_ff plus the element energies edot[e] = u_e . w_e = u_e^T A_e u_e
+ * (FP64 products and sums; each element's sum runs in an order fixed by nx
+ * alone, so it does not depend on the tuned elements per CTA).  Summed over
+ * elements this is the CG's <p, A p> (Section II-B's inner product of the
+ * direction with the assembled operator applied to it) for a p that is
+ * continuous across elements and zero on masked nodes; the FP64 solve with
+ * NEK_AX_FF takes its <p,w> this way.  edot: device, nelt doubles, 8-byte
+ * aligned, not overlapping u or w.  Async on stream.
+ */
+nek_status nek_ax_ff_energy(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+                            double* edot, void* stream);
+
 /* ------------------------------------------------------------ tuning ---
  * The AX kernels group elements into CTAs; the group size (1, 2 or 4 elements
  * per CTA where threads and shared memory allow) changes only occupancy, never

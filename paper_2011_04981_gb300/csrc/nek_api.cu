@@ -322,6 +322,22 @@ nek_status nek_gs_export(const nek_gs* gs, int64_t* offsets_host, int64_t* membe
     return NEK_OK;
 }
 
+nek_status nek_ax_ff_energy(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+                            double* edot, void* stream)
+{
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt < 0) return NEK_ERR_INVALID_ARG;
+    if (nelt == 0) return NEK_OK;
+    if (!D || !Gff || !u || !w || !edot) return NEK_ERR_INVALID_ARG;
+    if (!is_aligned(D, 8) || !is_aligned(Gff, 16) || !is_aligned(u, 8) || !is_aligned(w, 8) || !is_aligned(edot, 8))
+        return NEK_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(double) * (size_t)nelt * nx * nx * nx, ebytes = sizeof(double) * (size_t)nelt;
+    if (ranges_overlap(u, bytes, w, bytes) || ranges_overlap(edot, ebytes, u, bytes) ||
+        ranges_overlap(edot, ebytes, w, bytes))
+        return NEK_ERR_INVALID_ARG;
+    return launch_ax_ff(nelt, nx, D, Gff, u, w, static_cast<cudaStream_t>(stream), nullptr, nullptr, nullptr, edot);
+}
+
 nek_status nek_dssum(const nek_gs* gs, double* v, void* stream)
 {
     if (!gs) return NEK_ERR_INVALID_ARG;

@@ -238,10 +238,12 @@ constexpr int ff_min_blocks()
 // a CTA whose elements all belong to finished problems (eprob: problem of each
 // element, pdone: one byte per problem) returns at once (batched solves); DOT:
 // plain, and each element's energy u_e . (A_e u_e) is written to edot[e] (the
-// CG's <p, Ap> is their sum, see the solve); SKIP_DOT: both (batched solves).
-constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3, kModeSkipDot = 4;
+// CG's <p, Ap> is their sum, see the solve); SKIP_DOT, GATHER_DOT: energies
+// with the skip (batched solves) or the gather (unique-node solves).
+constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3, kModeSkipDot = 4, kModeGatherDot = 5;
 constexpr bool mode_skips(int m) { return m == kModeSkip || m == kModeSkipDot; }
-constexpr bool mode_energies(int m) { return m == kModeDot || m == kModeSkipDot; }
+constexpr bool mode_gathers(int m) { return m == kModeGather || m == kModeGatherDot; }
+constexpr bool mode_energies(int m) { return m == kModeDot || m == kModeSkipDot || m == kModeGatherDot; }
 
 // True when every element of the CTA belongs to a finished problem.
 template <int MODE>
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
         sDT[(q % NX) * NX + q / NX] = d;
     }
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
-    if constexpr (MODE == kModeGather) {
+    if constexpr (mode_gathers(MODE)) {
         const int32_t* idx = l2g + e0 * N3;
         for (int q = tid; q < ne * N3; q += NT) sU[q] = split_double(__ldg(u + __ldg(idx + q)));
     } else {
@@ -408,6 +410,7 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
         const float2* wse = sWs + el * N3;
         const float2* wte = sWt + el * N3;
         const double* ug = u + (e0 + el) * (int64_t)N3;
+        const int32_t* ig = l2g + (e0 + el) * (int64_t)N3;  // gather modes: u(p) = u[ig[p]]
         const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
                     mwt = sMax[4 * el + 3] * 1.0001f;
         const float bij = sCol[i] * mwr + sCol[j] * mws;
@@ -446,7 +449,8 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
                 const int p = i + NX * (j + NX * (k0 + q));
                 const double wv = join_pair(L::get(hi, q), L::get(lo, q));
                 we[p] = wv;
-                if constexpr (mode_energies(MODE)) energy = fma(__ldg(ug + p), wv, energy);
+                if constexpr (mode_energies(MODE))
+                    energy = fma(mode_gathers(MODE) ? __ldg(u + __ldg(ig + p)) : __ldg(ug + p), wv, energy);
             }
         }
     }
@@ -514,7 +518,7 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
         for (int q = tid; q < ne * N3; q += NT) {
             const int el = q / N3, p = q - el * N3;
             const int k = p / N2, ji = p - k * N2;
-            const float2 v = split_double(MODE == kModeGather ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
+            const float2 v = split_double(mode_gathers(MODE) ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
             float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
             dst[k & 1] = v.x;
             dst[2 + (k & 1)] = v.y;
@@ -625,6 +629,7 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
         const float4* wre = WR4 + el * PB;
         const float4* wse = WS4 + el * PB;
         const double* ug = u + (e0 + el) * (int64_t)N3 + i + NX * j;  // u(i, j, k) at ug[k * N2]
+        const int32_t* ig = l2g + (e0 + el) * (int64_t)N3 + i + NX * j;  // gather modes: at u[ig[k * N2]]
         const float2* wte = WT2 + el * N3 + i + NX * j;  // wt(i, j, l) at wte[l * N2]
         const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
                     mwt = sMax[4 * el + 3] * 1.0001f;
@@ -635,8 +640,13 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
             const int k0 = 2 * kp;
             double u0 = 0.0, u1 = 0.0;
             if constexpr (mode_energies(MODE)) {  // issued here, used after the contraction
-                u0 = __ldg(ug + k0 * N2);
-                u1 = __ldg(ug + (k0 + 1) * N2);
+                if constexpr (mode_gathers(MODE)) {
+                    u0 = __ldg(u + __ldg(ig + k0 * N2));
+                    u1 = __ldg(u + __ldg(ig + (k0 + 1) * N2));
+                } else {
+                    u0 = __ldg(ug + k0 * N2);
+                    u1 = __ldg(ug + (k0 + 1) * N2);
+                }
             }
             OffsetAcc<T> acc;
             acc.init(make_float2(offset_for(bij + sCol[k0] * mwt), offset_for(bij + sCol[k0 + 1] * mwt)));
@@ -713,6 +723,8 @@ nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff,
                                 cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
                                 double* edot)
 {
+    if (l2g && edot)
+        return launch_ax_ff_kernel<NX, EPB, kModeGatherDot>(nelt, D, Gff, u, w, s, l2g, nullptr, nullptr, edot);
     if (l2g)
         return launch_ax_ff_kernel<NX, EPB, kModeGather>(nelt, D, Gff, u, w, s, l2g, nullptr, nullptr, nullptr);
     if (eprob && pdone && edot)

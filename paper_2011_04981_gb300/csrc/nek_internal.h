@@ -61,9 +61,9 @@ nek_status launch_ax_fp64_epb(int epb, int64_t nelt, int nx, const double* D, co
 // eprob, pdone (optional, batched solves): problem of each element of the
 // launch and one byte per problem, nonzero once it has finished; CTAs whose
 // elements all belong to finished problems do nothing.
-// edot (optional, nelt doubles; not with l2g): edot[e] = u_e . w_e, the
-// element's energy, summed in an order fixed by nx alone (with eprob/pdone,
-// skipped elements' entries are left as they were).
+// edot (optional, nelt doubles): edot[e] = u_e . w_e, the element's energy
+// (u_e gathered through l2g when given), summed in an order fixed by nx alone
+// (with eprob/pdone, skipped elements' entries are left as they were).
 nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
                             double* w, cudaStream_t s, const int32_t* l2g = nullptr, const int32_t* eprob = nullptr,
                             const uint8_t* pdone = nullptr, double* edot = nullptr);

@@ -90,10 +90,11 @@ bool lvec_ok(const nek_lvec* lv, int64_t nelt, int nx)
     return lv && nelt >= 0 && nx >= kMinNx && nx <= kMaxNx && lv->npts == nelt * (int64_t)nx * nx * nx;
 }
 
+// edot (optional): element energies uL_e . (A_e uL_e) of the gathered field.
 nek_status lvec_ax(const nek_lvec* lv, int64_t nelt, int nx, const double* D, const float* Gff, const double* uL,
-                   double* wL, double* wE, cudaStream_t s)
+                   double* wL, double* wE, cudaStream_t s, double* edot = nullptr)
 {
-    nek_status st = launch_ax_ff(nelt, nx, D, Gff, uL, wE, s, lv->d_l2g);
+    nek_status st = launch_ax_ff(nelt, nx, D, Gff, uL, wE, s, lv->d_l2g, nullptr, nullptr, edot);
     if (st != NEK_OK) return st;
     k_lv_assemble<<<stream_blocks(lv->nl), 256, 0, s>>>(lv->nl, lv->d_off, lv->d_mem, wE, wL);
     return check_launch();
@@ -258,6 +259,7 @@ size_t nek_lvec_cg_workspace_bytes(const nek_lvec* lv)
     if (!lv) return 0;
     const size_t vec = pcg::align256(sizeof(double) * std::max<int64_t>(lv->nl, 1));
     return 3 * vec + pcg::align256(sizeof(double) * std::max<int64_t>(lv->npts, 1)) +
+           pcg::align256(sizeof(double) * std::max<int64_t>(lv->npts, 1)) +  // element energies (<= npts)
            pcg::align256(sizeof(double) * 2 * kMaxReduceBlocks) + pcg::align256(sizeof(pcg::Scalars));
 }
 
@@ -297,16 +299,20 @@ nek_status nek_lvec_cg_solve(const nek_lvec* lv, int64_t nelt, int nx, const dou
     b.w = reinterpret_cast<double*>(base + 2 * vec);
     double* wE = reinterpret_cast<double*>(base + 3 * vec);
     size_t off = 3 * vec + pcg::align256(sizeof(double) * lv->npts);
+    double* edot = reinterpret_cast<double*>(base + off);  // nelt entries
+    off += pcg::align256(sizeof(double) * lv->npts);
     b.parts = reinterpret_cast<double*>(base + off);
     off += pcg::align256(sizeof(double) * 2 * kMaxReduceBlocks);
     b.sc = reinterpret_cast<pcg::Scalars*>(base + off);
 
     pcg::Result res;
-    auto ax = [&](const double* p, double* w, double*, cudaStream_t ss) {
-        return lvec_ax(lv, nelt, nx, D, Gff, p, w, wE, ss);
+    // the operator's element energies give <p,w> (p is zero on masked nodes)
+    auto ax = [&](const double* p, double* w, double* ed, cudaStream_t ss) {
+        return lvec_ax(lv, nelt, nx, D, Gff, p, w, wE, ss, ed);
     };
+    const pcg::ElementEnergies ee{edot, nelt};
     st = pcg::run<double>(nullptr, lv->nl, static_cast<const double*>(nullptr), lv->d_mask, minvL, fL, xL, b, tol_rel,
-                          max_iter, check_every, time_ax, ax, s, &res);
+                          max_iter, check_every, time_ax, ax, s, &res, nullptr, &ee);
     if (iters_out) *iters_out = res.iters;
     if (relres_out) *relres_out = res.relres;
     if (opts) {

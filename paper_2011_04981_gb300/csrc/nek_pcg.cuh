@@ -255,11 +255,12 @@ __global__ void __launch_bounds__(NT) k_alpha(const double* __restrict__ parts, 
     }
 }
 
-// r -= alpha w; partials of <r,r>_c and <r,z>_c with z = minv r (not stored)
+// r -= alpha mask.w; partials of <r,r>_c and <r,z>_c with z = minv r (not stored)
 template <class V>
 __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ c, const V* __restrict__ minv,
                                                 const V* __restrict__ w, V* __restrict__ r, double* __restrict__ parts,
-                                                const Scalars* __restrict__ sc, const uint8_t* __restrict__ flags)
+                                                const Scalars* __restrict__ sc, const uint8_t* __restrict__ flags,
+                                                const uint8_t* __restrict__ mask)
 {
     __shared__ double sh[NT / 32];
     if (halted(sc)) return;
@@ -283,7 +284,9 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
         }
     } else {
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
-            const V rq = fma(-alpha, w[q], r[q]);
+            V wv = w[q];
+            if (!mask[q]) wv = V(0);  // the mask (already applied when k_pw ran)
+            const V rq = fma(-alpha, wv, r[q]);
             const V zq = minv[q] * rq;
             r[q] = rq;
             const double wq = cw(c, q);
@@ -365,7 +368,8 @@ struct Result {
 };
 
 // The element-energy path (see the top of this file): the operator writes
-// edot[e] = p_e . (A_e p_e) for its nelt elements.  Requires point flags.
+// edot[e] = p_e . (A_e p_e) for its nelt elements (k_update applies the mask,
+// from the point flags or the mask array).
 struct ElementEnergies {
     double* edot;
     int64_t nelt;
@@ -438,7 +442,7 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
             k_alpha<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
             launches += 1;
         }
-        k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.w, b.r, b.parts, b.sc, flags);
+        k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.w, b.r, b.parts, b.sc, flags, mask);
         k_beta<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
         k_p<V><<<sb, 256, 0, s>>>(n, minv, b.r, x, b.p, b.sc, it < max_iter ? 1 : 0);
         launches += 6;  // the operator, dssum, k_alpha, k_update, k_beta, k_p

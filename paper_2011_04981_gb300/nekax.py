@@ -84,6 +84,7 @@ _SIGS = {
     "nek_ax": ([_I64, _I, _P, _P, _P, _P, _P], _I),
     "nek_geom_ff": ([_I64, _I, _P, _P, _P], _I),
     "nek_ax_ff": ([_I64, _I, _P, _P, _P, _P, _P], _I),
+    "nek_ax_ff_energy": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_gs_create": ([_I64, _I, _P, ctypes.POINTER(_P)], _I),
     "nek_gs_destroy": ([_P], _I),
     "nek_gs_info": ([_P, _P, _P, _P], _I),
@@ -222,6 +223,12 @@ def geom_ff(nelt, nx, G, Gff, stream=None):
 
 def ax_ff(nelt, nx, D, Gff, u, w, stream=None):
     _check("nek_ax_ff", load().nek_ax_ff(nelt, nx, _ptr(D), _ptr(Gff), _ptr(u), _ptr(w), _stream(stream)))
+
+
+def ax_ff_energy(nelt, nx, D, Gff, u, w, edot, stream=None):
+    """w = AX u (float-float) and edot[e] = u_e . w_e."""
+    _check("nek_ax_ff_energy", load().nek_ax_ff_energy(nelt, nx, _ptr(D), _ptr(Gff), _ptr(u), _ptr(w), _ptr(edot),
+                                                       _stream(stream)))
 
 
 def mask(n, m, v, stream=None):

@@ -117,6 +117,11 @@ def test_ff_entry_points_reject_bad_arguments(lib):
     assert L.nek_ax_ff(4, 8, A16, A16 + 8, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # Gff misaligned
     assert L.nek_ax_ff(4, 8, A16, A16, A16 + 4, A16 * 2, None) == nekax.ERR_INVALID_ARG  # u misaligned
     assert L.nek_ax_ff(4, 8, A16, A16, A16, A16 + 4096, None) == nekax.ERR_INVALID_ARG  # overlap
+    assert L.nek_ax_ff_energy(4, 1, A16, A16, A16, A16 * 2, A16 * 4, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_ax_ff_energy(0, 8, None, None, None, None, None, None) == nekax.OK
+    assert L.nek_ax_ff_energy(4, 8, A16, A16, A16, A16 * 2, None, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_ff_energy(4, 8, A16, A16, A16, A16 * 2, A16 * 4 + 4, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_ff_energy(4, 8, A16, A16, A16, A16 * 2, A16 * 2 + 64, None) == nekax.ERR_INVALID_ARG  # on w
     assert L.nek_geom_ff(4, 1, A16, A16, None) == nekax.ERR_UNSUPPORTED_NX
     assert L.nek_geom_ff(4, 4, A16, A16 + 8, None) == nekax.ERR_INVALID_ARG
     assert L.nek_geom_ff(4, 4, A16, A16 + 64, None) == nekax.ERR_INVALID_ARG  # overlap

@@ -283,6 +283,42 @@ def test_ax_ff_parity_sweep(nx, nelt):
     assert _rel(w, ref.ax(D, G, u)) <= TOL_AX
 
 
+@pytest.mark.parametrize("nx", [3, 8, 10, 13])
+def test_ax_ff_energy_matches_oracle_and_ignores_epb(nx):
+    """edot[e] = u_e . (A_e u_e): against the oracle's operator, and bit-identical whatever the tuned
+    elements per CTA (each element's sum runs in an order fixed by nx)."""
+    rng = np.random.default_rng(40 + nx)
+    nelt = 11
+    xi, rho, D = ref.gll(nx)
+    mesh = inputs.box_mesh(nelt, 1, 1, nx, perturb=0.2, seed=nx)
+    G = ref.geom(mesh.corners, nx, xi, rho)
+    u = rng.uniform(-1, 1, size=(nelt, nx ** 3))
+    Gff = torch.empty((nelt, nx ** 3, 12), dtype=torch.float32, device=DEV)
+    nekax.geom_ff(nelt, nx, _t(G), Gff)
+    wr = ref.ax(D, G, u)
+    eref = np.einsum("ep,ep->e", u, wr)
+    bound = 1e-12 * np.abs(wr).max(axis=1) * np.abs(u).sum(axis=1) + 1e-13 * np.abs(u * wr).sum(axis=1)
+    lib = nekax.load()
+    outs = []
+    try:
+        for epb in (1, 2, 4):
+            if lib.nek_set_ax_epb(int(nekax.AX_FF), nx, epb) != nekax.OK:
+                continue
+            w = torch.full((nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+            ed = torch.full((nelt,), float("nan"), dtype=torch.float64, device=DEV)
+            nekax.ax_ff_energy(nelt, nx, _t(D), Gff, _t(u), w, ed)
+            torch.cuda.synchronize()
+            assert _rel(w.cpu().numpy(), wr) <= TOL_AX
+            e = ed.cpu().numpy()
+            assert np.all(np.abs(e - eref) <= bound), (epb, np.max(np.abs(e - eref) / bound))
+            outs.append(e)
+    finally:
+        lib.nek_set_ax_epb(int(nekax.AX_FF), nx, 0)
+    assert len(outs) >= 1
+    for e in outs[1:]:
+        assert np.array_equal(e, outs[0])
+
+
 def test_geom_ff_split_is_faithful():
     nx = 7
     mesh = inputs.box_mesh(3, 2, 2, nx, perturb=0.2, seed=4)
