@@ -61,6 +61,8 @@ def parse():
                     help="also time the unique-node (L-vector) solve against the E-vector solve")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the elements-per-CTA tuning (nek_tune_ax) before timing")
+    ap.add_argument("--epb", type=int, default=0,
+                    help="fix the AX elements per CTA (1, 2 or 4; nek_set_ax_epb) instead of tuning")
     ap.add_argument("--ax", default="ff", choices=["fp64", "ff"],
                     help="AX operator inside the solve: native FP64 or FP64-accurate float-float")
     return ap.parse_args()
@@ -488,10 +490,14 @@ def run_native(args):
     ax_impl = nekax.AX_FF if args.ax == "ff" else nekax.AX_FP64
     if ax_impl == nekax.AX_FF:
         P.prepare_ff()
-    if args.tune:
+    if args.epb:
+        if nekax.load().nek_set_ax_epb(int(ax_impl), nx, args.epb) != nekax.OK:
+            raise SystemExit("--epb %d does not fit the AX kernel at nx = %d" % (args.epb, nx))
+    elif args.tune:
         wt = torch.empty_like(f)
         nekax.tune_ax(ax_impl, mesh.nelt, nx, P.D, P.Gff if ax_impl == nekax.AX_FF else P.G, f, wt)
         del wt
+    ax_epb = nekax.load().nek_get_ax_epb(int(nekax.AX_FF_ENERGY if ax_impl == nekax.AX_FF else ax_impl), nx)
     for _ in range(args.warmup):
         P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, ax_impl=ax_impl)
     torch.cuda.synchronize()
@@ -581,7 +587,7 @@ def run_native(args):
         "gpu_launches": launches,
         "ax": {"gdofs": ax_gdofs, "ms_per_launch": ax_t * 1e3, "gflops": flops / ax_t / 1e9,
                "hbm_gbs": 64 * pts / ax_t / 1e9, "hbm_frac": 64 * pts / ax_t / 1e9 / hbm, "launches": ax_n,
-               "share_of_step": ax_ms / 1e3 / t_dev},
+               "share_of_step": ax_ms / 1e3 / t_dev, "elements_per_cta": ax_epb or "default"},
         "roofline": ({"bound": "alu", "achieved": flops / ax_t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                       "frac": flops / ax_t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic,
                       "kernel": "k_ax_fp64<%d>" % nx,

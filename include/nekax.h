@@ -53,8 +53,10 @@ typedef enum {
 
 /* Which AX operator a call uses. */
 typedef enum {
-    NEK_AX_FP64 = 0, /* nek_ax: native FP64 */
-    NEK_AX_FF = 1    /* nek_ax_ff: FP64-accurate float-float on the FP32 pipes; needs Gff */
+    NEK_AX_FP64 = 0,      /* nek_ax: native FP64 */
+    NEK_AX_FF = 1,        /* nek_ax_ff: FP64-accurate float-float on the FP32 pipes; needs Gff */
+    NEK_AX_FF_ENERGY = 2  /* nek_ax_ff's element-energy form (nek_ax_ff_energy and the solves):
+                             for nek_set_ax_epb / nek_get_ax_epb only */
 } nek_ax_impl;
 
 /* Opaque gather-scatter plan (see nek_gs_create). */
@@ -147,8 +149,9 @@ nek_status nek_ax_ff_energy(int64_t nelt, int nx, const double* D, const float* 
  * element energies that nek_cg_solve_ex uses is tuned too (kept on its own,
  * not reported).  nek_set_ax_epb sets the size
  * directly (0 restores the built-in default; a size that does not fit the
- * kernel's thread or shared-memory limits for that nx is NEK_ERR_INVALID_ARG);
- * nek_get_ax_epb reads it back.
+ * kernel's thread or shared-memory limits for that nx is NEK_ERR_INVALID_ARG;
+ * NEK_AX_FF sets both float-float forms, NEK_AX_FF_ENERGY the energy form
+ * only); nek_get_ax_epb reads it back (0 = the built-in default).
  * These settings are process-wide.  No paper counterpart: the paper picks its
  * FPGA kernel count by hand (Section IV).
  */

@@ -50,7 +50,7 @@ void gll_host(int nx, double* xi, double* rho, double* D);
 // Elements per CTA of the AX kernels: 0 = built-in default, else the value chosen
 // by nek_tune_ax for (impl, nx); impl kAxFfEnergy is the float-float kernel in
 // its element-energy form.
-constexpr int kAxFfEnergy = 2;
+constexpr int kAxFfEnergy = NEK_AX_FF_ENERGY;
 int tuned_epb(int impl, int nx);
 bool ax_fp64_epb_fits(int nx, int epb);
 bool ax_ff_epb_fits(int nx, int epb);

@@ -33,16 +33,19 @@ extern "C" {
 
 nek_status nek_set_ax_epb(int impl, int nx, int epb)
 {
-    if (impl != NEK_AX_FP64 && impl != NEK_AX_FF) return NEK_ERR_INVALID_ARG;
+    if (impl != NEK_AX_FP64 && impl != NEK_AX_FF && impl != NEK_AX_FF_ENERGY) return NEK_ERR_INVALID_ARG;
     if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
-    if (epb != 0 && !(impl == NEK_AX_FF ? ax_ff_epb_fits(nx, epb) : ax_fp64_epb_fits(nx, epb)))
+    if (epb != 0 && !(impl == NEK_AX_FP64 ? ax_fp64_epb_fits(nx, epb) : ax_ff_epb_fits(nx, epb)))
         return NEK_ERR_INVALID_ARG;  // not one of the compiled counts, or too many threads / too much smem
     g_epb[impl][nx].store(epb, std::memory_order_relaxed);
     if (impl == NEK_AX_FF) g_epb[kAxFfEnergy][nx].store(epb, std::memory_order_relaxed);
     return NEK_OK;
 }
 
-int nek_get_ax_epb(int impl, int nx) { return tuned_epb(impl, nx); }
+int nek_get_ax_epb(int impl, int nx)
+{
+    return impl == NEK_AX_FP64 || impl == NEK_AX_FF || impl == NEK_AX_FF_ENERGY ? tuned_epb(impl, nx) : 0;
+}
 
 nek_status nek_tune_ax(int impl, int64_t nelt, int nx, const double* D, const void* Gx, const double* u, double* w,
                        int* epb_out, float* ms_out, void* stream)

@@ -42,6 +42,7 @@ class NekError(RuntimeError):
 
 AX_FP64 = 0
 AX_FF = 1
+AX_FF_ENERGY = 2  # the element-energy form, for nek_set_ax_epb / nek_get_ax_epb
 
 
 class NekCgOpts(ctypes.Structure):

@@ -140,6 +140,11 @@ def test_tuning_and_lowp_entry_points_reject_bad_arguments(lib):
     assert L.nek_set_ax_epb(1, 16, 4) == nekax.ERR_INVALID_ARG  # 4 x 1024 threads does not fit
     assert L.nek_set_ax_epb(1, 8, 2) == nekax.OK and L.nek_get_ax_epb(1, 8) == 2
     assert L.nek_set_ax_epb(1, 8, 0) == nekax.OK and L.nek_get_ax_epb(1, 8) == 0
+    # NEK_AX_FF sets both float-float forms; NEK_AX_FF_ENERGY the energy form alone
+    assert L.nek_set_ax_epb(1, 8, 4) == nekax.OK and L.nek_get_ax_epb(2, 8) == 4
+    assert L.nek_set_ax_epb(2, 8, 1) == nekax.OK and L.nek_get_ax_epb(2, 8) == 1 and L.nek_get_ax_epb(1, 8) == 4
+    assert L.nek_set_ax_epb(1, 8, 0) == nekax.OK and L.nek_get_ax_epb(2, 8) == 0
+    assert L.nek_get_ax_epb(7, 8) == 0
     assert L.nek_tune_ax(0, 0, 8, A16, A16, A16, A16 * 2, None, None, None) == nekax.ERR_INVALID_ARG
     assert L.nek_tune_ax(0, 4, 8, A16, A16 + 8, A16, A16 * 2, None, None, None) == nekax.ERR_INVALID_ARG
     assert L.nek_tune_ax(0, 4, 8, A16, A16, A16, A16 + 64, None, None, None) == nekax.ERR_INVALID_ARG
