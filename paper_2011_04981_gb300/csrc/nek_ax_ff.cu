@@ -692,11 +692,13 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
 // resident warps per SM, fewer than k_ax_ffe's 13.5 busy ones.)
 constexpr int ffi_tpe(int) { return 128; }
 
+// CTAs per SM the register budget is set for: 20 resident warps (96 registers
+// a thread at one element per CTA; the kernel then spills 4-8 bytes).
 template <int NX, int EPB>
 constexpr int ffi_min_blocks()
 {
     constexpr int warps = (ffi_tpe(NX) * EPB + 31) / 32;
-    return warps >= 16 ? 1 : (16 / warps > 5 ? 5 : 16 / warps);
+    return warps >= 20 ? 1 : 20 / warps;
 }
 
 template <int NX, int EPB, int MODE>
