@@ -233,14 +233,17 @@ __global__ void __launch_bounds__(NT) k_pw(int64_t n, const V* __restrict__ c, c
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
 }
 
-__global__ void __launch_bounds__(NT) k_alpha(const double* __restrict__ parts, int nb, Scalars* sc)
+// NTA threads sum the nb partials (1024 for the nelt element energies, whose
+// loads then overlap better).
+template <int NTA = NT>
+__global__ void __launch_bounds__(NTA) k_alpha(const double* __restrict__ parts, int nb, Scalars* sc)
 {
-    __shared__ double sh[NT / 32];
+    __shared__ double sh[NTA / 32];
     if (halted(sc)) {
         if (threadIdx.x == 0) sc->xpend = 0;
         return;
     }
-    const double pw = sum_partials<NT>(parts, nb, sh);
+    const double pw = sum_partials<NTA>(parts, nb, sh);
     if (threadIdx.x == 0) {
         sc->it += 1;
         sc->pw = pw;
@@ -436,10 +439,10 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
         if (timed) cudaEventRecord(ev[2 * (it - 1) + 1], s);
         if ((st = dssum<V>(gs, b.w, s)) != NEK_OK) goto done;
         if (ee) {
-            k_alpha<<<1, NT, 0, s>>>(ee->edot, static_cast<int>(ee->nelt), b.sc);
+            k_alpha<1024><<<1, 1024, 0, s>>>(ee->edot, static_cast<int>(ee->nelt), b.sc);
         } else {
             k_pw<V><<<nb, NT, 0, s>>>(n, c, mask, b.p, b.w, b.parts, b.sc, flags);
-            k_alpha<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
+            k_alpha<><<<1, NT, 0, s>>>(b.parts, nb, b.sc);
             launches += 1;
         }
         k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.w, b.r, b.parts, b.sc, flags, mask);
