@@ -595,7 +595,7 @@ def run_native(args):
                               "1.25 TFLOP/s); HBM %s peak %.0f GB/s" % (hbm_kind, hbm)}
                      if args.ax == "fp64" else
                      {"bound": "hbm", "achieved": 64 * pts / ax_t / 1e9, "peak": hbm, "unit": "GB/s",
-                      "frac": 64 * pts / ax_t / 1e9 / hbm, "traffic": traffic, "kernel": ("k_ax_ffe<%d>" if nx in (10, 12) else "k_ax_ff<%d>") % nx,
+                      "frac": 64 * pts / ax_t / 1e9 / hbm, "traffic": traffic, "kernel": ("k_ax_ffi<%d>" if nx == 10 else "k_ax_ffe<%d>" if nx == 12 else "k_ax_ff<%d>") % nx,
                       "note": "FP64-accurate float-float AX, 64 algorithmic B/point (u 8 + G 48 + w 8); peak = %s "
                               "HBM copy; its instruction limit is the FP32 pipe (see profiles)" % hbm_kind}),
         "clocks": clk,
