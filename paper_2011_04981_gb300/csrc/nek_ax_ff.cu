@@ -719,7 +719,8 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
     float4* DS = reinterpret_cast<float4*>(WT2 + EPB * N3);    // DS[a*NX+b] = (Dh,Dh,Dl,Dl) of D[a][b]
     float4* DP = DS + N2;              // DP[l*NP+kp]  = (Dh[2kp][l], Dh[2kp+1][l], Dl[2kp][l], Dl[2kp+1][l])
     float4* DPT = DP + NX * NP;        // DPT[l*NP+kp] = (Dh[l][2kp], Dh[l][2kp+1], Dl[l][2kp], Dl[l][2kp+1])
-    float* sRow = reinterpret_cast<float*>(DPT + NX * NP);
+    float4* DSt = DPT + NX * NP;       // DSt[b*NX+a] = DS[a*NX+b]: the r-contraction's row of D read across i
+    float* sRow = reinterpret_cast<float*>(DSt + N2);
     float* sCol = sRow + NX;
     float* sMax = sCol + NX;
 
@@ -732,6 +733,7 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
         const int a = q / NX, b = q % NX;
         const float2 d = split_double(D[q]);
         DS[q] = make_float4(d.x, d.x, d.y, d.y);
+        DSt[b * NX + a] = make_float4(d.x, d.x, d.y, d.y);
         float* dp = reinterpret_cast<float*>(DP + b * NP + a / 2);  // D[a][b]: k = a, l = b
         dp[a & 1] = d.x;
         dp[2 + (a & 1)] = d.y;
@@ -803,7 +805,7 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
                 if ((l & 1) == 0) cu = uc[(l >> 1) * N2];
                 const float ch = (l & 1) ? cu.y : cu.x, cl = (l & 1) ? cu.w : cu.z;
                 const float4 a = ur[l], b = us[l * NX];
-                const float4 dr = DS[i * NX + l], ds = DS[j * NX + l], dt = DP[l * NP + kp];
+                const float4 dr = DSt[l * NX + i], ds = DS[j * NX + l], dt = DP[l * NP + kp];
                 ar.add(make_float2(dr.x, dr.y), make_float2(dr.z, dr.w), make_float2(a.x, a.y),
                        make_float2(a.z, a.w));
                 as.add(make_float2(ds.x, ds.y), make_float2(ds.z, ds.w), make_float2(b.x, b.y),
@@ -921,7 +923,9 @@ constexpr bool ff_item_layout()
 template <int NX, int EPB>
 constexpr size_t ff_variant_smem()
 {
-    if constexpr (ff_packed_layout<NX>())
+    if constexpr (ff_item_layout<NX>())
+        return ffe_smem_bytes<NX>(EPB) + sizeof(float4) * NX * NX;  // + the transposed D table
+    else if constexpr (ff_packed_layout<NX>())
         return ffe_smem_bytes<NX>(EPB);
     else
         return ff_smem_bytes<NX, EPB>();
