@@ -241,11 +241,17 @@ constexpr int ff_min_blocks()
 // element, pdone: one byte per problem) returns at once (batched solves); DOT:
 // plain, and each element's energy u_e . (A_e u_e) is written to edot[e] (the
 // CG's <p, Ap> is their sum, see the solve); SKIP_DOT, GATHER_DOT: energies
-// with the skip (batched solves) or the gather (unique-node solves).
-constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3, kModeSkipDot = 4, kModeGatherDot = 5;
+// with the skip (batched solves) or the gather (unique-node solves); DIR_DOT
+// (item-mapped kernel): energies, the input being the solve's direction after
+// the update that the kernel applies as it loads it (DirUpdate).
+constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3, kModeSkipDot = 4, kModeGatherDot = 5,
+              kModeDirDot = 6;
 constexpr bool mode_skips(int m) { return m == kModeSkip || m == kModeSkipDot; }
 constexpr bool mode_gathers(int m) { return m == kModeGather || m == kModeGatherDot; }
-constexpr bool mode_energies(int m) { return m == kModeDot || m == kModeSkipDot || m == kModeGatherDot; }
+constexpr bool mode_energies(int m)
+{
+    return m == kModeDot || m == kModeSkipDot || m == kModeGatherDot || m == kModeDirDot;
+}
 
 // True when every element of the CTA belongs to a finished problem.
 template <int MODE>
@@ -705,7 +711,8 @@ template <int NX, int EPB, int MODE>
 __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>()))
     k_ax_ffi(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
              const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g,
-             const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot)
+             const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot,
+             DirUpdate dir)
 {
     static_assert(NX % 2 == 0 && NX <= 12, "even nx up to 12");
     using T = float2;
@@ -745,13 +752,54 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
     {
         const double* src = u + e0 * N3;
         const int32_t* idx = l2g + e0 * N3;  // used in the gather modes only
-        for (int q = tid; q < ne * N3; q += NT) {
+        bool dir_x = false, dir_p = false;   // DIR_DOT: which updates apply
+        double dir_a = 0.0, dir_b = 0.0;
+        if constexpr (MODE == kModeDirDot) {
+            dir_x = dir.sc->xpend != 0;
+            dir_p = !(dir.sc->done || dir.sc->status != NEK_OK);
+            dir_a = dir.sc->alpha;
+            dir_b = dir.sc->beta;
+        }
+        auto stage = [&](int q, double val) {  // split u(q) into the k-pair layout
             const int el = q / N3, p = q - el * N3;
             const int k = p / N2, ji = p - k * N2;
-            const float2 v = split_double(mode_gathers(MODE) ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
+            const float2 v = split_double(val);
             float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
             dst[k & 1] = v.x;
             dst[2 + (k & 1)] = v.y;
+        };
+        if constexpr (MODE == kModeDirDot) {
+            // the solve's x / direction update, with the operations of its separate pass; four
+            // points per thread at a time, all loads issued before the stores
+            constexpr int B = 4;
+            for (int q0 = tid; q0 < ne * N3; q0 += B * NT) {
+                double pv[B], xv[B], mv[B], rv[B];
+#pragma unroll
+                for (int m = 0; m < B; m++) {
+                    const int q = q0 + m * NT;
+                    const int64_t g = e0 * N3 + (q < ne * N3 ? q : 0);
+                    pv[m] = dir.p[g];
+                    xv[m] = dir_x ? dir.x[g] : 0.0;
+                    mv[m] = dir.minv[g];
+                    rv[m] = dir.r[g];
+                }
+#pragma unroll
+                for (int m = 0; m < B; m++) {
+                    const int q = q0 + m * NT;
+                    if (q >= ne * N3) break;
+                    const int64_t g = e0 * N3 + q;
+                    double val = pv[m];
+                    if (dir_x) dir.x[g] = fma(dir_a, val, xv[m]);
+                    if (dir_p) {
+                        val = fma(dir_b, val, mv[m] * rv[m]);
+                        dir.p[g] = val;
+                    }
+                    stage(q, val);
+                }
+            }
+        } else {
+            for (int q = tid; q < ne * N3; q += NT)
+                stage(q, mode_gathers(MODE) ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
         }
     }
     __syncthreads();
@@ -866,7 +914,11 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
             const int p0 = c + N2 * k0;
             double u0 = 0.0, u1 = 0.0;
             if constexpr (mode_energies(MODE)) {  // issued here, used after the contraction
-                if constexpr (mode_gathers(MODE)) {
+                if constexpr (MODE == kModeDirDot) {  // written by this CTA: plain loads
+                    const double* pe = dir.p + (e0 + el) * (int64_t)N3;
+                    u0 = pe[p0];
+                    u1 = pe[p0 + N2];
+                } else if constexpr (mode_gathers(MODE)) {
                     u0 = __ldg(u + __ldg(ig + p0));
                     u1 = __ldg(u + __ldg(ig + p0 + N2));
                 } else {
@@ -934,7 +986,7 @@ constexpr size_t ff_variant_smem()
 template <int NX, int EPB, int MODE>
 nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
                                cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
-                               double* edot)
+                               double* edot, const DirUpdate* dir = nullptr)
 {
     constexpr size_t smem = ff_variant_smem<NX, EPB>();
     static std::atomic<uint64_t> configured{0};
@@ -945,7 +997,8 @@ nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, 
             nek_status st = ensure_dyn_smem(k_ax_ffi<NX, EPB, MODE>, smem, configured);
             if (st != NEK_OK) return st;
             k_ax_ffi<NX, EPB, MODE><<<(unsigned)blocks, ffi_tpe(NX) * EPB, smem, s>>>(
-                nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot);
+                nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot,
+                dir ? *dir : DirUpdate{});
         } else {
             nek_status st = ensure_dyn_smem(k_ax_ffe<NX, EPB, MODE>, smem, configured);
             if (st != NEK_OK) return st;
@@ -964,8 +1017,17 @@ nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, 
 template <int NX, int EPB>
 nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
                                 cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
-                                double* edot)
+                                double* edot, const DirUpdate* dir)
 {
+    if (dir) {
+        if constexpr (ff_item_layout<NX>()) {
+            if (!edot || l2g || eprob) return NEK_ERR_INVALID_ARG;
+            return launch_ax_ff_kernel<NX, EPB, kModeDirDot>(nelt, D, Gff, dir->p, w, s, nullptr, nullptr, nullptr,
+                                                             edot, dir);
+        } else {
+            return NEK_ERR_INVALID_ARG;
+        }
+    }
     if (l2g && edot)
         return launch_ax_ff_kernel<NX, EPB, kModeGatherDot>(nelt, D, Gff, u, w, s, l2g, nullptr, nullptr, edot);
     if (l2g)
@@ -990,27 +1052,27 @@ constexpr bool ff_fits()
 template <int NX>
 nek_status launch_ax_ff_nx(int epb, int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
                            cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
-                           double* edot)
+                           double* edot, const DirUpdate* dir)
 {
     if (epb <= 0) epb = ff_epb<NX>();
     switch (epb) {
         case 1:
             if constexpr (ff_fits<NX, 1>())
-                return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+                return launch_ax_ff_variant<NX, 1>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
             break;
         case 2:
             if constexpr (ff_fits<NX, 2>())
-                return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+                return launch_ax_ff_variant<NX, 2>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
             break;
         case 4:
             if constexpr (ff_fits<NX, 4>())
-                return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+                return launch_ax_ff_variant<NX, 4>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
             break;
         default:
             break;
     }
     if constexpr (ff_epb<NX>() != 1 && ff_epb<NX>() != 2 && ff_epb<NX>() != 4)
-        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        return launch_ax_ff_variant<NX, ff_epb<NX>()>(nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
     return NEK_ERR_INVALID_ARG;
 }
 
@@ -1026,24 +1088,24 @@ __global__ void k_g_to_ff(int64_t npts, const double* __restrict__ G, float2* __
 
 nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
                             double* w, cudaStream_t s, const int32_t* l2g, const int32_t* eprob,
-                            const uint8_t* pdone, double* edot)
+                            const uint8_t* pdone, double* edot, const DirUpdate* dir)
 {
     switch (nx) {
-        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
-        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot);
+        case 2: return launch_ax_ff_nx<2>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 3: return launch_ax_ff_nx<3>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 4: return launch_ax_ff_nx<4>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 5: return launch_ax_ff_nx<5>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 6: return launch_ax_ff_nx<6>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 7: return launch_ax_ff_nx<7>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 8: return launch_ax_ff_nx<8>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 9: return launch_ax_ff_nx<9>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 10: return launch_ax_ff_nx<10>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 11: return launch_ax_ff_nx<11>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 12: return launch_ax_ff_nx<12>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 13: return launch_ax_ff_nx<13>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
 }
@@ -1080,11 +1142,13 @@ bool ax_ff_epb_fits(int nx, int epb)
 
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                         cudaStream_t s, const int32_t* l2g, const int32_t* eprob, const uint8_t* pdone,
-                        double* edot)
+                        double* edot, const DirUpdate* dir)
 {
     return launch_ax_ff_epb(tuned_epb(edot ? kAxFfEnergy : NEK_AX_FF, nx), nelt, nx, D, Gff, u, w, s, l2g, eprob,
-                            pdone, edot);
+                            pdone, edot, dir);
 }
+
+bool ax_ff_dir_supported(int nx) { return nx == 10; }
 
 }  // namespace nek
 

@@ -165,10 +165,10 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
     // The float-float operator also writes element energies, which replace the
     // solve's <p,w> pass.
     const bool energies = ax_impl == NEK_AX_FF;
-    pcg::ElementEnergies ee{edot, nelt};
+    pcg::ElementEnergies ee{edot, nelt, ax_ff_dir_supported(nx)};  // and the direction update, where compiled
     if (st == NEK_OK) {
-        auto ax = [&](const double* p, double* w, double* ed, cudaStream_t ss) {
-            return ax_impl == NEK_AX_FF ? launch_ax_ff(nelt, nx, D, Gff, p, w, ss, nullptr, nullptr, nullptr, ed)
+        auto ax = [&](const double* p, double* w, double* ed, const DirUpdate* dir, cudaStream_t ss) {
+            return ax_impl == NEK_AX_FF ? launch_ax_ff(nelt, nx, D, Gff, p, w, ss, nullptr, nullptr, nullptr, ed, dir)
                                         : launch_ax_fp64(nelt, nx, D, G, p, w, ss);
         };
         st = pcg::run<double>(gs, n, gs->d_c, mask, mv, f, x, b, tol_rel, max_iter, check_every, time_ax, ax, s,

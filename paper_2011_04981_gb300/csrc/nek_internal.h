@@ -12,6 +12,8 @@ namespace nek {
 constexpr int kMinNx = 2;
 constexpr int kMaxNx = 16;
 
+struct DirUpdate;  // below
+
 // Record a CUDA error in the calling thread's last-error slot and map it to NEK_ERR_CUDA.
 nek_status cuda_fail(cudaError_t e);
 inline nek_status check_cuda(cudaError_t e) { return e == cudaSuccess ? NEK_OK : cuda_fail(e); }
@@ -66,14 +68,17 @@ nek_status launch_ax_fp64_epb(int epb, int64_t nelt, int nx, const double* D, co
 // (with eprob/pdone, skipped elements' entries are left as they were).
 nek_status launch_ax_ff_epb(int epb, int64_t nelt, int nx, const double* D, const float* Gff, const double* u,
                             double* w, cudaStream_t s, const int32_t* l2g = nullptr, const int32_t* eprob = nullptr,
-                            const uint8_t* pdone = nullptr, double* edot = nullptr);
+                            const uint8_t* pdone = nullptr, double* edot = nullptr,
+                            const DirUpdate* dir = nullptr);
 
 // Kernel launchers (arguments already validated).
 nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w,
                           cudaStream_t s);
+// dir (optional, with edot, without l2g / eprob, where ax_ff_dir_supported):
+// the direction update above; u is then ignored (the input is dir->p).
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                         cudaStream_t s, const int32_t* l2g = nullptr, const int32_t* eprob = nullptr,
-                        const uint8_t* pdone = nullptr, double* edot = nullptr);
+                        const uint8_t* pdone = nullptr, double* edot = nullptr, const DirUpdate* dir = nullptr);
 // edot (optional, nelt doubles): per-element energies u_e . w_e in FP64.
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
                           const float* u, float* w, cudaStream_t s, double* edot = nullptr);
@@ -81,6 +86,38 @@ nek_status launch_mask(int64_t n, const uint8_t* mask, double* v, cudaStream_t s
 // Diagonal of the element operators (before summation over shared nodes).
 nek_status launch_diag_local(int64_t nelt, int nx, const double* D, const double* G, double* d, cudaStream_t s);
 nek_status launch_dssum(const nek_gs* gs, double* v, cudaStream_t s);
+
+// Device scalars of the PCG loop (nek_pcg.cuh).
+struct PcgScalars {
+    double rz;      // <r, z>_c of the current iterate
+    double pw;      // <p, w>_c
+    double alpha;
+    double beta;
+    double rr;      // <r, r>_c
+    double bnorm;   // ||b||_c
+    double relres;  // ||r||_c / ||b||_c
+    double tol;
+    int done;       // residual test passed
+    int status;     // NEK_OK or NEK_ERR_BREAKDOWN
+    int iters;      // iterations completed when done/status was set
+    int it;         // iterations executed so far
+    int xpend;      // this iteration's x += alpha p is still to be applied
+};
+
+// The PCG direction update done by the float-float operator as it loads its
+// input (the solve's separate x / direction pass then disappears): on every
+// point of the launch, x += alpha p (old p) while sc->xpend is set, then
+// p = minv r + beta p while the solve goes on (not done, no breakdown), and
+// the operator is applied to the new p, which it also writes back to p.
+struct DirUpdate {
+    double* p;
+    const double* r;
+    const double* minv;
+    double* x;
+    const PcgScalars* sc;
+};
+// True where launch_ax_ff supports dir (the item-mapped kernel, nx = 10).
+bool ax_ff_dir_supported(int nx);
 
 // Deterministic block-partial reductions use this fixed grid for a given length.
 int reduce_blocks(int64_t n);

@@ -307,7 +307,7 @@ nek_status nek_lvec_cg_solve(const nek_lvec* lv, int64_t nelt, int nx, const dou
 
     pcg::Result res;
     // the operator's element energies give <p,w> (p is zero on masked nodes)
-    auto ax = [&](const double* p, double* w, double* ed, cudaStream_t ss) {
+    auto ax = [&](const double* p, double* w, double* ed, const DirUpdate*, cudaStream_t ss) {
         return lvec_ax(lv, nelt, nx, D, Gff, p, w, wE, ss, ed);
     };
     const pcg::ElementEnergies ee{edot, nelt};

@@ -606,7 +606,7 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
     auto ax64 = [&](const double* p, double* w) {
         return Gff ? launch_ax_ff(nelt, nx, D, Gff, p, w, s) : launch_ax_fp64(nelt, nx, D, G, p, w, s);
     };
-    auto ax_lo = [&](const float* p, float* w, double* ed, cudaStream_t ss) {
+    auto ax_lo = [&](const float* p, float* w, double* ed, const DirUpdate*, cudaStream_t ss) {
         return launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed);
     };
 

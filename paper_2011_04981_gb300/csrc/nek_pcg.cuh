@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "nek_internal.h"
@@ -37,21 +38,7 @@
 namespace nek {
 namespace pcg {
 
-struct Scalars {
-    double rz;      // <r, z>_c of the current iterate
-    double pw;      // <p, w>_c
-    double alpha;
-    double beta;
-    double rr;      // <r, r>_c
-    double bnorm;   // ||b||_c
-    double relres;  // ||r||_c / ||b||_c
-    double tol;
-    int done;       // residual test passed
-    int status;     // NEK_OK or NEK_ERR_BREAKDOWN
-    int iters;      // iterations completed when done/status was set
-    int it;         // iterations executed so far
-    int xpend;      // this iteration's x += alpha p is still to be applied (k_p)
-};
+using Scalars = PcgScalars;
 
 constexpr int NT = kReduceThreads;
 
@@ -372,10 +359,13 @@ struct Result {
 
 // The element-energy path (see the top of this file): the operator writes
 // edot[e] = p_e . (A_e p_e) for its nelt elements (k_update applies the mask,
-// from the point flags or the mask array).
+// from the point flags or the mask array).  fused_dir (FP64 vectors only): the
+// operator also applies the x / direction update as it loads p (DirUpdate), so
+// k_p runs once, after the loop, for the last x update.
 struct ElementEnergies {
     double* edot;
     int64_t nelt;
+    bool fused_dir = false;
 };
 
 namespace {
@@ -406,10 +396,11 @@ inline nek_status build_flags(const nek_gs* gs, int64_t n, const uint8_t* mask, 
     return check_launch();
 }
 
-// Runs PCG from x = 0.  `ax(p, w, edot, stream)` applies the element operator,
-// which gs then sums over shared nodes; with gs null, ax applies the assembled
-// operator itself.  edot is ee->edot on the element-energy path (ee non-null),
-// else null.  c null weights every entry by 1.
+// Runs PCG from x = 0.  `ax(p, w, edot, dir, stream)` applies the element
+// operator, which gs then sums over shared nodes; with gs null, ax applies the
+// assembled operator itself.  edot is ee->edot on the element-energy path (ee
+// non-null), else null; dir is the direction update the operator applies
+// first (ee->fused_dir), else null.  c null weights every entry by 1.
 // tol > 0: stop at convergence (NEK_ERR_NOT_CONVERGED after max_iter);
 // tol == 0: exactly max_iter iterations.  Leaves the stream synchronised.
 template <class V, class AxFn>
@@ -420,6 +411,9 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
     const int nb = reduce_blocks(n);
     const int sb = stream_blocks(n);
     int launches = 0;
+    const bool fused = ee && ee->fused_dir && std::is_same<V, double>::value;
+    DirUpdate dir{};
+    if constexpr (std::is_same<V, double>::value) dir = DirUpdate{b.p, b.r, minv, x, b.sc};
     std::vector<cudaEvent_t> ev;
     Scalars h{};
     nek_status st = NEK_OK;
@@ -435,7 +429,7 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
     for (int it = 1; it <= max_iter; it++) {
         const bool timed = time_ax && (size_t)(2 * it) <= ev.size();
         if (timed) cudaEventRecord(ev[2 * (it - 1)], s);
-        if ((st = ax(b.p, b.w, ee ? ee->edot : nullptr, s)) != NEK_OK) goto done;
+        if ((st = ax(b.p, b.w, ee ? ee->edot : nullptr, fused ? &dir : nullptr, s)) != NEK_OK) goto done;
         if (timed) cudaEventRecord(ev[2 * (it - 1) + 1], s);
         if ((st = dssum<V>(gs, b.w, s)) != NEK_OK) goto done;
         if (ee) {
@@ -447,14 +441,22 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
         }
         k_update<V><<<nb, NT, 0, s>>>(n, c, minv, b.w, b.r, b.parts, b.sc, flags, mask);
         k_beta<<<1, NT, 0, s>>>(b.parts, nb, b.sc);
-        k_p<V><<<sb, 256, 0, s>>>(n, minv, b.r, x, b.p, b.sc, it < max_iter ? 1 : 0);
-        launches += 6;  // the operator, dssum, k_alpha, k_update, k_beta, k_p
+        launches += 5;  // the operator, dssum, k_alpha, k_update, k_beta
+        if (!fused) {
+            k_p<V><<<sb, 256, 0, s>>>(n, minv, b.r, x, b.p, b.sc, it < max_iter ? 1 : 0);
+            launches += 1;
+        }
         if ((st = check_launch()) != NEK_OK) goto done;
         if (tol > 0.0 && (it % check_every == 0 || it == max_iter)) {
             if ((st = check_cuda(cudaMemcpyAsync(&h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) != NEK_OK) goto done;
             if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
             if (h.done || h.status != NEK_OK) break;
         }
+    }
+    if (fused) {  // the last iteration's x += alpha p (nothing when it was applied or never due)
+        k_p<V><<<sb, 256, 0, s>>>(n, minv, b.r, x, b.p, b.sc, 0);
+        launches += 1;
+        if ((st = check_launch()) != NEK_OK) goto done;
     }
     if ((st = check_cuda(cudaMemcpyAsync(&h, b.sc, sizeof(h), cudaMemcpyDeviceToHost, s))) != NEK_OK) goto done;
     if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
