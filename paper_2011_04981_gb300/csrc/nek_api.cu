@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "nek_internal.h"
+#include "nek_pcg.cuh"
 #include "nek_reduce.cuh"
 
 namespace nek {
@@ -49,26 +50,7 @@ nek_status launch_mask(int64_t n, const uint8_t* mask, double* v, cudaStream_t s
 // ------------------------------------------------------------------ dssum
 // One thread per group: left-to-right sum over members (ascending local index),
 // then the sum is written back to every member.  Groups are disjoint.
-__global__ void k_dssum(int64_t ngroups, const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
-                        double* __restrict__ v)
-{
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int a = off[g], b = off[g + 1];
-        double s = v[mem[a]];
-        for (int o = a + 1; o < b; o++) s += v[mem[o]];
-        for (int o = a; o < b; o++) v[mem[o]] = s;
-    }
-}
-
-nek_status launch_dssum(const nek_gs* gs, double* v, cudaStream_t s)
-{
-    if (gs->ngroups == 0) return NEK_OK;
-    int64_t nb = (gs->ngroups + 255) / 256;
-    int blocks = static_cast<int>(std::min<int64_t>(nb, 152 * 64));
-    k_dssum<<<blocks, 256, 0, s>>>(gs->ngroups, gs->d_offsets, gs->d_members, v);
-    return check_launch();
-}
+nek_status launch_dssum(const nek_gs* gs, double* v, cudaStream_t s) { return pcg::dssum<double>(gs, v, s); }
 
 // ------------------------------------------------------------------ dot
 __global__ void __launch_bounds__(kReduceThreads) k_dot_c_partials(int64_t n, const double* __restrict__ c,

@@ -109,17 +109,40 @@ inline int stream_blocks(int64_t n)
 namespace {
 
 // One thread per group: left-to-right sum over members (ascending local index),
-// written back to every member; groups are disjoint.
+// written back to every member; groups are disjoint.  A thread takes four
+// groups at a time and issues each level of their loads (offsets, the first
+// two members, their values) together before any store; members beyond the
+// second (edge and corner nodes) follow in order.
 template <class V>
 __global__ void k_dssum_t(int64_t ngroups, const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
                           V* __restrict__ v)
 {
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ngroups;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int a = off[g], b = off[g + 1];
-        V s = v[mem[a]];
-        for (int o = a + 1; o < b; o++) s += v[mem[o]];
-        for (int o = a; o < b; o++) v[mem[o]] = s;
+    constexpr int B = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g0 < ngroups; g0 += B * stride) {
+        int a[B], b[B], m0[B], m1[B];
+        V s[B];
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+            const int64_t g = g0 + k * stride < ngroups ? g0 + k * stride : g0;  // in bounds; unused when past
+            a[k] = off[g];
+            b[k] = off[g + 1];
+        }
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+            m0[k] = mem[a[k]];
+            m1[k] = mem[a[k] + 1];  // every group has at least two members
+        }
+#pragma unroll
+        for (int k = 0; k < B; k++) s[k] = v[m0[k]] + v[m1[k]];
+#pragma unroll
+        for (int k = 0; k < B; k++) {
+            if (g0 + k * stride >= ngroups) break;
+            for (int o = a[k] + 2; o < b[k]; o++) s[k] += v[mem[o]];
+            v[m0[k]] = s[k];
+            v[m1[k]] = s[k];
+            for (int o = a[k] + 2; o < b[k]; o++) v[mem[o]] = s[k];
+        }
     }
 }
 
