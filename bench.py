@@ -570,6 +570,9 @@ def run_native(args):
     flops = perfmodel.ax_flops_per_point(nx) * pts
     hbm, hbm_kind = peaks()
     traffic = traffic_from_profile(nx, mesh.nelt, args.ax)
+    # at nx = 10 the float-float operator of the solve also applies the x / direction update
+    fused_dir = args.ax == "ff" and nx == 10
+    ax_bpp = 104 if fused_dir else 64
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
@@ -586,7 +589,8 @@ def run_native(args):
                 "copies": "pinned host memory, on a second stream overlapping the neighbouring steps' solves"},
         "gpu_launches": launches,
         "ax": {"gdofs": ax_gdofs, "ms_per_launch": ax_t * 1e3, "gflops": flops / ax_t / 1e9,
-               "hbm_gbs": 64 * pts / ax_t / 1e9, "hbm_frac": 64 * pts / ax_t / 1e9 / hbm, "launches": ax_n,
+               "bytes_per_point": ax_bpp, "hbm_gbs": ax_bpp * pts / ax_t / 1e9,
+               "hbm_frac": ax_bpp * pts / ax_t / 1e9 / hbm, "launches": ax_n,
                "share_of_step": ax_ms / 1e3 / t_dev, "elements_per_cta": ax_epb or "default"},
         "roofline": ({"bound": "alu", "achieved": flops / ax_t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                       "frac": flops / ax_t / 1e12 / FP64_PEAK_TFLOPS, "traffic": traffic,
@@ -594,10 +598,14 @@ def run_native(args):
                       "note": "native FP64: DFMA-pipe bound; peak = 152 SM x 2 DFMA/clk x 2 x 2.07 GHz (nominal "
                               "1.25 TFLOP/s); HBM %s peak %.0f GB/s" % (hbm_kind, hbm)}
                      if args.ax == "fp64" else
-                     {"bound": "hbm", "achieved": 64 * pts / ax_t / 1e9, "peak": hbm, "unit": "GB/s",
-                      "frac": 64 * pts / ax_t / 1e9 / hbm, "traffic": traffic, "kernel": ("k_ax_ffi<%d>" if nx == 10 else "k_ax_ffe<%d>" if nx == 12 else "k_ax_ff<%d>") % nx,
-                      "note": "FP64-accurate float-float AX, 64 algorithmic B/point (u 8 + G 48 + w 8); peak = %s "
-                              "HBM copy; its instruction limit is the FP32 pipe (see profiles)" % hbm_kind}),
+                     {"bound": "hbm", "achieved": ax_bpp * pts / ax_t / 1e9, "peak": hbm, "unit": "GB/s",
+                      "frac": ax_bpp * pts / ax_t / 1e9 / hbm, "traffic": traffic,
+                      "kernel": ("k_ax_ffi<%d>" if nx == 10 else "k_ax_ffe<%d>" if nx == 12 else "k_ax_ff<%d>") % nx,
+                      "note": ("FP64-accurate float-float AX with the fused x / direction update, 104 algorithmic "
+                               "B/point (p in and out 16, r 8, minv 8, x in and out 16, G 48, w 8)" if fused_dir else
+                               "FP64-accurate float-float AX, 64 algorithmic B/point (u 8 + G 48 + w 8)") +
+                              "; peak = %s HBM copy; its instruction limit is the FP32 pipe (see profiles)"
+                              % hbm_kind}),
         "clocks": clk,
     }
     if args.sweep and rank == 0:
