@@ -21,7 +21,10 @@
 // pass: <p, mask.dssum(A_L p)>_c = sum over elements of p_e . (A_e p_e),
 // because p holds the same value in every copy of a node and is zero on masked
 // nodes (z = minv r and r vanish there).  The operator writes those energies
-// and k_alpha sums them.
+// and k_alpha sums them.  An operator that can also apply k_p's x / direction
+// update as it loads p (ElementEnergies::fused_dir, DirUpdate) takes over that
+// pass: the loop then runs operator, dssum, k_alpha, k_update, k_beta, and k_p
+// runs once after it for the last x update.
 // Reductions use a fixed grid per length and a fixed shuffle tree, so results
 // are deterministic.  Once the residual test passes, or a breakdown is seen, a
 // device flag makes every later update kernel of the call return at once.
