@@ -139,7 +139,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-AX_SOURCES = {"fp64": ("nek_ax.cu", "ax_fp64_traffic.json"), "ff": ("nek_ax_ff.cu", "ax_ff_traffic.json")}
+AX_SOURCES = {"fp64": ("nek_ax.cu", "ax_fp64_traffic.json"), "ff": ("nek_ax_ff_kernels.cuh", "ax_ff_traffic.json")}
 
 
 def kernel_source_sha(which="fp64"):

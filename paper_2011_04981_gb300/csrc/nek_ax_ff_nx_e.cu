@@ -1,0 +1,28 @@
+// Float-float AX launchers for nx = 14, 15, 16 (kernels in nek_ax_ff_kernels.cuh).
+#include "nek_ax_ff_kernels.cuh"
+
+namespace nek {
+
+nek_status launch_ax_ff_group_e(int nx, int epb, int64_t nelt, const double* D, const float* Gff, const double* u,
+                                  double* w, cudaStream_t s, const int32_t* l2g, const int32_t* eprob,
+                                  const uint8_t* pdone, double* edot, const DirUpdate* dir)
+{
+    switch (nx) {
+        case 14: return launch_ax_ff_nx<14>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 15: return launch_ax_ff_nx<15>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        case 16: return launch_ax_ff_nx<16>(epb, nelt, D, Gff, u, w, s, l2g, eprob, pdone, edot, dir);
+        default: return NEK_ERR_UNSUPPORTED_NX;
+    }
+}
+
+bool ax_ff_fits_group_e(int nx, int epb)
+{
+    switch (nx) {
+        case 14: return ff_fits_rt<14>(epb);
+        case 15: return ff_fits_rt<15>(epb);
+        case 16: return ff_fits_rt<16>(epb);
+        default: return false;
+    }
+}
+
+}  // namespace nek
