@@ -421,6 +421,30 @@ def test_cg_ff_check_every_and_workspace_reuse():
     assert torch.equal(x1, x2)
 
 
+def test_cg_ff_fused_update_breakdown_and_no_work():
+    """nx = 10 (the operator applies the x / direction update): a NaN in f breaks down on the first
+    iteration and leaves x finite where it was written; b = 0 returns x = 0 at once; a solve that runs
+    past convergence with check_every > 1 leaves x exactly as the solve that stops at once."""
+    mesh = inputs.box_mesh(2, 2, 3, 10, perturb=0.1, seed=8)
+    P = DeviceProblem(mesh, DEV)
+    f = _t(inputs.random_global_field(mesh, seed=3))
+    x = torch.empty_like(f)
+    fn = f.clone()
+    fn[0, 5 + 10 * 5 + 100 * 5] = float("nan")  # an interior node of element 0
+    r = P.cg(fn, x, tol=1e-8, max_iter=50, ax_impl=nekax.AX_FF)
+    assert r["status"] == nekax.ERR_BREAKDOWN and r["iters"] == 1
+    r = P.cg(torch.zeros_like(f), x, tol=1e-8, max_iter=50, ax_impl=nekax.AX_FF)
+    assert r["status"] == nekax.OK and r["iters"] == 0 and torch.count_nonzero(x) == 0
+    x1 = torch.empty_like(f)
+    x2 = torch.empty_like(f)
+    r1 = P.cg(f, x1, tol=1e-6, max_iter=500, check_every=1, ax_impl=nekax.AX_FF)
+    r2 = P.cg(f, x2, tol=1e-6, max_iter=500, check_every=50, ax_impl=nekax.AX_FF)  # overshoots by up to 49
+    assert r1["status"] == r2["status"] == nekax.OK and r1["iters"] == r2["iters"]
+    assert torch.equal(x1, x2)
+    Pr = ref.Problem(mesh)
+    assert Pr.residual(f.cpu().numpy(), x1.cpu().numpy()) <= 1e-6 * (1 + 1e-3)
+
+
 # ------------------------------------------------------------------ elements-per-CTA variants
 @pytest.mark.parametrize("impl", [nekax.AX_FP64, nekax.AX_FF])
 @pytest.mark.parametrize("nx", [5, 8, 10])
