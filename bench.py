@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -181,7 +182,25 @@ def cpu_baseline(nx, iters_budget_s=15.0):
     return {"value": mesh.npts * iters / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d Jacobi-PCG iterations on a %dx%dx%d-element deformed box, nx=%d (%d points), "
                       "single-threaded C oracle, %.1f s" % (iters, e, e, e, nx, mesh.npts, dt),
-            "seconds": dt}
+            "seconds": dt, "host": host_cpu()}
+
+
+def host_cpu():
+    """Logical CPUs and the CPU model of this host (the oracle uses one of them)."""
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            info = fh.read().splitlines()
+        names = [ln.split(":", 1)[1].strip() for ln in info if ln.lower().startswith("model name")]
+        parts = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU part")]
+        impl = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU implementer")]
+        if names:
+            model = names[0]
+        elif parts:
+            model = "%s implementer %s part %s" % (platform.machine(), impl[0] if impl else "?", parts[0])
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model}
 
 
 def max_over_ranks(dist, values, device):
