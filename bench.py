@@ -590,8 +590,8 @@ def run_native(args):
     flops = perfmodel.ax_flops_per_point(nx) * pts
     hbm, hbm_kind = peaks()
     traffic = traffic_from_profile(nx, mesh.nelt, args.ax)
-    # at nx = 10 the float-float operator of the solve also applies the x / direction update
-    fused_dir = args.ax == "ff" and nx == 10
+    # the float-float operator of the solve also applies the x / direction update
+    fused_dir = args.ax == "ff"
     ax_bpp = 104 if fused_dir else 64
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -54,7 +54,7 @@ nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff,
                             pdone, edot, dir);
 }
 
-bool ax_ff_dir_supported(int nx) { return nx == 10; }
+bool ax_ff_dir_supported(int nx) { return nx >= kMinNx && nx <= kMaxNx; }
 
 }  // namespace nek
 

@@ -247,9 +247,9 @@ constexpr int ff_min_blocks()
 // element, pdone: one byte per problem) returns at once (batched solves); DOT:
 // plain, and each element's energy u_e . (A_e u_e) is written to edot[e] (the
 // CG's <p, Ap> is their sum, see the solve); SKIP_DOT, GATHER_DOT: energies
-// with the skip (batched solves) or the gather (unique-node solves); DIR_DOT
-// (item-mapped kernel): energies, the input being the solve's direction after
-// the update that the kernel applies as it loads it (DirUpdate).
+// with the skip (batched solves) or the gather (unique-node solves); DIR_DOT:
+// energies, the input being the solve's direction after the update that the
+// kernel applies as it loads it (DirUpdate).
 constexpr int kModePlain = 0, kModeGather = 1, kModeSkip = 2, kModeDot = 3, kModeSkipDot = 4, kModeGatherDot = 5,
               kModeDirDot = 6;
 constexpr bool mode_skips(int m) { return m == kModeSkip || m == kModeSkipDot; }
@@ -273,11 +273,72 @@ __device__ __forceinline__ bool cta_skipped(const int32_t* __restrict__ eprob, c
     }
 }
 
+// Reads the launch's input points q in [0, count) of the CTA (local index q of
+// element block e0) and hands each value to stage(q, value): u[q] directly,
+// through l2g in the gather modes, and in DIR_DOT the solve's direction after
+// the update (x += alpha p, p = minv r + beta p, both written back), four
+// points per thread at a time with all loads issued before the stores (one
+// point at a time, each load would wait for the previous point's stores).
+template <int MODE, int NT, class Stage>
+__device__ __forceinline__ void load_input(int tid, int count, int64_t first, const double* __restrict__ u,
+                                           const int32_t* __restrict__ l2g, const DirUpdate& dir, Stage&& stage)
+{
+    if constexpr (MODE == kModeDirDot) {
+        const bool dx = dir.sc->xpend != 0, dp = !(dir.sc->done || dir.sc->status != NEK_OK);
+        const double da = dir.sc->alpha, db = dir.sc->beta;
+        constexpr int B = 4;
+        for (int q0 = tid; q0 < count; q0 += B * NT) {
+            double pv[B], xv[B], mv[B], rv[B];
+#pragma unroll
+            for (int m = 0; m < B; m++) {
+                const int q = q0 + m * NT;
+                const int64_t g = first + (q < count ? q : 0);
+                pv[m] = dir.p[g];
+                xv[m] = dx ? dir.x[g] : 0.0;
+                mv[m] = dir.minv[g];
+                rv[m] = dir.r[g];
+            }
+#pragma unroll
+            for (int m = 0; m < B; m++) {
+                const int q = q0 + m * NT;
+                if (q >= count) break;
+                const int64_t g = first + q;
+                double val = pv[m];
+                if (dx) dir.x[g] = fma(da, val, xv[m]);
+                if (dp) {
+                    val = fma(db, val, mv[m] * rv[m]);
+                    dir.p[g] = val;
+                }
+                stage(q, val);
+            }
+        }
+    } else {
+        for (int q = tid; q < count; q += NT)
+            stage(q, mode_gathers(MODE) ? __ldg(u + __ldg(l2g + first + q)) : __ldg(u + first + q));
+    }
+}
+
+// The input value at local point p of an element whose first point is `first`,
+// read again for the energy: DIR_DOT reads the direction this kernel wrote
+// (plain loads), the gather modes go through l2g.
+template <int MODE>
+__device__ __forceinline__ double reread_input(int64_t first, int p, const double* __restrict__ u,
+                                               const int32_t* __restrict__ l2g, const DirUpdate& dir)
+{
+    if constexpr (MODE == kModeDirDot)
+        return dir.p[first + p];
+    else if constexpr (mode_gathers(MODE))
+        return __ldg(u + __ldg(l2g + first + p));
+    else
+        return __ldg(u + first + p);
+}
+
 template <int NX, int EPB, int MODE>
 __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ff(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
             const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g,
-            const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot)
+            const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot,
+            DirUpdate dir)
 {
     using T = typename std::conditional<(NX % 2 == 0), float2, float>::type;
     using L = Lanes<T>;
@@ -307,13 +368,7 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
         sDT[(q % NX) * NX + q / NX] = d;
     }
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
-    if constexpr (mode_gathers(MODE)) {
-        const int32_t* idx = l2g + e0 * N3;
-        for (int q = tid; q < ne * N3; q += NT) sU[q] = split_double(__ldg(u + __ldg(idx + q)));
-    } else {
-        const double* src = u + e0 * N3;
-        for (int q = tid; q < ne * N3; q += NT) sU[q] = split_double(__ldg(src + q));
-    }
+    load_input<MODE, NT>(tid, ne * N3, e0 * N3, u, l2g, dir, [&](int q, double v) { sU[q] = split_double(v); });
     __syncthreads();
     for (int q = tid; q < NX; q += NT) {
         float r = 0.f, c = 0.f;
@@ -423,8 +478,6 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
         const float2* wre = sWr + el * N3;
         const float2* wse = sWs + el * N3;
         const float2* wte = sWt + el * N3;
-        const double* ug = u + (e0 + el) * (int64_t)N3;
-        const int32_t* ig = l2g + (e0 + el) * (int64_t)N3;  // gather modes: u(p) = u[ig[p]]
         const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
                     mwt = sMax[4 * el + 3] * 1.0001f;
         const float bij = sCol[i] * mwr + sCol[j] * mws;
@@ -464,7 +517,7 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
                 const double wv = join_pair(L::get(hi, q), L::get(lo, q));
                 we[p] = wv;
                 if constexpr (mode_energies(MODE))
-                    energy = fma(mode_gathers(MODE) ? __ldg(u + __ldg(ig + p)) : __ldg(ug + p), wv, energy);
+                    energy = fma(reread_input<MODE>((e0 + el) * (int64_t)N3, p, u, l2g, dir), wv, energy);
             }
         }
     }
@@ -492,7 +545,8 @@ template <int NX, int EPB, int MODE>
 __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     k_ax_ffe(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
              const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g,
-             const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot)
+             const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot,
+             DirUpdate dir)
 {
     static_assert(NX % 2 == 0 && NX <= 12, "even nx up to 12");
     using T = float2;
@@ -526,18 +580,14 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
         dt[2 + (b & 1)] = d.y;
     }
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
-    {
-        const double* src = u + e0 * N3;
-        const int32_t* idx = l2g + e0 * N3;  // used in the gather mode only
-        for (int q = tid; q < ne * N3; q += NT) {
-            const int el = q / N3, p = q - el * N3;
-            const int k = p / N2, ji = p - k * N2;
-            const float2 v = split_double(mode_gathers(MODE) ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
-            float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
-            dst[k & 1] = v.x;
-            dst[2 + (k & 1)] = v.y;
-        }
-    }
+    load_input<MODE, NT>(tid, ne * N3, e0 * N3, u, l2g, dir, [&](int q, double val) {
+        const int el = q / N3, p = q - el * N3;
+        const int k = p / N2, ji = p - k * N2;
+        const float2 v = split_double(val);
+        float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
+        dst[k & 1] = v.x;
+        dst[2 + (k & 1)] = v.y;
+    });
     __syncthreads();
     for (int q = tid; q < NX; q += NT) {
         float r = 0.f, c = 0.f;
@@ -642,8 +692,7 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
     if (active) {
         const float4* wre = WR4 + el * PB;
         const float4* wse = WS4 + el * PB;
-        const double* ug = u + (e0 + el) * (int64_t)N3 + i + NX * j;  // u(i, j, k) at ug[k * N2]
-        const int32_t* ig = l2g + (e0 + el) * (int64_t)N3 + i + NX * j;  // gather modes: at u[ig[k * N2]]
+        const int64_t ef = (e0 + el) * (int64_t)N3;  // the element's first point
         const float2* wte = WT2 + el * N3 + i + NX * j;  // wt(i, j, l) at wte[l * N2]
         const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
                     mwt = sMax[4 * el + 3] * 1.0001f;
@@ -654,13 +703,8 @@ __global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
             const int k0 = 2 * kp;
             double u0 = 0.0, u1 = 0.0;
             if constexpr (mode_energies(MODE)) {  // issued here, used after the contraction
-                if constexpr (mode_gathers(MODE)) {
-                    u0 = __ldg(u + __ldg(ig + k0 * N2));
-                    u1 = __ldg(u + __ldg(ig + (k0 + 1) * N2));
-                } else {
-                    u0 = __ldg(ug + k0 * N2);
-                    u1 = __ldg(ug + (k0 + 1) * N2);
-                }
+                u0 = reread_input<MODE>(ef, i + NX * (j + NX * k0), u, l2g, dir);
+                u1 = reread_input<MODE>(ef, i + NX * (j + NX * (k0 + 1)), u, l2g, dir);
             }
             OffsetAcc<T> acc;
             acc.init(make_float2(offset_for(bij + sCol[k0] * mwt), offset_for(bij + sCol[k0 + 1] * mwt)));
@@ -755,59 +799,14 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
         dt[2 + (b & 1)] = d.y;
     }
     for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
-    {
-        const double* src = u + e0 * N3;
-        const int32_t* idx = l2g + e0 * N3;  // used in the gather modes only
-        bool dir_x = false, dir_p = false;   // DIR_DOT: which updates apply
-        double dir_a = 0.0, dir_b = 0.0;
-        if constexpr (MODE == kModeDirDot) {
-            dir_x = dir.sc->xpend != 0;
-            dir_p = !(dir.sc->done || dir.sc->status != NEK_OK);
-            dir_a = dir.sc->alpha;
-            dir_b = dir.sc->beta;
-        }
-        auto stage = [&](int q, double val) {  // split u(q) into the k-pair layout
-            const int el = q / N3, p = q - el * N3;
-            const int k = p / N2, ji = p - k * N2;
-            const float2 v = split_double(val);
-            float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
-            dst[k & 1] = v.x;
-            dst[2 + (k & 1)] = v.y;
-        };
-        if constexpr (MODE == kModeDirDot) {
-            // the solve's x / direction update, with the operations of its separate pass; four
-            // points per thread at a time, all loads issued before the stores
-            constexpr int B = 4;
-            for (int q0 = tid; q0 < ne * N3; q0 += B * NT) {
-                double pv[B], xv[B], mv[B], rv[B];
-#pragma unroll
-                for (int m = 0; m < B; m++) {
-                    const int q = q0 + m * NT;
-                    const int64_t g = e0 * N3 + (q < ne * N3 ? q : 0);
-                    pv[m] = dir.p[g];
-                    xv[m] = dir_x ? dir.x[g] : 0.0;
-                    mv[m] = dir.minv[g];
-                    rv[m] = dir.r[g];
-                }
-#pragma unroll
-                for (int m = 0; m < B; m++) {
-                    const int q = q0 + m * NT;
-                    if (q >= ne * N3) break;
-                    const int64_t g = e0 * N3 + q;
-                    double val = pv[m];
-                    if (dir_x) dir.x[g] = fma(dir_a, val, xv[m]);
-                    if (dir_p) {
-                        val = fma(dir_b, val, mv[m] * rv[m]);
-                        dir.p[g] = val;
-                    }
-                    stage(q, val);
-                }
-            }
-        } else {
-            for (int q = tid; q < ne * N3; q += NT)
-                stage(q, mode_gathers(MODE) ? __ldg(u + __ldg(idx + q)) : __ldg(src + q));
-        }
-    }
+    load_input<MODE, NT>(tid, ne * N3, e0 * N3, u, l2g, dir, [&](int q, double val) {
+        const int el = q / N3, p = q - el * N3;
+        const int k = p / N2, ji = p - k * N2;
+        const float2 v = split_double(val);
+        float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
+        dst[k & 1] = v.x;
+        dst[2 + (k & 1)] = v.y;
+    });
     __syncthreads();
     for (int q = tid; q < NX; q += NT) {
         float r = 0.f, c = 0.f;
@@ -911,8 +910,7 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
         const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
                     mwt = sMax[4 * el + 3] * 1.0001f;
         double* we = w + (e0 + el) * (int64_t)N3;
-        const double* ug = u + (e0 + el) * (int64_t)N3;
-        const int32_t* ig = l2g + (e0 + el) * (int64_t)N3;  // gather modes: u(p) = u[ig[p]]
+        const int64_t ef = (e0 + el) * (int64_t)N3;  // the element's first point
 #pragma unroll 1
         for (int q = t; q < NITEM; q += TPE) {
             const int kp = q / N2, c = q - kp * N2;
@@ -920,17 +918,8 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
             const int p0 = c + N2 * k0;
             double u0 = 0.0, u1 = 0.0;
             if constexpr (mode_energies(MODE)) {  // issued here, used after the contraction
-                if constexpr (MODE == kModeDirDot) {  // written by this CTA: plain loads
-                    const double* pe = dir.p + (e0 + el) * (int64_t)N3;
-                    u0 = pe[p0];
-                    u1 = pe[p0 + N2];
-                } else if constexpr (mode_gathers(MODE)) {
-                    u0 = __ldg(u + __ldg(ig + p0));
-                    u1 = __ldg(u + __ldg(ig + p0 + N2));
-                } else {
-                    u0 = __ldg(ug + p0);
-                    u1 = __ldg(ug + p0 + N2);
-                }
+                u0 = reread_input<MODE>(ef, p0, u, l2g, dir);
+                u1 = reread_input<MODE>(ef, p0 + N2, u, l2g, dir);
             }
             const float bij = sCol[i] * mwr + sCol[j] * mws;
             OffsetAcc<T> acc;
@@ -1009,13 +998,14 @@ nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, 
             nek_status st = ensure_dyn_smem(k_ax_ffe<NX, EPB, MODE>, smem, configured);
             if (st != NEK_OK) return st;
             k_ax_ffe<NX, EPB, MODE><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
-                nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot);
+                nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot,
+                dir ? *dir : DirUpdate{});
         }
     } else {
         nek_status st = ensure_dyn_smem(k_ax_ff<NX, EPB, MODE>, smem, configured);
         if (st != NEK_OK) return st;
         k_ax_ff<NX, EPB, MODE><<<(unsigned)blocks, ff_threads_per_elem(NX) * EPB, smem, s>>>(
-            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot);
+            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot, dir ? *dir : DirUpdate{});
     }
     return check_launch();
 }
@@ -1026,13 +1016,9 @@ nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff,
                                 double* edot, const DirUpdate* dir)
 {
     if (dir) {
-        if constexpr (ff_item_layout<NX>()) {
-            if (!edot || l2g || eprob) return NEK_ERR_INVALID_ARG;
-            return launch_ax_ff_kernel<NX, EPB, kModeDirDot>(nelt, D, Gff, dir->p, w, s, nullptr, nullptr, nullptr,
-                                                             edot, dir);
-        } else {
-            return NEK_ERR_INVALID_ARG;
-        }
+        if (!edot || l2g || eprob) return NEK_ERR_INVALID_ARG;
+        return launch_ax_ff_kernel<NX, EPB, kModeDirDot>(nelt, D, Gff, dir->p, w, s, nullptr, nullptr, nullptr,
+                                                         edot, dir);
     }
     if (l2g && edot)
         return launch_ax_ff_kernel<NX, EPB, kModeGatherDot>(nelt, D, Gff, u, w, s, l2g, nullptr, nullptr, edot);

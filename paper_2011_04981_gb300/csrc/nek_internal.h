@@ -116,7 +116,7 @@ struct DirUpdate {
     double* x;
     const PcgScalars* sc;
 };
-// True where launch_ax_ff supports dir (the item-mapped kernel, nx = 10).
+// True where launch_ax_ff supports dir (every nx of the float-float kernels).
 bool ax_ff_dir_supported(int nx);
 
 // Deterministic block-partial reductions use this fixed grid for a given length.

@@ -395,11 +395,9 @@ def test_cg_ff_fixed_iterations(nx):
     for its in (1, 2, 23):
         res = P.cg(_t(f), x, tol=0.0, max_iter=its, ax_impl=nekax.AX_FF, time_ax=True)
         assert res["status"] == nekax.OK and res["iters"] == its and res["ax_launches"] == its
-        # point flags (2), init (2), then per iteration AX (with element energies; at nx = 10 also the
-        # x / direction update), dssum, alpha, r update, beta and, at other nx, the x / direction update;
-        # at nx = 10 one x update after the loop
-        per_it = 5 if nx == 10 else 6
-        assert res["kernel_launches"] == 2 + 2 + per_it * its + (1 if nx == 10 else 0)
+        # point flags (2), init (2), then per iteration AX (with element energies and the x / direction
+        # update), dssum, alpha, r update, beta; one x update after the loop
+        assert res["kernel_launches"] == 2 + 2 + 5 * its + 1
         st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 0.0, its)
         assert _rel(x.cpu().numpy(), xr) <= 1e-9, its
         assert abs(res["relres"] - rr) <= 1e-8 * rr
