@@ -29,7 +29,8 @@ namespace nek {
 
 namespace {
 
-constexpr int kChunk = 4096;  // points per reduction chunk
+constexpr int kChunk = 4096;   // points per reduction chunk
+constexpr int kGChunk = 2048;  // gather-scatter groups per dssum chunk
 constexpr int BT = 256;       // threads per chunk block
 
 struct BScal {
@@ -254,6 +255,17 @@ __global__ void kb_test(int nprob, double tol, BScal* __restrict__ sc, int* __re
 
 // x += alpha p (old p) while the problem's x update is pending; p = minv r +
 // beta p while it goes on
+// dssum over the groups of the problems still going: block b sums the groups
+// of chunk b unless its problem has finished (its vectors are frozen then).
+__global__ void __launch_bounds__(BT) kb_dssum(const int64_t* __restrict__ gch_begin,
+                                               const int32_t* __restrict__ gch_prob, const uint8_t* __restrict__ pdone,
+                                               const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
+                                               double* __restrict__ v)
+{
+    if (pdone[gch_prob[blockIdx.x]]) return;
+    pcg::dssum_groups<double>(gch_begin[blockIdx.x], gch_begin[blockIdx.x + 1], threadIdx.x, BT, off, mem, v);
+}
+
 __global__ void __launch_bounds__(BT) kb_p(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
                                            const double* __restrict__ minv, const double* __restrict__ r,
                                            double* __restrict__ x, double* __restrict__ p,
@@ -320,6 +332,9 @@ struct nek_batch {
     int* d_pch;           // nprob+1: chunk range of each problem
     int32_t* d_elem_prob; // nelt_total: problem of each element
     int64_t* d_pel;       // nprob+1: element range of each problem
+    int ngchunks;         // chunks of the gather-scatter groups, each within one problem
+    int64_t* d_gch_begin; // ngchunks+1: first group of each chunk
+    int32_t* d_gch_prob;  // ngchunks: problem of each chunk
 };
 
 using namespace nek;
@@ -391,6 +406,9 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
     b->d_pch = nullptr;
     b->d_elem_prob = nullptr;
     b->d_pel = nullptr;
+    b->ngchunks = 0;
+    b->d_gch_begin = nullptr;
+    b->d_gch_prob = nullptr;
     nek_status st = NEK_OK;
     try {
         // global ids of all problems in one space: problem q's ids are offset by
@@ -401,6 +419,10 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
         std::vector<int> pch(1, 0);
         std::vector<int32_t> elem_prob(static_cast<size_t>(nel));
         std::vector<int64_t> pel(1, 0);
+        std::vector<int64_t> gch_begin;  // group chunks: groups of problem q follow those of q - 1
+        std::vector<int32_t> gch_prob;
+        std::vector<int32_t> mult;       // multiplicity of each global id of one problem
+        int64_t gtot = 0;
         b->prob_pt0.assign(1, 0);
         int64_t pt = 0, goff = 0, el = 0;
         for (int q = 0; q < nprob; q++) {
@@ -412,6 +434,17 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
                 glo[pt + k] = g + goff;
                 gmax = std::max(gmax, g);
             }
+            // the plan orders groups by global id, and problem q's ids follow q - 1's: its groups are the
+            // next (number of its ids with two or more copies)
+            mult.assign(static_cast<size_t>(gmax + 1), 0);
+            for (int64_t k = 0; k < n; k++) mult[glo_num_host[pt + k]]++;
+            int64_t ngq = 0;
+            for (int32_t c : mult) ngq += c >= 2;
+            for (int64_t a = gtot; a < gtot + ngq; a += kGChunk) {
+                gch_begin.push_back(a);
+                gch_prob.push_back(q);
+            }
+            gtot += ngq;
             for (int64_t a = pt; a < pt + n; a += kChunk) {
                 ch_begin.push_back(a);
                 ch_prob.push_back(q);
@@ -429,6 +462,20 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
         ch_begin.push_back(npts);
         b->nchunks = static_cast<int>(ch_prob.size());
         if ((st = gs_create_flat(npts, glo.data(), &b->gs)) != NEK_OK) throw 3;
+        if (b->gs->ngroups != gtot) throw 3;  // the plan's grouping must be the one counted above
+        gch_begin.push_back(gtot);
+        b->ngchunks = static_cast<int>(gch_prob.size());
+        if ((st = check_cuda(cudaMalloc(&b->d_gch_begin, sizeof(int64_t) * gch_begin.size()))) != NEK_OK) throw 3;
+        if ((st = check_cuda(cudaMalloc(&b->d_gch_prob, sizeof(int32_t) * std::max<size_t>(gch_prob.size(), 1)))) !=
+            NEK_OK)
+            throw 3;
+        if ((st = check_cuda(cudaMemcpy(b->d_gch_begin, gch_begin.data(), sizeof(int64_t) * gch_begin.size(),
+                                        cudaMemcpyHostToDevice))) != NEK_OK)
+            throw 3;
+        if (!gch_prob.empty() &&
+            (st = check_cuda(cudaMemcpy(b->d_gch_prob, gch_prob.data(), sizeof(int32_t) * gch_prob.size(),
+                                        cudaMemcpyHostToDevice))) != NEK_OK)
+            throw 3;
         if ((st = check_cuda(cudaMalloc(&b->d_ch_begin, sizeof(int64_t) * ch_begin.size()))) != NEK_OK) throw 3;
         if ((st = check_cuda(cudaMalloc(&b->d_ch_prob, sizeof(int32_t) * ch_prob.size()))) != NEK_OK) throw 3;
         if ((st = check_cuda(cudaMalloc(&b->d_pch, sizeof(int) * pch.size()))) != NEK_OK) throw 3;
@@ -475,6 +522,8 @@ nek_status nek_batch_destroy(nek_batch* b)
     cudaFree(b->d_pch);
     cudaFree(b->d_elem_prob);
     cudaFree(b->d_pel);
+    cudaFree(b->d_gch_begin);
+    cudaFree(b->d_gch_prob);
     for (auto& g : b->groups) cudaFree(g.D);
     delete b;
     return NEK_OK;
@@ -549,8 +598,9 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
                                 : launch_ax_fp64(g.nelt, g.nx, g.D, G + g.pt0 * 6, pg, wg, ss);
             if (sa != NEK_OK) return sa;
         }
-        nek_status sd = pcg::dssum<double>(b->gs, L.w, ss);
-        if (sd != NEK_OK) return sd;
+        if (b->ngchunks > 0)
+            kb_dssum<<<b->ngchunks, BT, 0, ss>>>(b->d_gch_begin, b->d_gch_prob, L.pdone, b->gs->d_offsets,
+                                                 b->gs->d_members, L.w);
         // the float-float operator writes element energies, which give <p,w> (no kb_pw pass)
         if (!Gff) kb_pw<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, L.p, L.w, L.parts, L.sc);
         kb_alpha<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, L.sc, L.active, b->d_pel, Gff ? L.edot : nullptr);

@@ -111,23 +111,24 @@ inline int stream_blocks(int64_t n)
 
 namespace {
 
-// One thread per group: left-to-right sum over members (ascending local index),
-// written back to every member; groups are disjoint.  A thread takes four
-// groups at a time and issues each level of their loads (offsets, the first
-// two members, their values) together before any store; members beyond the
-// second (edge and corner nodes) follow in order.
+// Groups [g_begin, g_end) of a plan summed by the threads tid, tid + stride,
+// ...: one thread per group, a left-to-right sum over members (ascending local
+// index) written back to every member; groups are disjoint.  A thread takes
+// four groups at a time and issues each level of their loads (offsets, the
+// first two members, their values) together before any store; members beyond
+// the second (edge and corner nodes) follow in order.
 template <class V>
-__global__ void k_dssum_t(int64_t ngroups, const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
-                          V* __restrict__ v)
+__device__ __forceinline__ void dssum_groups(int64_t g_begin, int64_t g_end, int64_t tid, int64_t stride,
+                                             const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
+                                             V* __restrict__ v)
 {
     constexpr int B = 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g0 < ngroups; g0 += B * stride) {
+    for (int64_t g0 = g_begin + tid; g0 < g_end; g0 += B * stride) {
         int a[B], b[B], m0[B], m1[B];
         V s[B];
 #pragma unroll
         for (int k = 0; k < B; k++) {
-            const int64_t g = g0 + k * stride < ngroups ? g0 + k * stride : g0;  // in bounds; unused when past
+            const int64_t g = g0 + k * stride < g_end ? g0 + k * stride : g0;  // in bounds; unused when past
             a[k] = off[g];
             b[k] = off[g + 1];
         }
@@ -140,13 +141,21 @@ __global__ void k_dssum_t(int64_t ngroups, const int32_t* __restrict__ off, cons
         for (int k = 0; k < B; k++) s[k] = v[m0[k]] + v[m1[k]];
 #pragma unroll
         for (int k = 0; k < B; k++) {
-            if (g0 + k * stride >= ngroups) break;
+            if (g0 + k * stride >= g_end) break;
             for (int o = a[k] + 2; o < b[k]; o++) s[k] += v[mem[o]];
             v[m0[k]] = s[k];
             v[m1[k]] = s[k];
             for (int o = a[k] + 2; o < b[k]; o++) v[mem[o]] = s[k];
         }
     }
+}
+
+template <class V>
+__global__ void k_dssum_t(int64_t ngroups, const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
+                          V* __restrict__ v)
+{
+    dssum_groups<V>(0, ngroups, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, off,
+                    mem, v);
 }
 
 template <class V>
