@@ -443,6 +443,34 @@ def test_cg_ff_fused_update_breakdown_and_no_work():
     assert Pr.residual(f.cpu().numpy(), x1.cpu().numpy()) <= 1e-6 * (1 + 1e-3)
 
 
+@pytest.mark.parametrize("nx", [7, 8, 10, 12])
+def test_cg_ff_solve_bit_identical_across_elements_per_cta(nx):
+    """The solve's operator form (element energies, fused x / direction update) at every element count
+    per CTA that fits: the iterate after 15 iterations is bit-identical (energies are summed in an order
+    fixed by nx, the update is pointwise) and matches the oracle's PCG."""
+    mesh = inputs.box_mesh(3, 2, 2, nx, perturb=0.1, seed=20 + nx)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=7)
+    st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 0.0, 15)
+    lib = nekax.load()
+    outs = []
+    try:
+        for epb in (1, 2, 4):
+            if lib.nek_set_ax_epb(int(nekax.AX_FF_ENERGY), nx, epb) != nekax.OK:
+                continue
+            x = torch.full((mesh.nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+            res = P.cg(_t(f), x, tol=0.0, max_iter=15, ax_impl=nekax.AX_FF)
+            assert res["status"] == nekax.OK and res["iters"] == 15
+            outs.append(x.cpu().numpy())
+    finally:
+        lib.nek_set_ax_epb(int(nekax.AX_FF_ENERGY), nx, 0)
+    assert len(outs) >= 2
+    for xo in outs[1:]:
+        assert np.array_equal(xo, outs[0])
+    assert _rel(outs[0], xr) <= 1e-9
+
+
 # ------------------------------------------------------------------ elements-per-CTA variants
 @pytest.mark.parametrize("impl", [nekax.AX_FP64, nekax.AX_FF])
 @pytest.mark.parametrize("nx", [5, 8, 10])
