@@ -296,7 +296,9 @@ nek_status nek_dot_c_noalloc(int64_t n, const double* c, const double* a, const 
  * problem's own global ids (each starting anywhere >= 0; they are made disjoint
  * internally).  All points together must be < 2^31.  The handle owns the
  * gather-scatter plan over all problems, the reduction chunk table and one D per
- * distinct nx.  Synchronous.
+ * distinct nx.  Synchronous.  Within an nx, ordering the problems by size
+ * (smallest first) lets the solve stop launching the operator over the
+ * problems that have finished (the small ones usually finish first).
  */
 typedef struct nek_batch nek_batch;
 

@@ -326,6 +326,8 @@ struct nek_batch {
     nek_gs* gs;
     std::vector<nek::Group> groups;
     std::vector<int64_t> prob_pt0;  // first point of each problem, nprob+1
+    std::vector<int64_t> prob_el0;  // first element of each problem, nprob+1
+    std::vector<int> prob_group;    // group (nx run) of each problem
     int nchunks;
     int64_t* d_ch_begin;  // nchunks+1
     int32_t* d_ch_prob;   // nchunks
@@ -424,6 +426,7 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
         std::vector<int32_t> mult;       // multiplicity of each global id of one problem
         int64_t gtot = 0;
         b->prob_pt0.assign(1, 0);
+        b->prob_el0.assign(1, 0);
         int64_t pt = 0, goff = 0, el = 0;
         for (int q = 0; q < nprob; q++) {
             const int64_t n = nelt[q] * (int64_t)nx[q] * nx[q] * nx[q];
@@ -453,11 +456,13 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
             for (int64_t k = 0; k < nelt[q]; k++) elem_prob[el + k] = q;
             pel.push_back(el + nelt[q]);
             if (b->groups.empty() || b->groups.back().nx != nx[q]) b->groups.push_back(Group{nx[q], el, 0, pt, nullptr});
+            b->prob_group.push_back(static_cast<int>(b->groups.size()) - 1);
             b->groups.back().nelt += nelt[q];
             goff += gmax + 1;
             pt += n;
             el += nelt[q];
             b->prob_pt0.push_back(pt);
+            b->prob_el0.push_back(el);
         }
         ch_begin.push_back(npts);
         b->nchunks = static_cast<int>(ch_prob.size());
@@ -589,14 +594,25 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
     int active = 0;
     const int per_graph = iters_per_graph > 0 ? iters_per_graph : 0;
 
+    // Per group, the elements before ax_first[g] belong to finished problems only,
+    // and the operator is launched from there on.  With the problems of a group
+    // ordered by size (the larger need more iterations), the launches shrink as
+    // the small ones finish; ax_first is advanced at graph boundaries.
+    std::vector<int64_t> ax_first(b->groups.size(), 0);
+    int iter_launches = 0;  // launches enqueued by the last one_iteration
     auto one_iteration = [&](cudaStream_t ss) -> nek_status {
-        for (const auto& g : b->groups) {
-            const double* pg = L.p + g.pt0;
-            double* wg = L.w + g.pt0;
-            nek_status sa = Gff ? launch_ax_ff(g.nelt, g.nx, g.D, Gff + g.pt0 * 12, pg, wg, ss, nullptr,
-                                               b->d_elem_prob + g.elem0, L.pdone, L.edot + g.elem0)
-                                : launch_ax_fp64(g.nelt, g.nx, g.D, G + g.pt0 * 6, pg, wg, ss);
+        iter_launches = 0;
+        for (size_t gi = 0; gi < b->groups.size(); gi++) {
+            // the group's elements from the first one of a problem still going (see ax_first)
+            const auto& g = b->groups[gi];
+            const int64_t f0 = ax_first[gi];
+            if (f0 >= g.nelt) continue;
+            const int64_t pt = g.pt0 + f0 * (int64_t)g.nx * g.nx * g.nx;
+            nek_status sa = Gff ? launch_ax_ff(g.nelt - f0, g.nx, g.D, Gff + pt * 12, L.p + pt, L.w + pt, ss, nullptr,
+                                               b->d_elem_prob + g.elem0 + f0, L.pdone, L.edot + g.elem0 + f0)
+                                : launch_ax_fp64(g.nelt - f0, g.nx, g.D, G + pt * 6, L.p + pt, L.w + pt, ss);
             if (sa != NEK_OK) return sa;
+            iter_launches++;
         }
         if (b->ngchunks > 0)
             kb_dssum<<<b->ngchunks, BT, 0, ss>>>(b->d_gch_begin, b->d_gch_prob, L.pdone, b->gs->d_offsets,
@@ -608,9 +624,57 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
         kb_beta<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, nc, L.sc, L.active);
         kb_test<<<(np + 255) / 256, 256, 0, ss>>>(np, tol_rel, L.sc, L.active, L.pdone);
         kb_p<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, mv, L.r, x, L.p, L.sc);
+        iter_launches += (b->ngchunks > 0 ? 1 : 0) + (Gff ? 0 : 1) + 5;
         return check_launch();
     };
-    const int per_iter_launches = static_cast<int>(b->groups.size()) + (Gff ? 6 : 7);
+    int graph_iter_launches = 0;  // launches in one replay of the captured graph
+    // (Re)captures per_graph iterations with the current ax_first on a private
+    // stream (the caller's may be the legacy default stream, which cannot be
+    // captured); nothing runs during capture.  The graph is launched on the
+    // caller's stream.
+    auto capture = [&]() -> nek_status {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+        cudaStream_t cs = nullptr;
+        nek_status r = check_cuda(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        if (r != NEK_OK) return r;
+        r = check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        graph_iter_launches = 0;
+        if (r == NEK_OK) {
+            for (int k = 0; k < per_graph && r == NEK_OK; k++) {
+                r = one_iteration(cs);
+                graph_iter_launches += iter_launches;
+            }
+            cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+            if (r == NEK_OK) r = check_cuda(ce);
+        }
+        cudaStreamDestroy(cs);
+        if (r == NEK_OK) r = check_cuda(cudaGraphInstantiate(&gexec, graph, 0));
+        return r;
+    };
+    // Advances ax_first past the finished problems at the start of each group
+    // (pdone on the host); true when a group's launch shrank by an eighth or
+    // more since the last capture, which is then worth a new graph.
+    std::vector<uint8_t> hdone(static_cast<size_t>(np), 0);
+    auto advance_windows = [&]() -> bool {
+        bool shrunk = false;
+        for (size_t gi = 0; gi < b->groups.size(); gi++) {
+            const auto& g = b->groups[gi];
+            int64_t f0 = g.nelt;
+            for (int q = 0; q < np; q++) {
+                if (b->prob_group[q] != static_cast<int>(gi) || hdone[q]) continue;
+                f0 = b->prob_el0[q] - g.elem0;  // the group's first problem still going
+                break;
+            }
+            if (f0 - ax_first[gi] >= std::max<int64_t>(1, g.nelt / 8)) {
+                ax_first[gi] = f0;
+                shrunk = true;
+            }
+        }
+        return shrunk;
+    };
 
     if (!minv) {
         if ((st = nek_batch_jacobi_minv(b, G, mask, L.minv, stream)) != NEK_OK) goto done;
@@ -629,38 +693,29 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
     if (max_iter > 0) {
         if ((st = one_iteration(s)) != NEK_OK) goto done;
         it_done = 1;
-        launches += per_iter_launches;
+        launches += iter_launches;
     }
-    if (per_graph > 0 && it_done < max_iter) {
-        // Capture on a private stream (the caller's may be the legacy default
-        // stream, which cannot be captured); nothing runs during capture.  The
-        // graph is then launched on the caller's stream.
-        cudaStream_t cs = nullptr;
-        if ((st = check_cuda(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking))) != NEK_OK) goto done;
-        nek_status sc_st = check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        if (sc_st == NEK_OK) {
-            for (int k = 0; k < per_graph && sc_st == NEK_OK; k++) sc_st = one_iteration(cs);
-            cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-            if (sc_st == NEK_OK) sc_st = check_cuda(ce);
-        }
-        cudaStreamDestroy(cs);
-        if ((st = sc_st) != NEK_OK) goto done;
-        if ((st = check_cuda(cudaGraphInstantiate(&gexec, graph, 0))) != NEK_OK) goto done;
-    }
+    if (per_graph > 0 && it_done < max_iter)
+        if ((st = capture()) != NEK_OK) goto done;
     while (it_done < max_iter) {
         if ((st = check_cuda(cudaMemcpyAsync(&active, L.active, sizeof(int), cudaMemcpyDeviceToHost, s))) != NEK_OK)
             goto done;
+        if ((st = check_cuda(cudaMemcpyAsync(hdone.data(), L.pdone, static_cast<size_t>(np),
+                                             cudaMemcpyDeviceToHost, s))) != NEK_OK)
+            goto done;
         if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
         if (active <= 0) break;
+        if (advance_windows() && gexec)
+            if ((st = capture()) != NEK_OK) goto done;
         if (gexec && it_done + per_graph <= max_iter) {
             if ((st = check_cuda(cudaGraphLaunch(gexec, s))) != NEK_OK) goto done;
             it_done += per_graph;
-            launches += per_graph * per_iter_launches;
+            launches += graph_iter_launches;
             graph_launches++;
         } else {
             if ((st = one_iteration(s)) != NEK_OK) goto done;
             it_done += 1;
-            launches += per_iter_launches;
+            launches += iter_launches;
         }
     }
     {

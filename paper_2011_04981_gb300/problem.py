@@ -78,12 +78,14 @@ class DeviceProblem:
 
 
 class DeviceBatch:
-    """Many meshes solved together: concatenated (sorted by nx) device buffers and a nek_batch plan."""
+    """Many meshes solved together: concatenated device buffers and a nek_batch plan.  Problems are
+    ordered by nx (the plan's requirement) and, within an nx, by size: the larger need more iterations,
+    so the finished ones gather at the start of each nx run, which the solve then stops launching."""
 
     def __init__(self, meshes, fields, device="cuda", ff=True):
         import torch
 
-        order = sorted(range(len(meshes)), key=lambda q: meshes[q].nx)
+        order = sorted(range(len(meshes)), key=lambda q: (meshes[q].nx, meshes[q].nelt, q))
         self.order = order
         self.meshes = [meshes[q] for q in order]
         self.device = torch.device(device)
