@@ -620,7 +620,7 @@ def run_native(args):
                      if args.ax == "fp64" else
                      {"bound": "hbm", "achieved": ax_bpp * pts / ax_t / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": ax_bpp * pts / ax_t / 1e9 / hbm, "traffic": traffic,
-                      "kernel": ("k_ax_ffi<%d>" if nx == 10 else "k_ax_ffe<%d>" if nx == 12 else "k_ax_ff<%d>") % nx,
+                      "kernel": ("k_ax_ffi<%d>" if nx in (10, 12) else "k_ax_ff<%d>") % nx,
                       "note": ("FP64-accurate float-float AX with the fused x / direction update, 104 algorithmic "
                                "B/point (p in and out 16, r 8, minv 8, x in and out 16, G 48, w 8)" if fused_dir else
                                "FP64-accurate float-float AX, 64 algorithmic B/point (u 8 + G 48 + w 8)") +

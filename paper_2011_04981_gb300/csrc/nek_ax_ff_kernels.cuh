@@ -223,11 +223,13 @@ constexpr int ff_groups(int nx) { return (nx + ff_ppt(nx) - 1) / ff_ppt(nx); }
 constexpr int ff_threads_per_elem(int nx) { return nx * nx * ff_groups(nx); }
 
 // Default elements per CTA: at least ~128 threads per CTA, 1, 2 or 4 where
-// possible (nx = 10 uses the item-mapped kernel, 128 threads per element).
+// possible; nx = 10 and 12 run the item-mapped kernel with 128 and 144 threads
+// per element, whose measured best counts are 1 and 4 (the tuner may change them).
 template <int NX>
 constexpr int ff_epb()
 {
     if constexpr (NX == 10) return 1;
+    if constexpr (NX == 12) return 4;
     return ff_threads_per_elem(NX) >= 128 ? 1 : ff_threads_per_elem(NX) >= 64 ? 2 : 4;
 }
 
@@ -525,228 +527,31 @@ __global__ void __launch_bounds__(NX* NX* ff_groups(NX)* EPB, (ff_min_blocks<NX,
 }
 
 // ------------------------------------------------------------------------
-// Even nx <= 12: operands laid out for the packed f32x2 instructions.
+// nx = 10 and 12: operands laid out for the packed f32x2 instructions.
 //
 // Shared memory holds u, wr and ws as float4 (h_k, h_k+1, l_k, l_k+1) per
 // (k-pair, j, i), so one 16-byte load gives both packed operands of a term; D is
-// kept pre-splatted (h, h, l, l) and, for the t-direction, as k-pair tables.
-// A thread (e, i, j) walks its whole column; its u column stays in registers as
-// (h, l) pairs, wt goes to a fourth block read back as that column in phase 2.
+// kept pre-splatted (h, h, l, l), for the t-direction as k-pair tables, and for
+// the r-contraction transposed, so that a warp reads it across i without bank
+// conflicts; wt goes to a fourth block, read back by columns in phase 2.
 template <int NX>
-constexpr size_t ffe_smem_bytes(int epb)
+constexpr size_t kpair_smem_bytes(int epb)
 {
     // U4, WR4, WS4: [EPB][NX/2][NX][NX] float4 = 3 * 8 B per point; WT2 [EPB][N3]
-    // float2; DS [NX][NX], DP / DPT [NX][NX/2] float4; rowabs, colabs, maxima.
-    return sizeof(float4) * (3 * (size_t)epb * (NX / 2) * NX * NX + NX * NX + NX * NX) +
+    // float2; DS [NX][NX], DP / DPT [NX][NX/2], DSt [NX][NX] float4; rowabs,
+    // colabs, maxima.
+    return sizeof(float4) * (3 * (size_t)epb * (NX / 2) * NX * NX + 3 * NX * NX) +
            sizeof(float2) * (size_t)epb * NX * NX * NX + sizeof(float) * (2 * NX + 4 * (size_t)epb + 4) + 16;
 }
 
-template <int NX, int EPB, int MODE>
-__global__ void __launch_bounds__(NX* NX* EPB, (ff_min_blocks<NX, EPB>()))
-    k_ax_ffe(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
-             const double* __restrict__ u, double* __restrict__ w, const int32_t* __restrict__ l2g,
-             const int32_t* __restrict__ eprob, const uint8_t* __restrict__ pdone, double* __restrict__ edot,
-             DirUpdate dir)
-{
-    static_assert(NX % 2 == 0 && NX <= 12, "even nx up to 12");
-    using T = float2;
-    constexpr int NP = NX / 2, N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB, PB = NP * N2;  // PB: float4s per elt
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* U4 = reinterpret_cast<float4*>(smem_raw);  // [EPB][NP][NX][NX]
-    float4* WR4 = U4 + EPB * PB;
-    float4* WS4 = WR4 + EPB * PB;
-    float2* WT2 = reinterpret_cast<float2*>(WS4 + EPB * PB);  // [EPB][N3] wt (h, l)
-    float4* DS = reinterpret_cast<float4*>(WT2 + EPB * N3);    // DS[a*NX+b] = (Dh,Dh,Dl,Dl) of D[a][b]
-    float4* DP = DS + N2;              // DP[l*NP+kp]  = (Dh[2kp][l], Dh[2kp+1][l], Dl[2kp][l], Dl[2kp+1][l])
-    float4* DPT = DP + NX * NP;        // DPT[l*NP+kp] = (Dh[l][2kp], Dh[l][2kp+1], Dl[l][2kp], Dl[l][2kp+1])
-    float* sRow = reinterpret_cast<float*>(DPT + NX * NP);
-    float* sCol = sRow + NX;
-    float* sMax = sCol + NX;
-
-    const int tid = threadIdx.x;
-    const int64_t e0 = (int64_t)blockIdx.x * EPB;
-    const int ne = static_cast<int>(nelt - e0 < EPB ? nelt - e0 : EPB);
-    if (cta_skipped<MODE>(eprob, pdone, e0, ne)) return;  // uniform over the CTA, before any barrier
-
-    for (int q = tid; q < N2; q += NT) {
-        const int a = q / NX, b = q % NX;
-        const float2 d = split_double(D[q]);
-        DS[q] = make_float4(d.x, d.x, d.y, d.y);
-        float* dp = reinterpret_cast<float*>(DP + b * NP + a / 2);  // D[a][b]: k = a, l = b
-        dp[a & 1] = d.x;
-        dp[2 + (a & 1)] = d.y;
-        float* dt = reinterpret_cast<float*>(DPT + a * NP + b / 2);  // D[a][b]: l = a, k = b
-        dt[b & 1] = d.x;
-        dt[2 + (b & 1)] = d.y;
-    }
-    for (int q = tid; q < 4 * EPB; q += NT) sMax[q] = 0.f;
-    load_input<MODE, NT>(tid, ne * N3, e0 * N3, u, l2g, dir, [&](int q, double val) {
-        const int el = q / N3, p = q - el * N3;
-        const int k = p / N2, ji = p - k * N2;
-        const float2 v = split_double(val);
-        float* dst = reinterpret_cast<float*>(U4 + el * PB + (k / 2) * N2 + ji);
-        dst[k & 1] = v.x;
-        dst[2 + (k & 1)] = v.y;
-    });
-    __syncthreads();
-    for (int q = tid; q < NX; q += NT) {
-        float r = 0.f, c = 0.f;
-        for (int l = 0; l < NX; l++) {
-            r += fabsf(DS[q * NX + l].x);
-            c += fabsf(DS[l * NX + q].x);
-        }
-        sRow[q] = r * 1.0001f;
-        sCol[q] = c * 1.0001f;
-    }
-
-    const int el = tid / N2;
-    const int q2 = tid - el * N2;
-    const int i = q2 % NX, j = q2 / NX;
-    const bool active = el < ne;
-    const float4* ue = U4 + el * PB;
-    // own column of u as (h, l) pairs: uc[l] = u(i, j, l)
-    float2 uc[NX];
-    {
-        float m = 0.f;
-        if (active) {
-#pragma unroll
-            for (int kp = 0; kp < NP; kp++) {
-                const float4 v = ue[kp * N2 + j * NX + i];
-                uc[2 * kp] = make_float2(v.x, v.z);
-                uc[2 * kp + 1] = make_float2(v.y, v.w);
-                m = absmax_bits(v.x, absmax_bits(v.y, m));
-            }
-        }
-        segmented_max_to_smem(4 * el, m, sMax);
-    }
-    __syncthreads();
-
-    // ------------------------------------------------------------- phase 1
-    float mx_r = 0.f, mx_s = 0.f, mx_t = 0.f;
-    if (active) {
-        const float umax = sMax[4 * el] * 1.0001f;
-        const T sig_r = splat<T>(offset_for(sRow[i] * umax));
-        const T sig_s = splat<T>(offset_for(sRow[j] * umax));
-        const float4* Ge = Gff + (e0 + el) * (int64_t)N3 * 3;
-        float4* wre = WR4 + el * PB;
-        float4* wse = WS4 + el * PB;
-        float2* wte = WT2 + el * N3;
-#pragma unroll 1
-        for (int kp = 0; kp < NP; kp++) {
-            const int k0 = 2 * kp;
-            OffsetAcc<T> ar, as, at;
-            ar.init(sig_r);
-            as.init(sig_s);
-            at.init(make_float2(offset_for(sRow[k0] * umax), offset_for(sRow[k0 + 1] * umax)));
-            const float4* ur = ue + kp * N2 + j * NX;  // u(l, j, k0..k0+1) at ur[l]
-            const float4* us = ue + kp * N2 + i;       // u(i, l, k0..k0+1) at us[l * NX]
-#pragma unroll
-            for (int l = 0; l < NX; l++) {
-                const float4 a = ur[l], b = us[l * NX];
-                const float4 dr = DS[i * NX + l], ds = DS[j * NX + l], dt = DP[l * NP + kp];
-                ar.add(make_float2(dr.x, dr.y), make_float2(dr.z, dr.w), make_float2(a.x, a.y),
-                       make_float2(a.z, a.w));
-                as.add(make_float2(ds.x, ds.y), make_float2(ds.z, ds.w), make_float2(b.x, b.y),
-                       make_float2(b.z, b.w));
-                at.add(make_float2(dt.x, dt.y), make_float2(dt.z, dt.w), make_float2(uc[l].x, uc[l].x),
-                       make_float2(uc[l].y, uc[l].y));
-            }
-            T urh, url, ush, usl, uth, utl;
-            ar.finish(urh, url);
-            as.finish(ush, usl);
-            at.finish(uth, utl);
-            T gf[12];
-#pragma unroll
-            for (int q = 0; q < 2; q++) {
-                const int p = i + NX * (j + NX * (k0 + q));
-                const float4 a = __ldg(Ge + 3 * p), b = __ldg(Ge + 3 * p + 1), c = __ldg(Ge + 3 * p + 2);
-                const float v[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
-#pragma unroll
-                for (int t = 0; t < 12; t++) {
-                    if (q)
-                        gf[t].y = v[t];
-                    else
-                        gf[t].x = v[t];
-                }
-            }
-            T wrh, wrl, wsh, wsl, wth, wtl;
-            df_dot3(gf[0], gf[1], urh, url, gf[2], gf[3], ush, usl, gf[4], gf[5], uth, utl, wrh, wrl);
-            df_dot3(gf[2], gf[3], urh, url, gf[6], gf[7], ush, usl, gf[8], gf[9], uth, utl, wsh, wsl);
-            df_dot3(gf[4], gf[5], urh, url, gf[8], gf[9], ush, usl, gf[10], gf[11], uth, utl, wth, wtl);
-            wre[kp * N2 + j * NX + i] = make_float4(wrh.x, wrh.y, wrl.x, wrl.y);
-            wse[kp * N2 + j * NX + i] = make_float4(wsh.x, wsh.y, wsl.x, wsl.y);
-            wte[i + NX * (j + NX * k0)] = make_float2(wth.x, wtl.x);
-            wte[i + NX * (j + NX * (k0 + 1))] = make_float2(wth.y, wtl.y);
-            mx_r = absmax_bits(wrh.x, absmax_bits(wrh.y, mx_r));
-            mx_s = absmax_bits(wsh.x, absmax_bits(wsh.y, mx_s));
-            mx_t = absmax_bits(wth.x, absmax_bits(wth.y, mx_t));
-        }
-    }
-    segmented_max_to_smem(4 * el + 1, mx_r, sMax);
-    segmented_max_to_smem(4 * el + 2, mx_s, sMax);
-    segmented_max_to_smem(4 * el + 3, mx_t, sMax);
-    __syncthreads();
-
-    // ------------------------------------------------------------- phase 2
-    double energy = 0.0;  // kModeDot: sum of u . w over this thread's points
-    if (active) {
-        const float4* wre = WR4 + el * PB;
-        const float4* wse = WS4 + el * PB;
-        const int64_t ef = (e0 + el) * (int64_t)N3;  // the element's first point
-        const float2* wte = WT2 + el * N3 + i + NX * j;  // wt(i, j, l) at wte[l * N2]
-        const float mwr = sMax[4 * el + 1] * 1.0001f, mws = sMax[4 * el + 2] * 1.0001f,
-                    mwt = sMax[4 * el + 3] * 1.0001f;
-        const float bij = sCol[i] * mwr + sCol[j] * mws;
-        double* we = w + (e0 + el) * (int64_t)N3;
-#pragma unroll 1
-        for (int kp = 0; kp < NP; kp++) {
-            const int k0 = 2 * kp;
-            double u0 = 0.0, u1 = 0.0;
-            if constexpr (mode_energies(MODE)) {  // issued here, used after the contraction
-                u0 = reread_input<MODE>(ef, i + NX * (j + NX * k0), u, l2g, dir);
-                u1 = reread_input<MODE>(ef, i + NX * (j + NX * (k0 + 1)), u, l2g, dir);
-            }
-            OffsetAcc<T> acc;
-            acc.init(make_float2(offset_for(bij + sCol[k0] * mwt), offset_for(bij + sCol[k0 + 1] * mwt)));
-            const float4* rr = wre + kp * N2 + j * NX;  // wr(l, j, k0..k0+1) at rr[l]
-            const float4* ss = wse + kp * N2 + i;       // ws(i, l, k0..k0+1) at ss[l * NX]
-#pragma unroll
-            for (int l = 0; l < NX; l++) {
-                const float4 a = rr[l], b = ss[l * NX];
-                const float4 ci = DS[l * NX + i], cj = DS[l * NX + j], dk = DPT[l * NP + kp];
-                acc.add(make_float2(ci.x, ci.y), make_float2(ci.z, ci.w), make_float2(a.x, a.y),
-                        make_float2(a.z, a.w));
-                acc.add(make_float2(cj.x, cj.y), make_float2(cj.z, cj.w), make_float2(b.x, b.y),
-                        make_float2(b.z, b.w));
-                const float2 tc = wte[l * N2];
-                acc.add(make_float2(dk.x, dk.y), make_float2(dk.z, dk.w), make_float2(tc.x, tc.x),
-                        make_float2(tc.y, tc.y));
-            }
-            T hi, lo;
-            acc.finish(hi, lo);
-            const int p0 = i + NX * (j + NX * k0);
-            const double w0 = join_pair(hi.x, lo.x), w1 = join_pair(hi.y, lo.y);
-            we[p0] = w0;
-            we[p0 + N2] = w1;
-            if constexpr (mode_energies(MODE)) energy = fma(u1, w1, fma(u0, w0, energy));
-        }
-    }
-    if constexpr (mode_energies(MODE)) element_sums<N2, EPB>(energy, reinterpret_cast<double*>(U4), edot + e0, ne);
-}
-
-// ------------------------------------------------------------------------
-// Even nx <= 12, item mapping: the same shared-memory layout and the same
-// arithmetic per point as k_ax_ffe, but each thread takes (column, k-pair)
-// items q = t, t + TPE, ... of its element instead of one whole column, so the
-// element's columns fill whole warps: at nx = 10, TPE = 128 threads share 500
-// items (at most 4 each), where one column per thread makes a 100-thread CTA
-// run a fourth warp on 4 lanes, a quarter of its issue slots.  A thread reads
-// the column values of the t-contraction from shared memory (one 16-byte load
-// per k-pair) instead of holding its column in registers.  Every output is
-// summed in the same order as in k_ax_ffe.  (At nx = 12 whole warps need 96 or
-// 288 threads per element, which shared memory or registers then hold to 9
-// resident warps per SM, fewer than k_ax_ffe's 13.5 busy ones.)
-constexpr int ffi_tpe(int) { return 128; }
+// Item mapping: the TPE threads of an element take its (column, k-pair) items
+// q = t, t + TPE, ...  At nx = 10, 128 threads share 500 items (at most 4
+// each): one column per thread would make a 100-thread CTA run a fourth warp on
+// 4 lanes, a quarter of its issue slots.  At nx = 12, 144 threads take one
+// column each (6 items); with four elements per CTA that is 18 full warps.  A
+// thread reads the column values of the t-contraction from shared memory (one
+// 16-byte load per k-pair) instead of holding a column in registers.
+constexpr int ffi_tpe(int nx) { return nx == 12 ? 144 : 128; }
 
 // CTAs per SM the register budget is set for: 20 resident warps (96 registers
 // a thread at one element per CTA; the kernel then spills 4-8 bytes).
@@ -950,30 +755,22 @@ __global__ void __launch_bounds__(ffi_tpe(NX) * EPB, (ffi_min_blocks<NX, EPB>())
     if constexpr (mode_energies(MODE)) element_sums<TPE, EPB>(energy, reinterpret_cast<double*>(U4), edot + e0, ne);
 }
 
-// The k-pair layout is used where it measured faster than the column walk on
-// GB300 (nx = 10: 28.6 vs 25.6 GDOF/s; nx = 12: equal; nx = 8: 32.1 vs 36.4).
-// The choice is fixed per nx, never tuned at run time, because the two orders
-// of summation round differently.
-template <int NX>
-constexpr bool ff_packed_layout()
-{
-    return NX == 10 || NX == 12;
-}
-
-// nx = 10 runs the item-mapped form of the k-pair layout.
+// The k-pair layout (k_ax_ffi) is used where it measured faster than the
+// column walk on GB300 (nx = 10: 34.0 vs 25.6 GDOF/s; nx = 12: 26.5 vs 23.2;
+// nx = 8: 32.1 vs 36.4 with an earlier form of the layout).  The choice is
+// fixed per nx, never tuned at run time, because the two orders of summation
+// round differently.
 template <int NX>
 constexpr bool ff_item_layout()
 {
-    return NX == 10;
+    return NX == 10 || NX == 12;
 }
 
 template <int NX, int EPB>
 constexpr size_t ff_variant_smem()
 {
     if constexpr (ff_item_layout<NX>())
-        return ffe_smem_bytes<NX>(EPB) + sizeof(float4) * NX * NX;  // + the transposed D table
-    else if constexpr (ff_packed_layout<NX>())
-        return ffe_smem_bytes<NX>(EPB);
+        return kpair_smem_bytes<NX>(EPB);
     else
         return ff_smem_bytes<NX, EPB>();
 }
@@ -987,20 +784,11 @@ nek_status launch_ax_ff_kernel(int64_t nelt, const double* D, const float* Gff, 
     static std::atomic<uint64_t> configured{0};
     const int64_t blocks = (nelt + EPB - 1) / EPB;
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
-    if constexpr (ff_packed_layout<NX>()) {
-        if constexpr (ff_item_layout<NX>()) {
-            nek_status st = ensure_dyn_smem(k_ax_ffi<NX, EPB, MODE>, smem, configured);
-            if (st != NEK_OK) return st;
-            k_ax_ffi<NX, EPB, MODE><<<(unsigned)blocks, ffi_tpe(NX) * EPB, smem, s>>>(
-                nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot,
-                dir ? *dir : DirUpdate{});
-        } else {
-            nek_status st = ensure_dyn_smem(k_ax_ffe<NX, EPB, MODE>, smem, configured);
-            if (st != NEK_OK) return st;
-            k_ax_ffe<NX, EPB, MODE><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
-                nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot,
-                dir ? *dir : DirUpdate{});
-        }
+    if constexpr (ff_item_layout<NX>()) {
+        nek_status st = ensure_dyn_smem(k_ax_ffi<NX, EPB, MODE>, smem, configured);
+        if (st != NEK_OK) return st;
+        k_ax_ffi<NX, EPB, MODE><<<(unsigned)blocks, ffi_tpe(NX) * EPB, smem, s>>>(
+            nelt, D, reinterpret_cast<const float4*>(Gff), u, w, l2g, eprob, pdone, edot, dir ? *dir : DirUpdate{});
     } else {
         nek_status st = ensure_dyn_smem(k_ax_ff<NX, EPB, MODE>, smem, configured);
         if (st != NEK_OK) return st;
@@ -1035,9 +823,7 @@ nek_status launch_ax_ff_variant(int64_t nelt, const double* D, const float* Gff,
 template <int NX, int EPB>
 constexpr bool ff_fits()
 {
-    constexpr int threads = ff_item_layout<NX>()     ? ffi_tpe(NX) * EPB
-                            : ff_packed_layout<NX>() ? NX * NX * EPB
-                                                     : ff_threads_per_elem(NX) * EPB;
+    constexpr int threads = ff_item_layout<NX>() ? ffi_tpe(NX) * EPB : ff_threads_per_elem(NX) * EPB;
     return threads <= 1024 && ff_variant_smem<NX, EPB>() <= 227 * 1024;
 }
 
