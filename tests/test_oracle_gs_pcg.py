@@ -146,3 +146,21 @@ def test_pcg_fixed_iterations_and_breakdown():
     fn[0, 42] = np.nan  # node (2,2,2) of element 0: interior, not masked
     st, x, it, rr = ref.pcg(P.D, P.G, P.offsets, P.idx, P.mesh.mask, P.minv, fn, tol=1e-8)
     assert st == ref.BREAKDOWN
+
+
+@pytest.mark.parametrize("dims,nx", [((2, 2, 2), 4), ((3, 2, 2), 6), ((2, 3, 2), 10)])
+def test_element_energies_give_the_cg_inner_product(dims, nx):
+    """The identity the GPU solve uses for <p,w>: for p continuous across elements and zero on the
+    mask, <p, mask.dssum(A_L p)>_c equals the sum over elements of p_e . (A_e p_e).  A discontinuous p,
+    or one that is not zero on the mask, breaks it (so the check is not vacuous)."""
+    mesh = inputs.box_mesh(*dims, nx, perturb=0.15, seed=nx)
+    P = ref.Problem(mesh)
+    p = ref.mask_apply(mesh.mask, inputs.random_global_field(mesh, seed=3))
+    lhs = float(np.sum(P.c * p * P.apply(p)))
+    rhs = float(np.sum(p * ref.ax(P.D, P.G, p)))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    assert lhs > 0.0
+    for v in (inputs.random_local_field(mesh.nelt, nx, seed=4),  # a different value in every copy of a node
+              inputs.random_global_field(mesh, seed=5)):  # continuous but not zero on the mask
+        e_sum = float(np.sum(v * ref.ax(P.D, P.G, v)))
+        assert abs(float(np.sum(P.c * v * P.apply(v))) - e_sum) > 1e-6 * abs(e_sum)
