@@ -25,6 +25,13 @@
 // nek_geom_ff into [e][p][12] floats (48 B per point, the same HBM traffic as
 // FP64 G).
 //
+// Two kernel families: k_ax_ff walks (i, j) columns (or groups of planes
+// above nx = 12) with u, wr, ws, wt as float pairs in shared memory; k_ax_ffi
+// (nx = 10 and 12) keeps k-plane pairs as float4 so one load feeds a packed
+// instruction, and spreads an element's (column, k-pair) items over whole
+// warps.  Both take a compile-time load mode (plain, gathered, skipping
+// finished problems, with element energies, with the solve's direction update).
+//
 // This header holds the kernels and their launch templates; the per-nx
 // launchers are compiled in nek_ax_ff_nx_*.cu (a few nx each, so the build's
 // translation units compile in parallel) and nek_ax_ff.cu dispatches to them.
