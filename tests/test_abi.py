@@ -145,6 +145,9 @@ def test_tuning_and_lowp_entry_points_reject_bad_arguments(lib):
     assert L.nek_set_ax_epb(2, 8, 1) == nekax.OK and L.nek_get_ax_epb(2, 8) == 1 and L.nek_get_ax_epb(1, 8) == 4
     assert L.nek_set_ax_epb(1, 8, 0) == nekax.OK and L.nek_get_ax_epb(2, 8) == 0
     assert L.nek_get_ax_epb(7, 8) == 0
+    # nx = 12's item-mapped kernel at four elements per CTA (576 threads) just fits 227 KB of shared memory
+    assert L.nek_set_ax_epb(1, 12, 4) == nekax.OK and L.nek_set_ax_epb(1, 12, 0) == nekax.OK
+    assert L.nek_set_ax_epb(1, 10, 4) == nekax.OK and L.nek_set_ax_epb(1, 10, 0) == nekax.OK
     assert L.nek_tune_ax(0, 0, 8, A16, A16, A16, A16 * 2, None, None, None) == nekax.ERR_INVALID_ARG
     assert L.nek_tune_ax(0, 4, 8, A16, A16 + 8, A16, A16 * 2, None, None, None) == nekax.ERR_INVALID_ARG
     assert L.nek_tune_ax(0, 4, 8, A16, A16, A16, A16 + 64, None, None, None) == nekax.ERR_INVALID_ARG
