@@ -38,7 +38,7 @@ FP64_PEAK_TFLOPS = 1.2586  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=100, help="PCG iterations per step")
     ap.add_argument("--nx", type=int, default=10)
