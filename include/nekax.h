@@ -261,8 +261,8 @@ nek_status nek_jacobi_minv(const nek_gs* gs, int64_t nelt, int nx, const double*
 
 /* result[0] = sum_p c_p a_p b_p with c = 1/multiplicity (the global inner
  * product of two consistent fields; Section II-B's MPI_Allreduce becomes a
- * device reduction on one GPU).  a, b, result device; deterministic for a given
- * npts.  Uses library-owned scratch for per-block partial sums (allocated on the
+ * device reduction on one GPU).  a, b, result device, 8-byte aligned;
+ * deterministic for a given npts.  Uses library-owned scratch for per-block partial sums (allocated on the
  * first call for a plan and kept with it).  Async. */
 nek_status nek_dot_c(const nek_gs* gs, const double* a, const double* b, double* result, void* stream);
 
@@ -273,14 +273,17 @@ nek_status nek_dot_c(const nek_gs* gs, const double* a, const double* b, double*
  * counterpart; it is an interface convenience.
  *   n: number of points, 0 <= n <= 2^31-1 (larger n returns NEK_ERR_TOO_LARGE);
  *   c: weights (e.g. nek_gs_inv_multiplicity), a, b: inputs, result: output
- *      (1 double) -- all device pointers owned by the caller.
+ *      (1 double) -- all device pointers owned by the caller, 8-byte aligned
+ *      (else NEK_ERR_INVALID_ARG); n = 0 writes 0.
  *   result[0] = sum_p c_p a_p b_p, computed by the same kernels and grid as
  *   nek_dot_c, so the two agree bit for bit on the same inputs.
  * The per-block partial sums live in a fixed 9.5 KB array inside the library
  * (held on every GPU that loads it until the process exits); nothing is
  * allocated or freed.  The first call on a device looks the array's device
  * address up (which can load the library's GPU module); make that first call
- * before any stream capture.  All calls on a device share the array: calls that
+ * before any stream capture.  The address is kept per device together with the
+ * id of the context it belongs to; after cudaDeviceReset the next call is a
+ * first call again.  All calls on a device share the array: calls that
  * overlap on the GPU (different streams, no ordering) race and may return wrong
  * sums.  Async on stream.
  */
@@ -454,6 +457,25 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
                            const uint8_t* mask, const double* minv, const double* f, double* x, double tol_rel,
                            int max_iter, void* workspace, int* iters_out, double* relres_out, nek_cg_opts* opts,
                            void* stream);
+
+/* Same solve with f and x in HOST memory (pinned or pageable), for callers
+ * whose right-hand side and solution live on the host: f_host is copied to the
+ * device, the solve of nek_cg_solve_ex runs, and x is copied back to x_host;
+ * the call returns once x_host holds the result (also on NOT_CONVERGED and
+ * BREAKDOWN, which leave the last iterate there).  The copies are part of the
+ * call, one cudaMemcpyAsync each way on `stream`.
+ *   f_host, x_host: host, nelt*nx^3 doubles each, E-vector layout.
+ *   staging: device, >= nek_cg_host_staging_bytes(nelt, nx) bytes,
+ *     256-aligned (device copies of f and x), or NULL to allocate
+ *     (stream-ordered) and free inside the call.
+ *   Every other argument as nek_cg_solve_ex.  Synchronous.
+ */
+size_t nek_cg_host_staging_bytes(int64_t nelt, int nx);
+
+nek_status nek_cg_solve_host(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
+                             const uint8_t* mask, const double* minv, const double* f_host, double* x_host,
+                             double tol_rel, int max_iter, void* workspace, void* staging, int* iters_out,
+                             double* relres_out, nek_cg_opts* opts, void* stream);
 
 /* ------------------------------------------------- unique-node vectors ---
  * The solve on unique-node ("L-") vectors: every global node is stored once,

@@ -15,6 +15,13 @@
  * the paper leaves open is read as the standard spectral-element definition;
  * each function says which reading it takes.
  *
+ * OpenMP: the element loop of ref_ax, the group loop of ref_dssum and the
+ * pointwise loops of ref_pcg carry "omp parallel for" pragmas.  They split
+ * independent iterations only (elements, disjoint groups, points) and leave the
+ * dot products serial, so a build with -fopenmp computes every value with the
+ * same operations in the same order as the default build (which ignores the
+ * pragmas); it exists only to time the oracle on all host cores.
+ *
  * Layouts: an E-vector is [nelt][nx][nx][nx] with i fastest; the geometric
  * factors are [nelt][nx^3][6] in the order (rr, rs, rt, ss, st, tt) = g(1..6)
  * of Listing 1; D is row-major D[i*nx+l] = l_l'(xi_i) (the paper's dxm1, whose
@@ -110,11 +117,19 @@ int64_t ref_geom(int64_t nelt, int nx, const double* z, const double* rho, const
 int ref_ax(int64_t nelt, int nx, const double* D, const double* G, const double* u, double* w)
 {
     int64_t n3 = (int64_t)nx * nx * nx;
-    double* wr = (double*)malloc(sizeof(double) * n3 * 3);
-    if (!wr) return REF_NOMEM;
-    double* ws = wr + n3;
-    double* wt = ws + n3;
+    int status = REF_OK;
+#pragma omp parallel
+    {
+    double* wr = (double*)malloc(sizeof(double) * n3 * 3);  /* scratch of one element (per thread) */
+    if (!wr) {
+#pragma omp atomic write
+        status = REF_NOMEM;
+    }
+    double* ws = wr ? wr + n3 : NULL;
+    double* wt = ws ? ws + n3 : NULL;
+#pragma omp for schedule(static)
     for (int64_t e = 0; e < nelt; e++) {
+        if (!wr) continue;
         const double* ue = u + e * n3;
         const double* ge = G + e * n3 * 6;
         double* we = w + e * n3;
@@ -144,7 +159,8 @@ int ref_ax(int64_t nelt, int nx, const double* D, const double* G, const double*
                 }
     }
     free(wr);
-    return REF_OK;
+    }
+    return status;
 }
 
 /* ---- gather-scatter (the exchange with neighbouring elements of Section II-B) ----
@@ -196,6 +212,7 @@ int64_t ref_gs_build(int64_t n, const int64_t* glo, int64_t* offsets, int64_t* i
 
 void ref_dssum(int64_t ngroups, const int64_t* offsets, const int64_t* idx, double* v)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < ngroups; g++) {
         double s = v[idx[offsets[g]]];
         for (int64_t o = offsets[g] + 1; o < offsets[g + 1]; o++) s += v[idx[o]];
@@ -218,6 +235,7 @@ void ref_inv_multiplicity(int64_t n, int64_t ngroups, const int64_t* offsets, co
  * Dirichlet): v_p <- 0 where mask_p == 0. */
 void ref_mask(int64_t n, const uint8_t* mask, double* v)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < n; p++)
         if (mask[p] == 0) v[p] = 0.0;
 }
@@ -317,6 +335,7 @@ int ref_pcg(int64_t nelt, int nx, const double* D, const double* G, int64_t ngro
             break;
         }
         double alpha = rz / pw;
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < n; q++) {
             x[q] += alpha * p[q];
             r[q] -= alpha * w[q];
@@ -333,10 +352,12 @@ int ref_pcg(int64_t nelt, int nx, const double* D, const double* G, int64_t ngro
             status = REF_OK;
             break;
         }
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < n; q++) z[q] = minv[q] * r[q];
         double rz_new = wdot(n, c, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (int64_t q = 0; q < n; q++) p[q] = z[q] + beta * p[q];
     }
     free(buf);

@@ -197,3 +197,183 @@ def element_inputs(r, jr):
     x = np.stack([np.where(sr[:, None] > 0, r / np.where(sr > 0, sr, 1)[:, None], 0.0),
                   np.where(sj[:, None] > 0, jr / np.where(sj > 0, sj, 1)[:, None], 0.0)], axis=1)
     return x, sr, sj
+
+
+# ---------------------------------------------------------------------------
+# Componentwise rounding-error bounds of a reduced-precision evaluation.
+#
+# The GPU kernels evaluate the network in FP32 (and, in the tensor-core form,
+# round the input and the hidden activations to BF16 first).  Every rounding
+# follows the standard model fl(a op b) = (a op b)(1 + d), |d| <= u, and each
+# output, activation and gradient entry gets its own bound, propagated through
+# the layers to first order.  Two modes:
+#
+# * "worst": a sum of n terms is off by at most gamma_n = n u / (1 - n u) times
+#   the sum of the terms' absolute values, and an input error bound e_i reaches
+#   a linear output as sum_i |W_i| e_i (Higham, "Accuracy and Stability of
+#   Numerical Algorithms", Sec. 3.1).  Rigorous for any summation order, but it
+#   compounds the worst case of every layer, and through three 16-channel
+#   3x3x3 layers it overstates the error by orders of magnitude.
+# * "rms": roundings are independent and of mean zero (the model of Higham and
+#   Mary, "A new approach to probabilistic rounding error analysis", SIAM J.
+#   Sci. Comput. 2019): the sum's own error scales as sqrt(n) u times the sum
+#   of absolute values, and errors carried in from the inputs combine as
+#   sqrt(sum_i W_i^2 e_i^2); independent contributions add in quadrature.  The
+#   result is an error scale; a test multiplies it by a safety factor lambda.
+# ---------------------------------------------------------------------------
+
+U32 = 2.0 ** -24
+GELU_LIP = 1.1290      # max |gelu'(v)|, reached at v = sqrt(2)
+GELU2_LIP = 0.7979     # max |gelu''(v)| = 2 phi(0)
+GELU_ABS = 8 * U32     # FP32 gelu: relative error in |gelu| plus absolute error in |v| (erf near -1)
+GELUP_ABS = 16 * U32   # FP32 gelu': absolute error (it is O(1))
+
+
+def gamma(n, u=U32):
+    return n * u / (1.0 - n * u)
+
+
+class _Rules:
+    """How errors combine in one mode (see above)."""
+
+    def __init__(self, mode, u):
+        if mode not in ("worst", "rms"):
+            raise ValueError(mode)
+        self.worst, self.u = mode == "worst", u
+
+    def sum_err(self, n):
+        """Factor on the sum of absolute values for a sum of n rounded terms."""
+        return gamma(n, self.u) if self.worst else math.sqrt(n) * self.u
+
+    def add(self, *parts):
+        if self.worst:
+            return sum(parts)
+        return np.sqrt(sum(np.asarray(p) ** 2 for p in parts))
+
+    def lin(self, f, e, W):
+        """Error carried through a linear map f(input, weights) from input errors e."""
+        return f(e, np.abs(W)) if self.worst else np.sqrt(f(e * e, W * W))
+
+    def bil(self, f, e1, a2, a1, e2):
+        """Error of f(v1, v2) (bilinear, e.g. a weight gradient) from errors e1, e2 of v1, v2."""
+        if self.worst:
+            return f(e1, np.abs(a2)) + f(np.abs(a1), e2)
+        return np.sqrt(f(e1 * e1, a2 * a2) + f(a1 * a1, e2 * e2))
+
+
+def _conv_nb(x, W):
+    return conv(x, W, np.zeros(W.shape[0]))
+
+
+def forward_bound(theta, x, u_act=0.0, u=U32, mode="worst"):
+    """(y, cache, bounds): the FP64 network on x and, per output, the error bound
+    (mode "worst") or error scale (mode "rms") of an evaluation with unit
+    roundoff u in every sum and with the input and both hidden activations
+    rounded to a unit roundoff u_act (0 = no rounding) before the convolution
+    that reads them.  bounds = (dx0, dh1, da1, dh2, da2, dy), each an array of
+    the matching activation's shape."""
+    R = _Rules(mode, u)
+    P = unpack(theta)
+    y, cache = forward(theta, x, keep=True)
+    x0, h1, a1, h2, a2 = cache
+    dx0 = u_act * np.abs(x0)
+
+    def layer(a, da, W, b, cin):
+        absum = _conv_nb(np.abs(a) + da, np.abs(W)) + np.abs(b)[None, :, None, None, None]
+        return R.add(R.lin(_conv_nb, da, W), R.sum_err(27 * cin + 1) * absum)
+
+    def act(h, a, dh):
+        da = R.add(GELU_LIP * dh, GELU_ABS * (np.abs(a) + np.abs(h)))
+        return R.add(da, u_act * (np.abs(a) + da))
+
+    dh1 = layer(x0, dx0, P["W1"], P["b1"], CIN)
+    da1 = act(h1, a1, dh1)
+    dh2 = layer(a1, da1, P["W2"], P["b2"], CH)
+    da2 = act(h2, a2, dh2)
+    dy = layer(a2, da2, P["W3"], P["b3"], CH)
+    return y, cache, (dx0, dh1, da1, dh2, da2, dy)
+
+
+def _backward_bound(theta, cache, fb, dy, ddy, B, R):
+    """Per-parameter bound (or scale) of the gradient of sum(dy * y) evaluated
+    with roundoff R.u from a forward whose errors are fb (forward_bound) and an
+    output gradient dy known to within ddy.  Weight-gradient sums run over the
+    points of a sample and then over the batch: 512 + B terms."""
+    P = unpack(theta)
+    x0, h1, a1, h2, a2 = cache
+    _, dh1e, da1e, dh2e, da2e, _ = fb
+    nsum = x0.shape[2] * x0.shape[3] * x0.shape[4] + B
+    g = {}
+
+    def wgrad(dh, ddh, a, da):
+        absum = conv_weight_grad(np.abs(dh), np.abs(a) + da)
+        return R.add(R.bil(conv_weight_grad, ddh, a, dh, da), R.sum_err(nsum) * absum)
+
+    def bgrad(dh, ddh):
+        s = (lambda v: v.sum(axis=(0, 2, 3, 4)))
+        carried = s(ddh) if R.worst else np.sqrt(s(ddh * ddh))
+        return R.add(carried, R.sum_err(nsum) * s(np.abs(dh)))
+
+    def through(dh_out, ddh_out, W, cout, h, dhe):
+        v = conv_input_grad(dh_out, W)
+        dv = R.add(R.lin(conv_input_grad, ddh_out, W),
+                   R.sum_err(27 * cout) * conv_input_grad(np.abs(dh_out), np.abs(W)))
+        gp = gelu_grad(h)
+        dh = v * gp
+        ddh = R.add(dv * np.abs(gp), (np.abs(v) + dv) * (GELU2_LIP * dhe + GELUP_ABS), R.u * np.abs(dh))
+        return dh, ddh
+
+    g["W3"] = wgrad(dy, ddy, a2, da2e)
+    g["b3"] = bgrad(dy, ddy)
+    dh2, ddh2 = through(dy, ddy, P["W3"], 1, h2, dh2e)
+    g["W2"] = wgrad(dh2, ddh2, a1, da1e)
+    g["b2"] = bgrad(dh2, ddh2)
+    dh1, ddh1 = through(dh2, ddh2, P["W2"], CH, h1, dh1e)
+    g["W1"] = wgrad(dh1, ddh1, x0, 0.0 * x0)
+    g["b1"] = bgrad(dh1, ddh1)
+    return pack(g)
+
+
+def loss_and_grad_bound(theta, x, t, u=U32, mode="worst"):
+    """(L, grad, bound): loss_and_grad plus a per-parameter error bound (or
+    scale, mode "rms") of an FP32 evaluation: forward, loss, backward and the
+    sum over the batch."""
+    R = _Rules(mode, u)
+    B = x.shape[0]
+    y, cache, fb = forward_bound(theta, x, 0.0, u, mode)
+    n = t[0].size
+    den = np.sum(t ** 2, axis=(1, 2, 3))
+    r = y[:, 0] - t
+    L = float(np.mean(np.sum(r ** 2, axis=(1, 2, 3)) / den))
+    dy = (2.0 / B) * (r / den[:, None, None, None])[:, None]
+    dr = R.add(fb[5][:, 0], u * np.abs(r))
+    ddy = R.add((2.0 / B) * (R.add(dr, R.sum_err(n) * np.abs(r)) / den[:, None, None, None])[:, None],
+                3 * u * np.abs(dy))
+    g, _ = backward(theta, cache, dy)
+    return L, g, _backward_bound(theta, cache, fb, dy, ddy, B, R)
+
+
+def energy_loss_and_grad_bound(theta, x, t, A, Aabs, nx, u=U32, mode="worst"):
+    """(L, grad, bound) of the element-energy loss, with A d and A t formed by a
+    reduced-precision operator whose componentwise error is at most
+    4 (u + (2 nx + 3) u) Aabs |v| (Aabs = the element matrix of |D| and |G|)."""
+    R = _Rules(mode, u)
+    B = x.shape[0]
+    y, cache, fb = forward_bound(theta, x, 0.0, u, mode)
+    yf = y[:, 0].reshape(B, -1)
+    tt = t.reshape(B, -1)
+    d = yf - tt
+    Ad = np.einsum("bpq,bq->bp", A, d)
+    den = np.einsum("bp,bpq,bq->b", tt, A, tt)
+    L = float(np.mean(np.sum(d * Ad, axis=1) / den))
+    dy = ((2.0 / B) * Ad / den[:, None]).reshape(y.shape)
+    g, _ = backward(theta, cache, dy)
+    cax = 4 * (u + (2 * nx + 3) * u)
+    dd = R.add(fb[5][:, 0].reshape(B, -1), u * np.abs(d))
+    mv = (lambda e, M: np.einsum("bpq,bq->bp", M, e))
+    dAd = R.add(R.lin(mv, dd, Aabs) if not R.worst else mv(dd, Aabs), cax * mv(np.abs(d) + dd, Aabs))
+    At_abs = mv(np.abs(tt), Aabs)
+    dden = (cax + R.sum_err(tt.shape[1]) * (1 + cax)) * np.sum(np.abs(tt) * At_abs, axis=1)
+    ddy = R.add((2.0 / B) * dAd / den[:, None], (2.0 / B) * np.abs(Ad) * dden[:, None] / den[:, None] ** 2,
+                3 * u * np.abs(dy.reshape(B, -1)))
+    return L, g, _backward_bound(theta, cache, fb, dy, ddy.reshape(y.shape), B, R)

@@ -29,21 +29,34 @@ from . import gll as _gll
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nekref.c")
 _SO = os.path.join(_HERE, "_nekref.so")
+_SO_OMP = os.path.join(_HERE, "_nekref_omp.so")
 
 OK, INVALID, NOT_CONVERGED, BREAKDOWN, NOMEM = 0, 1, 4, 5, 7
 
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle (plain gcc, no FMA contraction)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + ".tmp.%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-               "-o", tmp, _SRC, "-lm"]
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the C oracle (plain gcc, no FMA contraction).  openmp=True builds
+    the same source with -fopenmp into a second library, used only to time the
+    oracle on all host cores (same operations in the same order, see nekref.c)."""
+    so = _SO_OMP if openmp else _SO
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"] + \
+              (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _SO)
-    return _SO
+        os.replace(tmp, so)
+    return so
+
+
+def openmp_library():
+    """Path of the -fopenmp build of the oracle (built on first use), or None
+    when this host's compiler cannot build it."""
+    try:
+        return build(openmp=True)
+    except (OSError, subprocess.CalledProcessError):
+        return None
 
 
 def _open(path):

@@ -1,4 +1,6 @@
 // Status handling, GLL, mask, gather-scatter plan and dssum, weighted dot.
+#include <cuda.h>  // CUcontext / CUresult types only: the two driver calls below are fetched at run time
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -86,11 +88,49 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Per device: the array's device address and the id of the context it was
+// looked up in.  cudaDeviceReset destroys the primary context (and with it the
+// module that holds the array); the next context can place the array
+// elsewhere, so an address is reused only while the context id is unchanged.
+struct NoAllocSlot {
+    double* ptr = nullptr;
+    unsigned long long ctx_id = 0;
+};
+NoAllocSlot g_noalloc_slot[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Id of the calling thread's current context, 0 if there is none (driver
+// entry points fetched through the runtime, so the library does not link
+// libcuda itself).
+nek_status current_context_id(unsigned long long* id)
+{
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        nek_status st = check_cuda(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1));
+        if (st == NEK_OK) st = check_cuda(cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2));
+        if (st != NEK_OK) return st;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) return NEK_ERR_CUDA;
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return NEK_ERR_CUDA;
+    if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return NEK_ERR_CUDA;
+    return NEK_OK;
+}
 
 // Device address of g_noalloc_partials on the current device.  In host code the
-// symbol's name is only a host-side stand-in, so the address is looked up once
-// per device with cudaGetSymbolAddress (which may load the module) and cached.
+// symbol's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress (which may load the module) the first time a device is
+// used, and again only if that device's context has been replaced since.
 nek_status noalloc_scratch(double** out)
 {
     int dev = 0;
@@ -98,13 +138,17 @@ nek_status noalloc_scratch(double** out)
     if (st != NEK_OK) return st;
     if (dev < 0 || dev >= kMaxDevices) return NEK_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocSlot& slot = g_noalloc_slot[dev];
+    unsigned long long id = 0;
+    if ((st = current_context_id(&id)) != NEK_OK) return st;
+    if (!slot.ptr || id == 0 || id != slot.ctx_id) {
         void* p = nullptr;
-        st = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_partials));
-        if (st != NEK_OK) return st;
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
+        if ((st = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_partials))) != NEK_OK) return st;
+        if ((st = current_context_id(&id)) != NEK_OK) return st;  // the lookup made the primary context current
+        slot.ptr = static_cast<double*>(p);
+        slot.ctx_id = id;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return NEK_OK;
 }
 }  // namespace
@@ -118,9 +162,10 @@ extern "C" {
 nek_status nek_dot_c_noalloc(int64_t n, const double* c, const double* a, const double* b, double* result,
                              void* stream)
 {
-    if (n < 0 || !result) return NEK_ERR_INVALID_ARG;
+    if (n < 0 || !result || !is_aligned(result, 8)) return NEK_ERR_INVALID_ARG;
     if (n > kNoAllocMaxPoints) return NEK_ERR_TOO_LARGE;
-    if (n > 0 && (!c || !a || !b)) return NEK_ERR_INVALID_ARG;
+    if (n > 0 && (!c || !a || !b || !is_aligned(c, 8) || !is_aligned(a, 8) || !is_aligned(b, 8)))
+        return NEK_ERR_INVALID_ARG;
     double* parts = nullptr;
     nek_status st = noalloc_scratch(&parts);
     if (st != NEK_OK) return st;
@@ -339,9 +384,9 @@ nek_status nek_gs_inv_multiplicity(const nek_gs* gs, double* c, void* stream)
 
 nek_status nek_dot_c(const nek_gs* gs, const double* a, const double* b, double* result, void* stream)
 {
-    if (!gs || !result) return NEK_ERR_INVALID_ARG;
+    if (!gs || !result || !is_aligned(result, 8)) return NEK_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (gs->npts > 0 && (!a || !b)) return NEK_ERR_INVALID_ARG;
+    if (gs->npts > 0 && (!a || !b || !is_aligned(a, 8) || !is_aligned(b, 8))) return NEK_ERR_INVALID_ARG;
     if (!gs->d_partials) {
         nek_status st = check_cuda(cudaMalloc(&const_cast<nek_gs*>(gs)->d_partials, sizeof(double) * kMaxReduceBlocks));
         if (st != NEK_OK) return NEK_ERR_NOMEM;

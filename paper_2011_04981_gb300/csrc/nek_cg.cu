@@ -189,6 +189,46 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
     return st;
 }
 
+size_t nek_cg_host_staging_bytes(int64_t nelt, int nx)
+{
+    if (nelt < 0 || nx < kMinNx || nx > kMaxNx) return 0;
+    return 2 * pcg::align256(sizeof(double) * std::max<size_t>((size_t)nelt * nx * nx * nx, 1));
+}
+
+nek_status nek_cg_solve_host(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
+                             const uint8_t* mask, const double* minv, const double* f_host, double* x_host,
+                             double tol_rel, int max_iter, void* workspace, void* staging, int* iters_out,
+                             double* relres_out, nek_cg_opts* opts, void* stream)
+{
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (!gs || nelt < 0 || max_iter < 0 || !(tol_rel >= 0.0)) return NEK_ERR_INVALID_ARG;
+    const int64_t n = nelt * (int64_t)nx * nx * nx;
+    if (gs->npts != n) return NEK_ERR_INVALID_ARG;
+    if (n == 0) return NEK_OK;
+    if (!f_host || !x_host || (staging && !is_aligned(staging, 256))) return NEK_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* st_buf = staging;
+    nek_status st = NEK_OK;
+    if (!st_buf && (st = check_cuda(cudaMallocAsync(&st_buf, nek_cg_host_staging_bytes(nelt, nx), s))) != NEK_OK)
+        return NEK_ERR_NOMEM;
+    double* fd = static_cast<double*>(st_buf);
+    double* xd = reinterpret_cast<double*>(static_cast<char*>(st_buf) + pcg::align256(sizeof(double) * n));
+    const size_t bytes = sizeof(double) * (size_t)n;
+    st = check_cuda(cudaMemcpyAsync(fd, f_host, bytes, cudaMemcpyHostToDevice, s));
+    if (st == NEK_OK)
+        st = nek_cg_solve_ex(gs, nelt, nx, D, G, mask, minv, fd, xd, tol_rel, max_iter, workspace, iters_out,
+                             relres_out, opts, stream);
+    if (st == NEK_OK || st == NEK_ERR_NOT_CONVERGED || st == NEK_ERR_BREAKDOWN) {
+        nek_status st2 = check_cuda(cudaMemcpyAsync(x_host, xd, bytes, cudaMemcpyDeviceToHost, s));
+        if (st2 != NEK_OK) st = st2;
+    }
+    if (!staging) cudaFreeAsync(st_buf, s);
+    nek_status st3 = check_cuda(cudaStreamSynchronize(s));
+    return st == NEK_OK ? st3 : st;
+}
+
 nek_status nek_cg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
                         const uint8_t* mask, const double* minv, const double* f, double* x, double tol_rel,
                         int max_iter, void* workspace, int* iters_out, double* relres_out, void* stream)

@@ -55,7 +55,8 @@ struct Lp<__half> {
 // slot[key] = max(slot[key], v) for v >= 0, one shared-memory atomic per key per warp.
 __device__ __forceinline__ void segmented_max_to_smem(int key, float v, float* slot)
 {
-    const unsigned same = __match_any_sync(0xffffffffu, key);
+    // Lanes beyond a partial last warp do not exist, so only the active lanes are named.
+    const unsigned same = __match_any_sync(__activemask(), key);
     const unsigned m = __reduce_max_sync(same, __float_as_uint(v));
     if ((threadIdx.x & 31) == __ffs(same) - 1) atomicMax(reinterpret_cast<unsigned*>(slot + key), m);
 }

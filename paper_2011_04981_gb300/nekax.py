@@ -131,6 +131,9 @@ _SIGS = {
     "nek_cg_solve": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, _P], _I),
     "nek_cg_solve_ex": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, ctypes.POINTER(NekCgOpts), _P],
                         _I),
+    "nek_cg_host_staging_bytes": ([_I64, _I], ctypes.c_size_t),
+    "nek_cg_solve_host": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, _P, ctypes.POINTER(NekCgOpts),
+                           _P], _I),
     "nek_lvec_create": ([_I64, _P, _P, ctypes.POINTER(_P)], _I),
     "nek_lvec_destroy": ([_P], _I),
     "nek_lvec_size": ([_P], _I64),
@@ -472,6 +475,25 @@ def cg_solve(gs: GsPlan, nelt, nx, D, G, m, minv, f, x, tol=1e-8, max_iter=1000,
                                 ctypes.byref(opts), _stream(stream))
     if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
         raise NekError("nek_cg_solve", st)
+    return dict(status=st, iters=it.value, relres=rr.value, ax_ms_total=opts.ax_ms_total,
+                ax_launches=opts.ax_launches, kernel_launches=opts.kernel_launches)
+
+
+def cg_host_staging_bytes(nelt, nx):
+    return int(load().nek_cg_host_staging_bytes(nelt, nx))
+
+
+def cg_solve_host(gs: GsPlan, nelt, nx, D, G, m, minv, f_host, x_host, tol=1e-8, max_iter=1000, workspace=None,
+                  staging=None, check_every=1, time_ax=False, stream=None, ax_impl=AX_FP64, Gff=None):
+    """Jacobi-PCG with f and x in host memory (nek_cg_solve_host: the library copies f in and x out)."""
+    it = _I(0)
+    rr = _D(0.0)
+    opts = NekCgOpts(check_every, 1 if time_ax else 0, 0.0, 0, 0, int(ax_impl), _ptr(Gff))
+    st = load().nek_cg_solve_host(gs.handle, nelt, nx, _ptr(D), _ptr(G), _ptr(m), _ptr(minv), _ptr(f_host),
+                                  _ptr(x_host), float(tol), int(max_iter), _ptr(workspace), _ptr(staging),
+                                  ctypes.byref(it), ctypes.byref(rr), ctypes.byref(opts), _stream(stream))
+    if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+        raise NekError("nek_cg_solve_host", st)
     return dict(status=st, iters=it.value, relres=rr.value, ax_ms_total=opts.ax_ms_total,
                 ax_launches=opts.ax_launches, kernel_launches=opts.kernel_launches)
 

@@ -56,6 +56,14 @@ class DeviceProblem:
         return nekax.cg_solve(self.gs, self.nelt, self.nx, self.D, self.G, self.mask, self.minv, f, x, tol,
                               max_iter, workspace, check_every, time_ax, stream, ax_impl=ax_impl, Gff=Gff)
 
+    def cg_host(self, f_host, x_host, tol=1e-8, max_iter=1000, workspace=None, staging=None, check_every=1,
+                time_ax=False, stream=None, ax_impl=nekax.AX_FP64):
+        """The same solve with f and x in host memory (the library copies them)."""
+        Gff = self.prepare_ff() if ax_impl == nekax.AX_FF else None
+        return nekax.cg_solve_host(self.gs, self.nelt, self.nx, self.D, self.G, self.mask, self.minv, f_host,
+                                   x_host, tol, max_iter, workspace, staging, check_every, time_ax, stream,
+                                   ax_impl=ax_impl, Gff=Gff)
+
     def lvec(self):
         """Unique-node plan, its Jacobi inverse diagonal and solve workspace (built once)."""
         import torch

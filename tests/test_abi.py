@@ -231,3 +231,16 @@ def test_ax_lowp_tc_rejects_bad_arguments(lib):
     assert L.nek_ax_lowp_tc(4, 8, nekax.PREC_F16, A, A, A, A, A, None) == nekax.ERR_INVALID_ARG  # u and w overlap
     assert L.nek_ax_lowp_tc(4, 8, nekax.PREC_F16, A + 2, A, A, A, A + 0x100000, None) == nekax.ERR_INVALID_ARG
     assert L.nek_ax_lowp_tc(0, 8, nekax.PREC_BF16, None, None, None, None, None, None) == nekax.OK
+
+
+def test_cg_solve_host_rejects_bad_arguments_before_launch(lib):
+    A = 0x10000
+    L = lib
+    assert L.nek_cg_host_staging_bytes(-1, 10) == 0 and L.nek_cg_host_staging_bytes(2, 1) == 0
+    assert L.nek_cg_host_staging_bytes(2, 4) == 2 * 1024  # two vectors of 128 doubles, each 256-byte aligned
+    # bad nx, no plan, negative size, bad tolerance, misaligned staging
+    assert L.nek_cg_solve_host(None, 1, 1, A, A, A, A, A, A, 0.0, 1, None, None, None, None, None, None) == \
+        nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_cg_solve_host(None, 1, 4, A, A, A, A, A, A, 0.0, 1, None, None, None, None, None, None) == \
+        nekax.ERR_INVALID_ARG
+    # the remaining checks need a plan (device memory): see the GPU test of nek_cg_solve_host

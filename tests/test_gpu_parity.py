@@ -471,6 +471,70 @@ def test_cg_ff_solve_bit_identical_across_elements_per_cta(nx):
     assert _rel(outs[0], xr) <= 1e-9
 
 
+def test_cg_bench_size_fixed_iterations_match_oracle():
+    """The solve the benchmark times, at its size: the 32x32x32 box at nx = 10 with the benchmark's
+    seeds, the float-float operator in its solve form (element energies, fused x / direction update,
+    one element per CTA, the tuned count) and the native FP64 operator, three fixed iterations each.
+    Every element of the iterate is compared with the oracle's PCG; this covers the fused update's
+    load and store offsets over all 32.8 M points."""
+    nx = 10
+    mesh = inputs.box_mesh(32, 32, 32, nx, perturb=0.1, seed=1)
+    f = inputs.random_global_field(mesh, seed=2)
+    its = 3
+    P = DeviceProblem(mesh, DEV)
+    lib = nekax.load()
+    got = {}
+    try:
+        assert lib.nek_set_ax_epb(int(nekax.AX_FF_ENERGY), nx, 1) == nekax.OK
+        for impl in (nekax.AX_FF, nekax.AX_FP64):
+            x = torch.full((mesh.nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+            res = P.cg(_t(f), x, tol=0.0, max_iter=its, ax_impl=impl)
+            assert res["status"] == nekax.OK and res["iters"] == its, res
+            got[impl] = (x.cpu().numpy(), res["relres"])
+            del x
+    finally:
+        lib.nek_set_ax_epb(int(nekax.AX_FF_ENERGY), nx, 0)
+    del P
+    torch.cuda.empty_cache()
+    Pr = ref.Problem(mesh)
+    st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 0.0, its)
+    assert st == ref.OK and itr == its
+    for impl, (xg, relres) in got.items():
+        assert np.all(np.isfinite(xg)), impl
+        err = np.max(np.abs(xg - xr), axis=1)  # element by element
+        worst = int(np.argmax(err))
+        assert np.max(err) <= 1e-9 * np.max(np.abs(xr)), (impl, worst, float(err[worst]))
+        assert abs(relres - rr) <= 1e-8 * rr, (impl, relres, rr)
+        assert np.all(xg[mesh.mask == 0] == 0.0)
+
+
+def test_cg_host_buffers_same_as_device_solve():
+    """nek_cg_solve_host (f and x in host memory, copied by the library) gives the device solve's x bit
+    for bit, with pinned and pageable host buffers, staging allocated inside or passed in."""
+    nx = 10
+    mesh = inputs.box_mesh(3, 2, 3, nx, perturb=0.1, seed=4)
+    P = DeviceProblem(mesh, DEV)
+    f = inputs.random_global_field(mesh, seed=6)
+    xd = torch.empty((mesh.nelt, nx ** 3), dtype=torch.float64, device=DEV)
+    rd = P.cg(_t(f), xd, tol=1e-9, max_iter=500, ax_impl=nekax.AX_FF)
+    staging = torch.empty(nekax.cg_host_staging_bytes(mesh.nelt, nx) // 8 + 32, dtype=torch.float64, device=DEV)
+    for pinned, stg in ((True, None), (False, staging)):
+        fh = torch.from_numpy(f.copy())
+        xh = torch.full_like(fh, float("nan"))
+        if pinned:
+            fh, xh = fh.pin_memory(), xh.pin_memory()
+        rh = P.cg_host(fh, xh, tol=1e-9, max_iter=500, ax_impl=nekax.AX_FF, staging=stg)
+        assert rh["status"] == rd["status"] == nekax.OK and rh["iters"] == rd["iters"]
+        assert torch.equal(xh, xd.cpu())
+    L = nekax.load()
+    A = 0x10000
+    args = [P.gs.handle, mesh.nelt, nx, A, A, A, A, A, A, 0.0, 1, None, None, None, None, None, None]
+    for pos, bad in ((9, -1.0), (7, None), (8, None), (12, A + 16), (1, mesh.nelt + 1)):
+        a = list(args)
+        a[pos] = bad
+        assert L.nek_cg_solve_host(*a) == nekax.ERR_INVALID_ARG, pos
+
+
 # ------------------------------------------------------------------ elements-per-CTA variants
 @pytest.mark.parametrize("impl", [nekax.AX_FP64, nekax.AX_FF])
 @pytest.mark.parametrize("nx", [5, 8, 10])

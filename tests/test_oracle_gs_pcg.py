@@ -164,3 +164,23 @@ def test_element_energies_give_the_cg_inner_product(dims, nx):
               inputs.random_global_field(mesh, seed=5)):  # continuous but not zero on the mask
         e_sum = float(np.sum(v * ref.ax(P.D, P.G, v)))
         assert abs(float(np.sum(P.c * v * P.apply(v))) - e_sum) > 1e-6 * abs(e_sum)
+
+
+def test_openmp_build_is_the_same_oracle():
+    """The -fopenmp build (used only to time the oracle on all host cores) splits
+    independent loops only: AX, dssum and 12 PCG iterations are bit-identical to
+    the default build's."""
+    so = ref.openmp_library()
+    if so is None:
+        pytest.skip("no OpenMP-capable C compiler on this host")
+    mesh = inputs.box_mesh(5, 4, 3, 7, perturb=0.15, seed=11)
+    P = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=12)
+    u = inputs.random_local_field(mesh.nelt, 7, seed=13)
+    base = (ref.ax(P.D, P.G, u), ref.dssum(P.offsets, P.idx, u),
+            ref.pcg(P.D, P.G, P.offsets, P.idx, mesh.mask, P.minv, f, 0.0, 12))
+    with ref.using_library(so):
+        omp = (ref.ax(P.D, P.G, u), ref.dssum(P.offsets, P.idx, u),
+               ref.pcg(P.D, P.G, P.offsets, P.idx, mesh.mask, P.minv, f, 0.0, 12))
+    assert np.array_equal(base[0], omp[0]) and np.array_equal(base[1], omp[1])
+    assert np.array_equal(base[2][1], omp[2][1]) and base[2][3] == omp[2][3]
