@@ -4,16 +4,26 @@
 One step is one ``nek_cg_solve`` call of 100 Jacobi-PCG iterations (tol = 0, a
 fixed iteration count), i.e. 100 passes of the whole solve path: AX, dssum,
 mask, the weighted dot products and the vector updates.  ``value`` is local
-grid points x iterations per second (GDOF/s) over all ranks.  The AX kernel is
-timed inside the same region with CUDA events on the solve's stream; it gives the
-roofline entry and the AX-only GDOF/s and %-of-HBM figures.
+grid points x iterations per second (GDOF/s) over all ranks, with the
+FP64-accurate float-float operator.  The AX kernel is timed inside the same
+region with CUDA events on the solve's stream; it gives the roofline entry.
+``e2e`` times the same steps through ``nek_cg_solve_host`` (f and x in pinned
+host memory, both copies inside the call).
+
+The default run also carries the rest of the metric (rank 0, after the timed
+region): the same solve with the native FP64 operator, the standalone AX sweep
+(nx = 8, 10, 12, 16, both FP64 operators), time to a relative residual of 1e-8
+for native-FP64 and float-float Jacobi-PCG, FP64 defect correction with FP32 /
+BF16 / FP16 inner solves (to 1e-8 and 1e-10), the learned-preconditioner
+comparison, the batched uneven solves, and the oracle's CPU time on one and on
+all host cores.  ``--extras none`` skips all of that.
 
 Inputs are synthetic (seeded deformed-box mesh, f ~ U[-1,1] per global node);
 the geometric factors alone are 1.57 GB, far larger than the 129 MB L2, so no
 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--iters 100] [--nx 10]
-                  [--impl reference] [--sweep] [--solve]
+                  [--impl reference] [--extras native,sweep,solve,mixed,learned,batch,lvec | none]
 """
 from __future__ import annotations
 
@@ -44,29 +54,41 @@ def parse():
     ap.add_argument("--nx", type=int, default=10)
     ap.add_argument("--elems", type=int, default=32, help="elements per box edge")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--sweep", action="store_true", help="also time standalone AX at nx = 8, 10, 12, 16")
-    ap.add_argument("--solve", action="store_true", help="also time one solve to 1e-8 relative residual")
+    ap.add_argument("--extras", default="native,sweep,solve,mixed,learned,batch",
+                    help="comma list of blocks after the timed region (native, sweep, solve, mixed, learned, "
+                         "batch, lvec), 'all' or 'none'")
+    ap.add_argument("--sweep", action="store_true", help="add the standalone AX sweep to --extras")
+    ap.add_argument("--solve", action="store_true", help="add the solves to 1e-8 to --extras")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-threads", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-seconds", type=float, default=None,
                     help="bound on the oracle's CPU time per sample (default: about 10-15 s for cpu_baseline, "
                          "120 s spread over the steps of --impl reference)")
-    ap.add_argument("--mixed", action="store_true",
-                    help="also time FP64 defect correction with FP32/BF16/FP16 inner solves (to 1e-8 and 1e-10)")
-    ap.add_argument("--batch", type=int, default=0,
-                    help="also solve this many uneven problems (nelt log-uniform in [8,4096]) batched")
-    ap.add_argument("--learned", action="store_true",
-                    help="also train the element network and compare flexible CG with it against Jacobi-PCG")
+    ap.add_argument("--mixed", action="store_true", help="add defect correction (FP32/BF16/FP16) to --extras")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="problems of the batched block (nelt log-uniform in [8,4096])")
+    ap.add_argument("--learned", action="store_true", help="add the learned-preconditioner block to --extras")
     ap.add_argument("--learned-meshes", type=int, default=200)
     ap.add_argument("--learned-epochs", type=int, default=30)
-    ap.add_argument("--lvec", action="store_true",
-                    help="also time the unique-node (L-vector) solve against the E-vector solve")
+    ap.add_argument("--lvec", action="store_true", help="add the unique-node (L-vector) block to --extras")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="skip the elements-per-CTA tuning (nek_tune_ax) before timing")
     ap.add_argument("--epb", type=int, default=0,
                     help="fix the AX elements per CTA (1, 2 or 4; nek_set_ax_epb) instead of tuning")
     ap.add_argument("--ax", default="ff", choices=["fp64", "ff"],
                     help="AX operator inside the solve: native FP64 or FP64-accurate float-float")
-    return ap.parse_args()
+    args = ap.parse_args()
+    names = {"native", "sweep", "solve", "mixed", "learned", "batch", "lvec"}
+    ex = args.extras.strip().lower()
+    sel = set(names) if ex == "all" else set() if ex in ("none", "") else {s.strip() for s in ex.split(",")}
+    if sel - names:
+        ap.error("unknown --extras: %s" % ",".join(sorted(sel - names)))
+    for flag in ("sweep", "solve", "mixed", "learned", "lvec"):
+        if getattr(args, flag):
+            sel.add(flag)
+    args.extra_set = sel
+    return args
 
 
 def dist_env():
@@ -160,10 +182,12 @@ def traffic_from_profile(nx, nelt, which="fp64"):
         return None
 
 
-def cpu_baseline(nx, iters_budget_s=15.0):
-    """Time the oracle (as it stands, single-threaded C) on a bounded sample of
-    the same workload: Jacobi-PCG iterations on a 12x12x12-element box of the
-    same family (same nx, perturbation and seed recipe)."""
+def _oracle_pcg_samples(nx, budget_s, samples=1, lib_path=None, max_iters=200):
+    """Time the oracle (as it stands) on a bounded sample of the workload: Jacobi-PCG iterations on a
+    12x12x12-element box of the same family (same nx, perturbation and seed recipe).  Returns the mesh's
+    point count and one (iterations, seconds) pair per sample."""
+    import contextlib
+
     from oracle import ref
     from paper_2011_04981_gb300 import inputs
 
@@ -171,18 +195,63 @@ def cpu_baseline(nx, iters_budget_s=15.0):
     mesh = inputs.box_mesh(e, e, e, nx, perturb=0.1, seed=1)
     P = ref.Problem(mesh)
     f = inputs.random_global_field(mesh, seed=2)
-    t0 = time.perf_counter()
-    ref.pcg(P.D, P.G, P.offsets, P.idx, mesh.mask, P.minv, f, tol=0.0, max_iter=2)
-    t1 = time.perf_counter()
-    per_it = (t1 - t0) / 2
-    iters = max(2, min(200, int(iters_budget_s / max(per_it, 1e-6))))
-    t0 = time.perf_counter()
-    ref.pcg(P.D, P.G, P.offsets, P.idx, mesh.mask, P.minv, f, tol=0.0, max_iter=iters)
-    dt = time.perf_counter() - t0
-    return {"value": mesh.npts * iters / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d Jacobi-PCG iterations on a %dx%dx%d-element deformed box, nx=%d (%d points), "
-                      "single-threaded C oracle, %.1f s" % (iters, e, e, e, nx, mesh.npts, dt),
-            "seconds": dt, "host": host_cpu()}
+    ctx = ref.using_library(lib_path) if lib_path else contextlib.nullcontext()
+    out = []
+    with ctx:
+        t0 = time.perf_counter()
+        ref.pcg(P.D, P.G, P.offsets, P.idx, mesh.mask, P.minv, f, tol=0.0, max_iter=2)
+        per_it = (time.perf_counter() - t0) / 2
+        iters = max(2, min(max_iters, int(budget_s / max(per_it, 1e-6))))
+        for _ in range(samples):
+            t0 = time.perf_counter()
+            ref.pcg(P.D, P.G, P.offsets, P.idx, mesh.mask, P.minv, f, tol=0.0, max_iter=iters)
+            out.append((iters, time.perf_counter() - t0))
+    return mesh.npts, out
+
+
+def cpu_baseline(nx, iters_budget_s=15.0, threads=1, samples=1, warmup=0):
+    """The oracle's rate on `threads` host threads: 1 = the default build in this process; more = its
+    -fopenmp build (same operations, independent loops split over threads) in a child process with
+    OMP_NUM_THREADS set, so that its OpenMP runtime is not the one PyTorch loaded.  `warmup` untimed
+    samples come first; the result's 'per_sample' lists (iterations, seconds) of each timed sample."""
+    if threads <= 1:
+        npts, smp = _oracle_pcg_samples(nx, iters_budget_s, warmup + samples)
+        smp = smp[warmup:]
+        build = "single-threaded C oracle"
+    else:
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads), OMP_PROC_BIND="false")
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-baseline-only", "--cpu-threads", str(threads),
+               "--nx", str(nx), "--cpu-seconds", str(iters_budget_s), "--steps", str(samples), "--warmup",
+               str(warmup)]
+        r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=60 + 4 * iters_budget_s * samples)
+        lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+        if r.returncode != 0 or not lines:
+            return {"unavailable": "OpenMP oracle run failed: %s" % (r.stderr.strip().splitlines() or ["?"])[-1]}
+        d = json.loads(lines[-1])
+        if "unavailable" in d:
+            return d
+        npts, smp = d["npts"], [tuple(s) for s in d["samples"]]
+        build = "C oracle built with -fopenmp, %d threads" % threads
+    its = sum(i for i, _ in smp)
+    secs = sum(s for _, s in smp)
+    return {"value": npts * its / secs / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d x %d Jacobi-PCG iterations on a 12x12x12-element deformed box, nx=%d (%d points), %s, "
+                      "%.1f s" % (len(smp), smp[0][0], nx, npts, build, secs),
+            "seconds": secs, "per_sample": smp, "host": host_cpu()}
+
+
+def cpu_baseline_child(args):
+    """--cpu-baseline-only: run the -fopenmp oracle sample(s) and print one JSON line."""
+    from oracle import ref
+
+    so = ref.openmp_library()
+    if so is None:
+        print(json.dumps({"unavailable": "no OpenMP-capable C compiler on this host"}))
+        return 0
+    npts, smp = _oracle_pcg_samples(args.nx, args.cpu_seconds or 15.0, max(1, args.steps + args.warmup), so,
+                                    max_iters=4000)
+    print(json.dumps({"npts": npts, "samples": smp[args.warmup:], "threads": args.cpu_threads}))
+    return 0
 
 
 def host_cpu():
@@ -214,26 +283,28 @@ def max_over_ranks(dist, values, device):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
+    """The oracle on the host's cores (all of them, through its -fopenmp build; one if that build is not
+    available), each step a bounded sample of the workload."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    cb = None
-    steps_val = []
     budget = args.cpu_seconds if args.cpu_seconds else max(3.0, 120.0 / max(1, args.steps + args.warmup))
-    for s in range(args.warmup + args.steps):
-        r = cpu_baseline(args.nx, iters_budget_s=budget)
-        if s >= args.warmup:
-            steps_val.append(r)
-        cb = r
-    tot_pts_it = sum(r["value"] * r["seconds"] for r in steps_val)
-    tot_s = sum(r["seconds"] for r in steps_val)
-    value = tot_pts_it / tot_s
+    threads = os.cpu_count() or 1
+    cb = cpu_baseline(args.nx, budget, threads=threads, samples=args.steps, warmup=args.warmup) \
+        if threads > 1 else None
+    if cb is None or "unavailable" in cb:
+        threads = 1
+        cb = cpu_baseline(args.nx, budget, threads=1, samples=args.steps, warmup=args.warmup)
+    steps = cb["per_sample"]
+    npts = 12 ** 3 * args.nx ** 3
+    tot_s = sum(s for _, s in steps)
+    value = npts * sum(i for i, _ in steps) / tot_s / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_s / len(steps_val),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_s / len(steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "Jacobi-PCG iterations, deformed box, nx=%d, FP64 (oracle sample)" % args.nx,
                        "elements": 12 ** 3, "nx": args.nx},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"],
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": cb["sample"],
                              "host": cb.get("host")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
@@ -478,6 +549,71 @@ def learned_block(torch, n_meshes=200, epochs=30, eval_elems=24):
             "eval_mesh": "%d^3 elements, nx=8, perturbation 0.15 h, stretch up to 8:1" % eval_elems, **cmp}
 
 
+def native_fp64_block(torch, P, f, x, ws, iters, steps=3, tune=True):
+    """The headline solve with the native FP64 operator (nek_ax on the FP64 pipe): fixed-iteration rate and
+    its AX launches timed inside the solve."""
+    from paper_2011_04981_gb300 import nekax, perfmodel
+
+    nx = P.nx
+    if tune:
+        wt = torch.empty_like(f)
+        nekax.tune_ax(nekax.AX_FP64, P.nelt, nx, P.D, P.G, f, wt)
+        del wt
+    P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, ax_impl=nekax.AX_FP64)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ax_ms, ax_n = 0.0, 0
+    e0.record(s)
+    for _ in range(steps):
+        r = P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, time_ax=True, ax_impl=nekax.AX_FP64)
+        assert r["status"] == nekax.OK and r["iters"] == iters, r
+        ax_ms += r["ax_ms_total"]
+        ax_n += r["ax_launches"]
+    e1.record(s)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    ax_t = ax_ms / max(ax_n, 1) / 1e3
+    hbm, kind = peaks()
+    flops = perfmodel.ax_flops_per_point(nx) * P.npts
+    return {"gdofs": P.npts * iters * steps / t / 1e9, "ms_per_step": 1e3 * t / steps, "steps": steps,
+            "iters_per_step": iters,
+            "ax": {"kernel": "k_ax_fp64<%d>" % nx, "gdofs": P.npts / ax_t / 1e9, "ms_per_launch": ax_t * 1e3,
+                   "tflops": flops / ax_t / 1e12, "fp64_pipe_frac": flops / ax_t / 1e12 / FP64_PEAK_TFLOPS,
+                   "hbm_frac_64B": 64 * P.npts / ax_t / 1e9 / hbm, "share_of_step": ax_ms / 1e3 / t,
+                   "elements_per_cta": nekax.get_ax_epb(nekax.AX_FP64, nx)},
+            "note": "native FP64 (the paper's arithmetic); FP64 peak = 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                    "= %.4f TFLOP/s; HBM %s %.0f GB/s" % (FP64_PEAK_TFLOPS, kind, hbm)}
+
+
+def solves_to_tol(torch, P, f, x, ws, tol=1e-8):
+    """Seconds, iterations and final residual of Jacobi-PCG to a relative residual of tol with each FP64
+    operator (wall clock around the synchronous call)."""
+    from paper_2011_04981_gb300 import nekax
+
+    out = {}
+    for name, impl in (("fp64_native", nekax.AX_FP64), ("fp64_float_float", nekax.AX_FF)):
+        P.cg(f, x, tol=tol, max_iter=5, workspace=ws, ax_impl=impl)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = P.cg(f, x, tol=tol, max_iter=20000, workspace=ws, check_every=20, ax_impl=impl)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"],
+                     "status": nekax.status_string(r["status"])}
+    return out
+
+
+def _guard(name, fn):
+    """Run one block of the extras; a failure is recorded in the line instead of losing the line."""
+    try:
+        return fn()
+    except Exception as exc:  # noqa: BLE001 -- the line must still be printed
+        import traceback
+
+        traceback.print_exc()
+        return {"error": "%s: %s" % (type(exc).__name__, exc)}
+
+
 def run_native(args):
     import torch
 
@@ -504,6 +640,7 @@ def run_native(args):
     x = torch.empty_like(f)
     x_host = torch.empty_like(f_host).pin_memory()
     ws = torch.empty(nekax.cg_workspace_bytes(mesh.nelt, nx, False) // 8 + 64, dtype=torch.float64, device="cuda")
+    staging = torch.empty(nekax.cg_host_staging_bytes(mesh.nelt, nx) // 8 + 64, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     iters = args.iters
 
@@ -543,38 +680,15 @@ def run_native(args):
     t_dev = e0.elapsed_time(e1) / 1e3
     clk = clocks.stop()
 
-    # end to end through the public call: every step copies its f from pinned host memory to the device and
-    # its x back.  The copies run on a second stream, double-buffered, so that step s+1's upload and step s's
-    # download overlap the neighbouring solves (each solve returns synchronised).
-    cs = torch.cuda.Stream()
-    f_dev, x_dev = [f, torch.empty_like(f)], [x, torch.empty_like(x)]
-    x_hosts = [x_host, torch.empty_like(x_host).pin_memory()]
-    ev_in = [torch.cuda.Event(), torch.cuda.Event()]   # upload of f_dev[b] done
-    ev_out = [torch.cuda.Event(), torch.cuda.Event()]  # solve on buffer b done
-    ev_dl = [torch.cuda.Event(), torch.cuda.Event()]   # download of x_dev[b] done
+    # end to end through the public host-buffer call: every step, nek_cg_solve_host copies that step's f
+    # from pinned host memory to the device, solves, and copies x back before it returns.
+    P.cg_host(f_host, x_host, tol=0.0, max_iter=iters, workspace=ws, staging=staging, ax_impl=ax_impl)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    with torch.cuda.stream(cs):
-        f_dev[0].copy_(f_host, non_blocking=True)
-        ev_in[0].record(cs)
-    for step in range(args.steps):
-        cur, nxt = step % 2, (step + 1) % 2
-        stream.wait_event(ev_in[cur])
-        if step >= 2:
-            stream.wait_event(ev_dl[cur])  # step-2's x_dev[cur] has reached the host
-        if step + 1 < args.steps:
-            with torch.cuda.stream(cs):
-                if step >= 1:
-                    cs.wait_event(ev_out[nxt])  # step-1 has finished with f_dev[nxt] and x_dev[nxt]
-                f_dev[nxt].copy_(f_host, non_blocking=True)
-                ev_in[nxt].record(cs)
-        P.cg(f_dev[cur], x_dev[cur], tol=0.0, max_iter=iters, workspace=ws, ax_impl=ax_impl)
-        ev_out[cur].record(stream)
-        with torch.cuda.stream(cs):
-            cs.wait_event(ev_out[cur])
-            x_hosts[cur].copy_(x_dev[cur], non_blocking=True)
-            ev_dl[cur].record(cs)
+    for _ in range(args.steps):
+        r = P.cg_host(f_host, x_host, tol=0.0, max_iter=iters, workspace=ws, staging=staging, ax_impl=ax_impl)
+        assert r["status"] == nekax.OK and r["iters"] == iters, r
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     barrier()
@@ -596,7 +710,8 @@ def run_native(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.ax == "fp64" else "f64 (AX in f32-pair float-float)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.ax == "fp64" else "f64 (AX in f32-pair float-float, FP64-accurate)",
         "data": "synthetic",
         "config": {"workload": "Jacobi-PCG, %d PCG iterations per step (AX+dssum+mask+dots+updates), "
                                "%dx%dx%d deformed box (perturbation 0.1 h), nx=%d, FP64-accurate, AX %s"
@@ -606,7 +721,7 @@ def run_native(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (G alone %.2f GB), no flush" % (pts * 48 / 1e9)},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": pts * 8, "d2h_bytes_per_step": pts * 8,
-                "copies": "pinned host memory, on a second stream overlapping the neighbouring steps' solves"},
+                "api": "nek_cg_solve_host: f and x in pinned host memory, both copies inside the call"},
         "gpu_launches": launches,
         "ax": {"gdofs": ax_gdofs, "ms_per_launch": ax_t * 1e3, "gflops": flops / ax_t / 1e9,
                "bytes_per_point": ax_bpp, "hbm_gbs": ax_bpp * pts / ax_t / 1e9,
@@ -624,31 +739,40 @@ def run_native(args):
                       "note": ("FP64-accurate float-float AX with the fused x / direction update, 104 algorithmic "
                                "B/point (p in and out 16, r 8, minv 8, x in and out 16, G 48, w 8)" if fused_dir else
                                "FP64-accurate float-float AX, 64 algorithmic B/point (u 8 + G 48 + w 8)") +
-                              "; peak = %s HBM copy; its instruction limit is the FP32 pipe (see profiles)"
-                              % hbm_kind}),
+                              "; peak = %s HBM copy (MEASURED_PEAKS hbm_gbs); its instruction limit is the FP32 "
+                              "pipe (see profiles)" % hbm_kind}),
         "clocks": clk,
     }
-    if args.sweep and rank == 0:
-        line["ax_sweep"] = ax_sweep(torch, tune=args.tune)
-    if args.solve and rank == 0:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = P.cg(f, x, tol=1e-8, max_iter=20000, workspace=ws, check_every=20, ax_impl=ax_impl)
-        torch.cuda.synchronize()
-        line["cg_to_1e-8"] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"],
-                              "status": nekax.status_string(r["status"]), "precision": "fp64 jacobi-pcg"}
-    if args.learned and rank == 0:
-        line["learned"] = learned_block(torch, args.learned_meshes, args.learned_epochs)
-    if args.mixed and rank == 0:
-        line["mixed"] = mixed_block(torch, P, f, x)
-    if args.lvec and rank == 0:
-        line["lvec"] = lvec_block(torch, P, iters)
-    if args.batch and rank == 0:
-        del ws
-        line["batch"] = batch_block(torch, args.batch)
+    ex = args.extra_set if rank == 0 else set()
+    if "native" in ex and args.ax == "ff":
+        line["fp64_native"] = _guard("native", lambda: native_fp64_block(torch, P, f, x, ws, iters,
+                                                                         tune=args.tune))
+    if "solve" in ex:
+        line["cg_to_1e-8"] = _guard("solve", lambda: solves_to_tol(torch, P, f, x, ws))
+    if "mixed" in ex:
+        line["mixed"] = _guard("mixed", lambda: mixed_block(torch, P, f, x))
+    if "lvec" in ex:
+        line["lvec"] = _guard("lvec", lambda: lvec_block(torch, P, iters))
+    if "sweep" in ex:
+        line["ax_sweep"] = _guard("sweep", lambda: ax_sweep(torch, tune=args.tune))
+    if "learned" in ex:
+        line["learned"] = _guard("learned", lambda: learned_block(torch, args.learned_meshes, args.learned_epochs))
+    if "batch" in ex and args.batch > 0:
+        del ws, staging
+        torch.cuda.empty_cache()
+        line["batch"] = _guard("batch", lambda: batch_block(torch, args.batch))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline(nx, iters_budget_s=args.cpu_seconds or 15.0)
-        cb.pop("seconds", None)
+        budget = args.cpu_seconds or 12.0
+        single = cpu_baseline(nx, iters_budget_s=budget)
+        threads = os.cpu_count() or 1
+        allc = cpu_baseline(nx, iters_budget_s=budget, threads=threads) if threads > 1 else {"unavailable": "1 core"}
+        if "unavailable" in allc:
+            cb = dict(single)
+        else:
+            cb = dict(allc)
+            cb["single_core"] = {"value": single["value"], "cores": 1, "sample": single["sample"]}
+        for k in ("seconds", "per_sample"):
+            cb.pop(k, None)
         line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -659,6 +783,8 @@ def run_native(args):
 
 def main():
     args = parse()
+    if args.cpu_baseline_only:
+        return cpu_baseline_child(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)
