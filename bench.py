@@ -541,7 +541,7 @@ def learned_block(torch, n_meshes=200, epochs=30, eval_elems=24):
     theta0 = learned.init_params(0, "cuda")
     val0 = learned.validation_loss(theta0, val_data)
     mesh = learned.mesh_family(seed=777, e=eval_elems)
-    cmp = learned.compare_on_mesh(theta, mesh, seed=3)
+    cmp = learned.compare_on_mesh(theta, mesh, seed=3, theta_untrained=theta0)
     cmp["net_apply"] = net_apply_rates(torch, theta, mesh)
     return {"pairs": len(data), "data_seconds": t_data, "train_seconds": t_train, "epochs": epochs,
             "loss": "element energy norm", "train_loss_first_last": [hist[0], hist[-1]],

@@ -252,6 +252,13 @@ nek_status nek_gs_inv_multiplicity(const nek_gs* gs, double* c, void* stream);
  * is not specified, the box boundary is read as Dirichlet).  n points, device. */
 nek_status nek_mask(int64_t n, const uint8_t* mask, double* v, void* stream);
 
+/* Residual of the masked, assembled system (the quantity Section II-B's CG
+ * iteration drives to zero): r = mask.(f - dssum(AX x)), AX through nek_ax_ff
+ * when Gff is given, else nek_ax with G.  f, x, r: device E-vectors, r must not
+ * overlap f or x.  Async. */
+nek_status nek_residual(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G, const float* Gff,
+                        const uint8_t* mask, const double* f, const double* x, double* r, void* stream);
+
 /* ----------------------------------------------------- Jacobi / vectors ---
  * Jacobi preconditioner (Section II-B's basic preconditioner, read as the
  * inverse assembled diagonal): minv = mask ? 1/dssum(diag_e(A)) : 0.
@@ -355,6 +362,13 @@ int nek_net_param_count(void);
 nek_status nek_net_prep(int64_t nelt, int nx, const double* r, const double* minv, float* xin, float* scale,
                         void* stream);
 
+/* Training target of the network for one (x_k, x*) pair of the solver: target[e][p] =
+ * (xs - xk)[e][p] / scale[e] (the error in units of the element's rms(minv r), FP64
+ * arithmetic, one FP32 rounding; 0 where scale[e] is 0).  xs, xk: FP64 E-vectors
+ * (nx = 8); scale: from nek_net_prep; target: nelt*512 floats. */
+nek_status nek_net_target(int64_t nelt, int nx, const double* xs, const double* xk, const float* scale,
+                          float* target, void* stream);
+
 /* z[e][p] = net(xin[e])[p] * scale[e] * c[e][p] (FP64 out; c = 1/multiplicity). */
 nek_status nek_net_apply(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
                          const double* c, double* z, void* stream);
@@ -394,12 +408,21 @@ nek_status nek_adam_step(int n, float* theta, const float* grad, float* m, float
                          float beta2, float eps, int step, void* stream);
 
 /*
- * Flexible CG (Polak-Ribiere beta) preconditioned by the network,
- * M(r) = mask(dssum(nek_net_apply_bf16(r))), falling back to Jacobi (and restarting
- * the direction) when the relative residual has not fallen by stag_factor
- * (0 < stag_factor < 1) in the last stag_window iterations.  theta NULL runs the
- * same loop with Jacobi throughout.  AX is nek_ax_ff when Gff is given, else
- * nek_ax.  nx must be 8.  Synchronous.
+ * Truncated flexible CG, FCG(m) (Notay 2000), preconditioned by the network,
+ * M(r) = mask(dssum(nek_net_apply_bf16(r))): each new direction is z = M(r)
+ * made A-orthogonal to the last m directions, alpha = <p, r>/<p, A p>.  The
+ * network is not a fixed SPD operator, so the short recurrence of CG loses
+ * orthogonality over long solves; the explicit window restores it (m = 1 is
+ * flexible CG with the Polak-Ribiere-type coefficient).  Falls back to Jacobi
+ * (emptying the window) when the relative residual has not fallen by
+ * stag_factor (0 < stag_factor < 1) in the last stag_window iterations.  theta
+ * NULL runs the same loop with Jacobi throughout (for a fixed SPD
+ * preconditioner every m gives the PCG iterates in exact arithmetic).  AX is
+ * nek_ax_ff when Gff is given, else nek_ax.  nx must be 8; 1 <= truncation
+ * <= 16 (else NEK_ERR_INVALID_ARG).  workspace: device, >=
+ * nek_fcg_trunc_workspace_bytes(...) bytes (it holds 2 (m + 1) E-vectors for
+ * the directions and their images), 256-aligned, or NULL to allocate inside the
+ * call.  Synchronous.  nek_fcg_solve is nek_fcg_solve_trunc with m = 1.
  */
 typedef struct {
     int iters;            /* iterations run */
@@ -411,6 +434,11 @@ typedef struct {
 } nek_fcg_info;
 
 size_t nek_fcg_workspace_bytes(int64_t nelt, int nx, int need_minv);
+size_t nek_fcg_trunc_workspace_bytes(int64_t nelt, int nx, int need_minv, int truncation);
+nek_status nek_fcg_solve_trunc(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
+                               const float* Gff, const uint8_t* mask, const double* minv, const float* theta,
+                               const double* f, double* x, double tol_rel, int max_iter, int truncation,
+                               int stag_window, double stag_factor, void* workspace, nek_fcg_info* info, void* stream);
 nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G, const float* Gff,
                          const uint8_t* mask, const double* minv, const float* theta, const double* f, double* x,
                          double tol_rel, int max_iter, int stag_window, double stag_factor, void* workspace,

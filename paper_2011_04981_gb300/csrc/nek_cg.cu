@@ -47,6 +47,14 @@ __global__ void k_diag_local(int64_t nelt, int nx, const double* __restrict__ D,
     }
 }
 
+// r = mask ? f - w : 0
+__global__ void k_residual(int64_t n, const uint8_t* __restrict__ mask, const double* __restrict__ f,
+                           double* __restrict__ r)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+        r[p] = mask[p] ? f[p] - r[p] : 0.0;
+}
+
 __global__ void k_invert_masked(int64_t n, const uint8_t* __restrict__ mask, double* __restrict__ d)
 {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
@@ -82,6 +90,26 @@ nek_status nek_jacobi_minv(const nek_gs* gs, int64_t nelt, int nx, const double*
     if (st != NEK_OK) return st;
     if ((st = launch_dssum(gs, minv, s)) != NEK_OK) return st;
     k_invert_masked<<<stream_blocks(n), 256, 0, s>>>(n, mask, minv);
+    return check_launch();
+}
+
+nek_status nek_residual(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G, const float* Gff,
+                        const uint8_t* mask, const double* f, const double* x, double* r, void* stream)
+{
+    if (nx < kMinNx || nx > kMaxNx) return NEK_ERR_UNSUPPORTED_NX;
+    if (!gs || nelt < 0) return NEK_ERR_INVALID_ARG;
+    const int64_t n = nelt * (int64_t)nx * nx * nx;
+    if (gs->npts != n) return NEK_ERR_INVALID_ARG;
+    if (n == 0) return NEK_OK;
+    if (!D || !mask || !f || !x || !r || (!G && !Gff) || x == r || f == r) return NEK_ERR_INVALID_ARG;
+    if ((Gff && !is_aligned(Gff, 16)) || (!Gff && !is_aligned(G, 16)) || !is_aligned(f, 8) || !is_aligned(x, 8) ||
+        !is_aligned(r, 8))
+        return NEK_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    nek_status st = Gff ? launch_ax_ff(nelt, nx, D, Gff, x, r, s) : launch_ax_fp64(nelt, nx, D, G, x, r, s);
+    if (st == NEK_OK) st = launch_dssum(gs, r, s);
+    if (st != NEK_OK) return st;
+    k_residual<<<stream_blocks(n), 256, 0, s>>>(n, mask, f, r);
     return check_launch();
 }
 

@@ -1,17 +1,20 @@
 // Flexible CG with the learned element preconditioner, falling back to Jacobi.
 //
-// Flexible CG (Notay, 2000) tolerates a preconditioner that is not a fixed SPD
-// matrix by taking the Polak-Ribiere coefficient
-//   beta = <r_new - r_old, z_new> / <r_old, z_old>
-// instead of <r_new, z_new>/<r_old, z_old>.  Iteration (inner products weighted
-// by 1/multiplicity, as in the Jacobi-PCG solve):
-//   w = mask(dssum(AX p)); alpha = <r,z>/<p,w>; x += alpha p; r_old = r;
-//   r -= alpha w; stop if ||r||/||b|| <= tol; z = M(r); beta as above;
-//   p = z + beta p,
-// with M(r) = mask(dssum(net(r) * rms(Jacobi r) / multiplicity)).  If the
-// relative residual has not fallen by `stag_factor` within the last `stag_window`
-// iterations, M becomes Jacobi (z = Minv r) for the rest of the solve and the
-// search direction restarts from z.
+// Truncated flexible CG, FCG(m) (Notay, "Flexible conjugate gradients", SIAM J.
+// Sci. Comput. 22, 2000), tolerates a preconditioner that is not a fixed SPD
+// matrix -- here a nonlinear network -- by making every new direction
+// A-orthogonal to the last m directions explicitly instead of relying on the
+// short recurrence.  Iteration k (inner products weighted by 1/multiplicity, as
+// in the Jacobi-PCG solve):
+//   z = M(r);  p_k = z - sum_{i = k-m}^{k-1} (<z, A p_i> / <p_i, A p_i>) p_i;
+//   w = mask(dssum(AX p_k));  alpha = <p_k, r> / <p_k, w>;  x += alpha p_k;
+//   r -= alpha w;  stop if ||r||/||b|| <= tol,
+// with M(r) = mask(dssum(net(r) * rms(Jacobi r) / multiplicity)).  m = 1 is
+// flexible CG with the Polak-Ribiere-type coefficient; for a fixed SPD M every m
+// gives the PCG iterates in exact arithmetic.  If the relative residual has not
+// fallen by `stag_factor` within the last `stag_window` iterations, M becomes
+// Jacobi (z = Minv r) for the rest of the solve and the direction window is
+// emptied (a restart).
 #include <vector>
 
 #include "nek_internal.h"
@@ -29,55 +32,31 @@ nek_status launch_net_prep(int64_t nelt, const double* r, const double* minv, fl
 namespace {
 
 constexpr int NT = kReduceThreads;
+constexpr int kMaxTrunc = 16;
 
 struct FScal {
-    double rz, pw, alpha, beta, rr, bnorm, relres, num;
+    double alpha, pw, pr, rr, bnorm, relres;
+    double beta[kMaxTrunc];      // coefficients of the window's directions
+    double pwv[kMaxTrunc + 1];   // <p_i, A p_i> per ring slot
 };
 
-// w <- mask.w, partial <p,w>
-__global__ void __launch_bounds__(NT) kf_pw(int64_t n, const double* __restrict__ c, const uint8_t* __restrict__ mask,
-                                            const double* __restrict__ p, double* __restrict__ w,
-                                            double* __restrict__ parts)
+// Ring slots of the directions the new one is orthogonalised against.
+struct Window {
+    int n;
+    int slot[kMaxTrunc];
+};
+
+// x = 0, r = mask.f, partial <r,r>
+__global__ void __launch_bounds__(NT) kf_init(int64_t n, const double* __restrict__ c,
+                                              const uint8_t* __restrict__ mask, const double* __restrict__ f,
+                                              double* __restrict__ x, double* __restrict__ r,
+                                              double* __restrict__ parts)
 {
     __shared__ double sh[NT / 32];
     double acc = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
-        double wq = w[q];
-        if (!mask[q]) {
-            wq = 0.0;
-            w[q] = 0.0;
-        }
-        acc += c[q] * p[q] * wq;
-    }
-    const double t = block_sum<NT>(acc, sh);
-    if (threadIdx.x == 0) parts[blockIdx.x] = t;
-}
-
-__global__ void __launch_bounds__(NT) kf_alpha(const double* __restrict__ parts, int nb, FScal* sc)
-{
-    __shared__ double sh[NT / 32];
-    const double pw = sum_partials<NT>(parts, nb, sh);
-    if (threadIdx.x == 0) {
-        sc->pw = pw;
-        sc->alpha = sc->rz / pw;
-    }
-}
-
-// x += alpha p; r_old = r; r -= alpha w; partial <r,r>
-__global__ void __launch_bounds__(NT) kf_update(int64_t n, const double* __restrict__ c,
-                                                const double* __restrict__ p, const double* __restrict__ w,
-                                                double* __restrict__ x, double* __restrict__ r,
-                                                double* __restrict__ r_old, double* __restrict__ parts,
-                                                const FScal* __restrict__ sc)
-{
-    __shared__ double sh[NT / 32];
-    const double alpha = sc->alpha;
-    double acc = 0.0;
-    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
-        x[q] = fma(alpha, p[q], x[q]);
-        const double ro = r[q];
-        const double rq = fma(-alpha, w[q], ro);
-        r_old[q] = ro;
+        const double rq = mask[q] ? f[q] : 0.0;
+        x[q] = 0.0;
         r[q] = rq;
         acc += c[q] * rq * rq;
     }
@@ -104,22 +83,76 @@ __global__ void kf_jacobi(int64_t n, const double* __restrict__ minv, const doub
         z[q] = minv[q] * r[q];
 }
 
-// z <- mask.z ; partials <r,z>, <r_old,z>
+// z <- mask.z; partials of <z, W_i> for the window's slots (parts[i * nb + block])
 __global__ void __launch_bounds__(NT) kf_zdots(int64_t n, const double* __restrict__ c,
-                                               const uint8_t* __restrict__ mask, const double* __restrict__ r,
-                                               const double* __restrict__ r_old, double* __restrict__ z,
+                                               const uint8_t* __restrict__ mask, double* __restrict__ z,
+                                               const double* __restrict__ Wbase, int64_t stride, Window win,
                                                double* __restrict__ parts)
 {
     __shared__ double sh[NT / 32];
-    double a = 0.0, b = 0.0;
+    double acc[kMaxTrunc];
+#pragma unroll
+    for (int i = 0; i < kMaxTrunc; i++) acc[i] = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
         double zq = z[q];
         if (!mask[q]) {
             zq = 0.0;
             z[q] = 0.0;
         }
-        a += c[q] * r[q] * zq;
-        b += c[q] * r_old[q] * zq;
+        const double cz = c[q] * zq;
+#pragma unroll
+        for (int i = 0; i < kMaxTrunc; i++)
+            if (i < win.n) acc[i] += cz * Wbase[win.slot[i] * stride + q];
+    }
+    for (int i = 0; i < win.n; i++) {
+        const double t = block_sum<NT>(acc[i], sh);
+        if (threadIdx.x == 0) parts[i * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// beta_i = <z, W_i> / <p_i, W_i>
+__global__ void __launch_bounds__(NT) kf_betas(const double* __restrict__ parts, int nb, Window win, FScal* sc)
+{
+    __shared__ double sh[NT / 32];
+    for (int i = 0; i < win.n; i++) {
+        const double d = sum_partials<NT>(parts + i * nb, nb, sh);
+        if (threadIdx.x == 0) sc->beta[i] = d / sc->pwv[win.slot[i]];
+    }
+}
+
+// P_cur = z - sum_i beta_i P_i
+__global__ void kf_p(int64_t n, const double* __restrict__ z, double* __restrict__ Pbase, int64_t stride, int cur,
+                     Window win, const FScal* __restrict__ sc)
+{
+    double beta[kMaxTrunc];
+#pragma unroll
+    for (int i = 0; i < kMaxTrunc; i++) beta[i] = i < win.n ? sc->beta[i] : 0.0;
+    double* pc = Pbase + cur * stride;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        double v = z[q];
+#pragma unroll
+        for (int i = 0; i < kMaxTrunc; i++)
+            if (i < win.n) v = fma(-beta[i], Pbase[win.slot[i] * stride + q], v);
+        pc[q] = v;
+    }
+}
+
+// w <- mask.w; partials <p,w> and <p,r>
+__global__ void __launch_bounds__(NT) kf_pw(int64_t n, const double* __restrict__ c, const uint8_t* __restrict__ mask,
+                                            const double* __restrict__ p, double* __restrict__ w,
+                                            const double* __restrict__ r, double* __restrict__ parts)
+{
+    __shared__ double sh[NT / 32];
+    double a = 0.0, b = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
+        double wq = w[q];
+        if (!mask[q]) {
+            wq = 0.0;
+            w[q] = 0.0;
+        }
+        const double cp = c[q] * p[q];
+        a += cp * wq;
+        b += cp * r[q];
     }
     double t = block_sum<NT>(a, sh);
     if (threadIdx.x == 0) parts[blockIdx.x] = t;
@@ -127,39 +160,32 @@ __global__ void __launch_bounds__(NT) kf_zdots(int64_t n, const double* __restri
     if (threadIdx.x == 0) parts[gridDim.x + blockIdx.x] = t;
 }
 
-// beta = (<r,z> - <r_old,z>) / rz_old (0 on restart); rz = <r,z>
-__global__ void __launch_bounds__(NT) kf_beta(const double* __restrict__ parts, int nb, int restart, FScal* sc)
+__global__ void __launch_bounds__(NT) kf_alpha(const double* __restrict__ parts, int nb, int cur, FScal* sc)
 {
     __shared__ double sh[NT / 32];
-    const double rz = sum_partials<NT>(parts, nb, sh);
-    const double roz = sum_partials<NT>(parts + nb, nb, sh);
+    const double pw = sum_partials<NT>(parts, nb, sh);
+    const double pr = sum_partials<NT>(parts + nb, nb, sh);
     if (threadIdx.x == 0) {
-        sc->num = rz - roz;
-        sc->beta = restart ? 0.0 : (rz - roz) / sc->rz;
-        sc->rz = rz;
+        sc->pw = pw;
+        sc->pr = pr;
+        sc->pwv[cur] = pw;
+        sc->alpha = pr / pw;
     }
 }
 
-__global__ void kf_p(int64_t n, const double* __restrict__ z, double* __restrict__ p, const FScal* __restrict__ sc)
-{
-    const double beta = sc->beta;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
-        p[q] = fma(beta, p[q], z[q]);
-}
-
-// x = 0, r = mask.f, partial <r,r>
-__global__ void __launch_bounds__(NT) kf_init(int64_t n, const double* __restrict__ c,
-                                              const uint8_t* __restrict__ mask, const double* __restrict__ f,
-                                              double* __restrict__ x, double* __restrict__ r,
-                                              double* __restrict__ r_old, double* __restrict__ parts)
+// x += alpha p; r -= alpha w; partial <r,r>
+__global__ void __launch_bounds__(NT) kf_update(int64_t n, const double* __restrict__ c,
+                                                const double* __restrict__ p, const double* __restrict__ w,
+                                                double* __restrict__ x, double* __restrict__ r,
+                                                double* __restrict__ parts, const FScal* __restrict__ sc)
 {
     __shared__ double sh[NT / 32];
+    const double alpha = sc->alpha;
     double acc = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
-        const double rq = mask[q] ? f[q] : 0.0;
-        x[q] = 0.0;
+        x[q] = fma(alpha, p[q], x[q]);
+        const double rq = fma(-alpha, w[q], r[q]);
         r[q] = rq;
-        r_old[q] = 0.0;
         acc += c[q] * rq * rq;
     }
     const double t = block_sum<NT>(acc, sh);
@@ -169,13 +195,14 @@ __global__ void __launch_bounds__(NT) kf_init(int64_t n, const double* __restric
 inline size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct FLayout {
-    double *r, *r_old, *z, *p, *w, *minv, *parts;
+    double *r, *z, *P, *W, *minv, *parts;
+    int64_t stride;  // doubles between ring slots
     float *xin, *scale;
     FScal* sc;
     size_t bytes;
 };
 
-FLayout f_layout(char* base, int64_t nelt, int nx, bool need_minv)
+FLayout f_layout(char* base, int64_t nelt, int nx, bool need_minv, int m)
 {
     FLayout L{};
     const int64_t n = nelt * (int64_t)nx * nx * nx;
@@ -186,15 +213,15 @@ FLayout f_layout(char* base, int64_t nelt, int nx, bool need_minv)
         return q;
     };
     const size_t v = sizeof(double) * std::max<int64_t>(n, 1);
+    L.stride = static_cast<int64_t>(al256(v) / sizeof(double));
     L.r = reinterpret_cast<double*>(take(v));
-    L.r_old = reinterpret_cast<double*>(take(v));
     L.z = reinterpret_cast<double*>(take(v));
-    L.p = reinterpret_cast<double*>(take(v));
-    L.w = reinterpret_cast<double*>(take(v));
+    L.P = reinterpret_cast<double*>(take(al256(v) * (m + 1)));
+    L.W = reinterpret_cast<double*>(take(al256(v) * (m + 1)));
     L.minv = need_minv ? reinterpret_cast<double*>(take(v)) : nullptr;
     L.xin = reinterpret_cast<float*>(take(sizeof(float) * 2 * std::max<int64_t>(n, 1)));
     L.scale = reinterpret_cast<float*>(take(sizeof(float) * std::max<int64_t>(nelt, 1)));
-    L.parts = reinterpret_cast<double*>(take(sizeof(double) * 2 * kMaxReduceBlocks));
+    L.parts = reinterpret_cast<double*>(take(sizeof(double) * kMaxTrunc * kMaxReduceBlocks));
     L.sc = reinterpret_cast<FScal*>(take(sizeof(FScal)));
     L.bytes = off;
     return L;
@@ -208,21 +235,26 @@ using namespace nek;
 
 extern "C" {
 
-size_t nek_fcg_workspace_bytes(int64_t nelt, int nx, int need_minv)
+size_t nek_fcg_trunc_workspace_bytes(int64_t nelt, int nx, int need_minv, int truncation)
 {
-    if (nelt < 0 || nx < kMinNx || nx > kMaxNx) return 0;
-    return f_layout(nullptr, nelt, nx, need_minv != 0).bytes;
+    if (nelt < 0 || nx < kMinNx || nx > kMaxNx || truncation < 1 || truncation > kMaxTrunc) return 0;
+    return f_layout(nullptr, nelt, nx, need_minv != 0, truncation).bytes;
 }
 
-nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G, const float* Gff,
-                         const uint8_t* mask, const double* minv, const float* theta, const double* f, double* x,
-                         double tol_rel, int max_iter, int stag_window, double stag_factor, void* workspace,
-                         nek_fcg_info* info, void* stream)
+size_t nek_fcg_workspace_bytes(int64_t nelt, int nx, int need_minv)
+{
+    return nek_fcg_trunc_workspace_bytes(nelt, nx, need_minv, 1);
+}
+
+nek_status nek_fcg_solve_trunc(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,
+                               const float* Gff, const uint8_t* mask, const double* minv, const float* theta,
+                               const double* f, double* x, double tol_rel, int max_iter, int truncation,
+                               int stag_window, double stag_factor, void* workspace, nek_fcg_info* info, void* stream)
 {
     if (info) *info = nek_fcg_info{};
     if (nx != 8) return NEK_ERR_UNSUPPORTED_NX;  // the network is built for 8^3 element blocks
     if (!gs || nelt < 0 || max_iter < 0 || !(tol_rel > 0.0) || stag_window < 1 || !(stag_factor > 0.0) ||
-        !(stag_factor < 1.0))
+        !(stag_factor < 1.0) || truncation < 1 || truncation > kMaxTrunc)
         return NEK_ERR_INVALID_ARG;
     const int64_t n = nelt * (int64_t)nx * nx * nx;
     if (gs->npts != n) return NEK_ERR_INVALID_ARG;
@@ -230,11 +262,12 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
     if (!D || !G || !mask || !f || !x || !is_aligned(G, 16) || !is_aligned(x, 8) || (Gff && !is_aligned(Gff, 16)) ||
         (minv && !is_aligned(minv, 8)) || (workspace && !is_aligned(workspace, 256)))
         return NEK_ERR_INVALID_ARG;
+    const int m = truncation;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t bytes = nek_fcg_workspace_bytes(nelt, nx, minv == nullptr);
+    const size_t bytes = nek_fcg_trunc_workspace_bytes(nelt, nx, minv == nullptr, m);
     void* ws = workspace;
     if (!ws && check_cuda(cudaMallocAsync(&ws, bytes, s)) != NEK_OK) return NEK_ERR_NOMEM;
-    FLayout L = f_layout(static_cast<char*>(ws), nelt, nx, minv == nullptr);
+    FLayout L = f_layout(static_cast<char*>(ws), nelt, nx, minv == nullptr, m);
     const double* mv = minv;
     const int nb = reduce_blocks(n);
     const int sb = pcg::stream_blocks(n);
@@ -243,12 +276,15 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
     std::vector<double> hist;
     bool net = theta != nullptr;
     int it = 0, fell_back = 0, net_apps = 0, launches = 0;
+    // ring of the last m directions: slot of direction k is k mod (m + 1); `have`
+    // directions are in the window (0 after a restart)
+    int have = 0;
     // one event pair per network application, read once at the end (no host
     // synchronisation inside the loop for the timing)
     std::vector<cudaEvent_t> nev;
     double net_ms = 0.0;
 
-    auto precondition = [&](int restart) -> nek_status {
+    auto precondition = [&]() -> nek_status {
         if (net) {
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             const bool timed = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
@@ -271,9 +307,6 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
             kf_jacobi<<<sb, 256, 0, s>>>(n, mv, L.r, L.z);
             launches += 1;
         }
-        kf_zdots<<<nb, NT, 0, s>>>(n, gs->d_c, mask, L.r, L.r_old, L.z, L.parts);
-        kf_beta<<<1, NT, 0, s>>>(L.parts, nb, restart, L.sc);
-        launches += 2;
         return check_launch();
     };
 
@@ -282,7 +315,7 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
         mv = L.minv;
         launches += 3;
     }
-    kf_init<<<nb, NT, 0, s>>>(n, gs->d_c, mask, f, x, L.r, L.r_old, L.parts);
+    kf_init<<<nb, NT, 0, s>>>(n, gs->d_c, mask, f, x, L.r, L.parts);
     kf_rr<<<1, NT, 0, s>>>(L.parts, nb, 1, L.sc);
     launches += 2;
     if ((st = check_launch()) != NEK_OK) goto done;
@@ -294,15 +327,29 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
     }
     if (h.bnorm == 0.0) goto done;
     hist.push_back(1.0);
-    if ((st = precondition(1)) != NEK_OK) goto done;
-    cudaMemcpyAsync(L.p, L.z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
     for (it = 1; it <= max_iter; it++) {
-        st = Gff ? launch_ax_ff(nelt, nx, D, Gff, L.p, L.w, s) : launch_ax_fp64(nelt, nx, D, G, L.p, L.w, s);
+        // the new direction: z = M(r), made A-orthogonal to the window
+        if ((st = precondition()) != NEK_OK) goto done;
+        const int cur = it % (m + 1);
+        Window win{};
+        win.n = have;
+        for (int i = 0; i < have; i++) win.slot[i] = ((it - 1 - i) % (m + 1) + (m + 1)) % (m + 1);
+        kf_zdots<<<nb, NT, 0, s>>>(n, gs->d_c, mask, L.z, L.W, L.stride, win, L.parts);
+        launches += 1;
+        if (have > 0) {
+            kf_betas<<<1, NT, 0, s>>>(L.parts, nb, win, L.sc);
+            launches += 1;
+        }
+        kf_p<<<sb, 256, 0, s>>>(n, L.z, L.P, L.stride, cur, win, L.sc);
+        launches += 1;
+        double* p = L.P + cur * L.stride;
+        double* w = L.W + cur * L.stride;
+        st = Gff ? launch_ax_ff(nelt, nx, D, Gff, p, w, s) : launch_ax_fp64(nelt, nx, D, G, p, w, s);
         if (st != NEK_OK) goto done;
-        if ((st = pcg::dssum<double>(gs, L.w, s)) != NEK_OK) goto done;
-        kf_pw<<<nb, NT, 0, s>>>(n, gs->d_c, mask, L.p, L.w, L.parts);
-        kf_alpha<<<1, NT, 0, s>>>(L.parts, nb, L.sc);
-        kf_update<<<nb, NT, 0, s>>>(n, gs->d_c, L.p, L.w, x, L.r, L.r_old, L.parts, L.sc);
+        if ((st = pcg::dssum<double>(gs, w, s)) != NEK_OK) goto done;
+        kf_pw<<<nb, NT, 0, s>>>(n, gs->d_c, mask, p, w, L.r, L.parts);
+        kf_alpha<<<1, NT, 0, s>>>(L.parts, nb, cur, L.sc);
+        kf_update<<<nb, NT, 0, s>>>(n, gs->d_c, p, w, x, L.r, L.parts, L.sc);
         kf_rr<<<1, NT, 0, s>>>(L.parts, nb, 0, L.sc);
         launches += 6;
         if ((st = check_launch()) != NEK_OK) goto done;
@@ -314,15 +361,12 @@ nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D
         }
         hist.push_back(h.relres);
         if (h.relres <= tol_rel) break;
-        int restart = 0;
+        have = have < m ? have + 1 : m;
         if (net && it >= stag_window && h.relres > stag_factor * hist[it - stag_window]) {
             net = false;
             fell_back = it;
-            restart = 1;
+            have = 0;  // restart: the Jacobi directions start a new window
         }
-        if ((st = precondition(restart)) != NEK_OK) goto done;
-        kf_p<<<sb, 256, 0, s>>>(n, L.z, L.p, L.sc);
-        launches += 1;
     }
     if (it > max_iter) {
         it = max_iter;
@@ -350,6 +394,15 @@ done:
         if (st == NEK_OK) st = st2;
     }
     return st;
+}
+
+nek_status nek_fcg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G, const float* Gff,
+                         const uint8_t* mask, const double* minv, const float* theta, const double* f, double* x,
+                         double tol_rel, int max_iter, int stag_window, double stag_factor, void* workspace,
+                         nek_fcg_info* info, void* stream)
+{
+    return nek_fcg_solve_trunc(gs, nelt, nx, D, G, Gff, mask, minv, theta, f, x, tol_rel, max_iter, 1, stag_window,
+                               stag_factor, workspace, info, stream);
 }
 
 }  // extern "C"

@@ -536,6 +536,17 @@ nek_status launch_net_apply(int64_t nelt, const float* theta, const float* xin, 
     return check_launch();
 }
 
+// target[e][p] = (xs - xk)[e][p] / scale[e] (FP64 difference and quotient, one FP32 rounding); 0 where
+// the element's scale is 0.
+__global__ void k_net_target(int64_t n, const double* __restrict__ xs, const double* __restrict__ xk,
+                             const float* __restrict__ scale, float* __restrict__ target)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const double s = (double)scale[q / NP];
+        target[q] = s > 0.0 ? (float)((xs[q] - xk[q]) / s) : 0.f;
+    }
+}
+
 nek_status launch_net_prep(int64_t nelt, const double* r, const double* minv, float* xin, float* scale,
                            cudaStream_t s)
 {
@@ -592,6 +603,18 @@ nek_status nek_net_prep(int64_t nelt, int nx, const double* r, const double* min
     if (nelt == 0) return NEK_OK;
     if (!r || !minv || !xin || !scale) return NEK_ERR_INVALID_ARG;
     return launch_net_prep(nelt, r, minv, xin, scale, static_cast<cudaStream_t>(stream));
+}
+
+nek_status nek_net_target(int64_t nelt, int nx, const double* xs, const double* xk, const float* scale,
+                          float* target, void* stream)
+{
+    if (nx != NXN) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt < 0) return NEK_ERR_INVALID_ARG;
+    if (nelt == 0) return NEK_OK;
+    if (!xs || !xk || !scale || !target) return NEK_ERR_INVALID_ARG;
+    const int64_t n = nelt * NP;
+    k_net_target<<<pcg::stream_blocks(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, xs, xk, scale, target);
+    return check_launch();
 }
 
 nek_status nek_net_apply(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,

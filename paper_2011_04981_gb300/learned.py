@@ -34,11 +34,8 @@ def mesh_family(seed, e=8):
 
 
 def _residual(P, f, x, w):
-    """w = mask(f - dssum(AX x)) on the device."""
-    P.ax_ff(x, w)
-    P.gs.dssum(w)
-    w.neg_().add_(f)
-    nekax.mask(P.npts, P.mask, w)
+    """w = mask(f - dssum(AX x)) on the device (nek_residual with the float-float operator)."""
+    nekax.residual(P.gs, P.nelt, P.nx, P.D, P.G, P.prepare_ff(), P.mask, f, x, w)
 
 
 class TrainingSet:
@@ -75,17 +72,19 @@ def make_training_data(n_meshes=200, pairs_per_mesh=100, snapshots=5, e=8, seed=
         r = torch.empty_like(f)
         xin = torch.empty((mesh.nelt, 2, 512), dtype=torch.float32, device=device)
         sc = torch.empty(mesh.nelt, dtype=torch.float32, device=device)
+        tgt = torch.empty((mesh.nelt, 512), dtype=torch.float32, device=device)
         per = max(1, pairs_per_mesh // len(ks))
         for k in ks:
             P.cg(f, xk, tol=0.0, max_iter=int(k), ax_impl=nekax.AX_FF)
             _residual(P, f, xk, r)
             nekax.net_prep(mesh.nelt, NX, r, P.minv, xin, sc)
-            err = xs - xk  # nek_net_apply weights each element's output by 1/multiplicity
+            # (xs - xk) / scale; nek_net_apply weights each element's output by 1/multiplicity
+            nekax.net_target(mesh.nelt, NX, xs, xk, sc, tgt)
             good = torch.nonzero(sc > 0).flatten()
             sel = good[torch.from_numpy(rng.choice(good.numel(), size=min(per, good.numel()), replace=False)).to(
                 device)]
             X.append(xin[sel].clone())
-            T.append((err[sel] / sc[sel, None].double()).float())
+            T.append(tgt[sel].clone())
             GL.append(Glp[sel].clone())
             GS.append(gsc[sel].clone())
         del P
@@ -166,8 +165,13 @@ def validation_loss(theta, data, batch=256, kind="energy"):
     return tot / max(cnt, 1)
 
 
-def compare_on_mesh(theta, mesh, seed=0, tol=1e-8, device="cuda", stag_window=100, stag_factor=0.5):
-    """Time and iterations to tol: Jacobi-PCG versus flexible CG with the network."""
+TRUNCATION = 8  # FCG(m) window: the directions each new one is made A-orthogonal to
+
+
+def compare_on_mesh(theta, mesh, seed=0, tol=1e-8, device="cuda", stag_window=200, stag_factor=0.8,
+                    truncation=TRUNCATION, theta_untrained=None):
+    """Time and iterations to tol: Jacobi-PCG versus truncated flexible CG with the network (and, when
+    theta_untrained is given, with that network too)."""
     import torch
 
     P = DeviceProblem(mesh, device)
@@ -177,18 +181,22 @@ def compare_on_mesh(theta, mesh, seed=0, tol=1e-8, device="cuda", stag_window=10
     out = {}
     # warm-up of both paths
     P.cg(f, x, tol=tol, max_iter=5, ax_impl=nekax.AX_FF)
-    nekax.fcg_solve(P.gs, mesh.nelt, NX, P.D, P.G, Gff, P.mask, P.minv, theta, f, x, tol=tol, max_iter=5)
+    nekax.fcg_solve(P.gs, mesh.nelt, NX, P.D, P.G, Gff, P.mask, P.minv, theta, f, x, tol=tol, max_iter=5,
+                    truncation=truncation)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     r = P.cg(f, x, tol=tol, max_iter=100000, ax_impl=nekax.AX_FF, check_every=10)
     torch.cuda.synchronize()
     out["jacobi_pcg"] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"]}
-    t0 = time.perf_counter()
-    r = nekax.fcg_solve(P.gs, mesh.nelt, NX, P.D, P.G, Gff, P.mask, P.minv, theta, f, x, tol=tol, max_iter=100000,
-                        stag_window=stag_window, stag_factor=stag_factor)
-    torch.cuda.synchronize()
-    out["learned_fcg"] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"],
-                          "fell_back_at": r["fell_back_at"], "net_ms": r["net_ms"],
-                          "net_applications": r["net_applications"],
-                          "status": nekax.status_string(r["status"])}
+    runs = [("learned_fcg", theta)] + ([("untrained_fcg", theta_untrained)] if theta_untrained is not None else [])
+    for name, th in runs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = nekax.fcg_solve(P.gs, mesh.nelt, NX, P.D, P.G, Gff, P.mask, P.minv, th, f, x, tol=tol, max_iter=100000,
+                            stag_window=stag_window, stag_factor=stag_factor, truncation=truncation)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": time.perf_counter() - t0, "iters": r["iters"], "relres": r["relres"],
+                     "fell_back_at": r["fell_back_at"], "net_ms": r["net_ms"],
+                     "net_applications": r["net_applications"], "truncation": truncation,
+                     "status": nekax.status_string(r["status"])}
     return out

@@ -96,6 +96,7 @@ _SIGS = {
     "nek_jacobi_minv": ([_P, _I64, _I, _P, _P, _P, _P, _P], _I),
     "nek_dot_c": ([_P, _P, _P, _P, _P], _I),
     "nek_dot_c_noalloc": ([_I64, _P, _P, _P, _P, _P], _I),
+    "nek_residual": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "nek_cg_workspace_bytes": ([_I64, _I, _I], ctypes.c_size_t),
     "nek_batch_create": ([_I, _P, _P, _P, ctypes.POINTER(_P)], _I),
     "nek_batch_destroy": ([_P], _I),
@@ -107,6 +108,7 @@ _SIGS = {
                             _P], _I),
     "nek_net_param_count": ([], _I),
     "nek_net_prep": ([_I64, _I, _P, _P, _P, _P, _P], _I),
+    "nek_net_target": ([_I64, _I, _P, _P, _P, _P, _P], _I),
     "nek_net_apply": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_apply_bf16": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_train_workspace_bytes": ([_I], ctypes.c_size_t),
@@ -118,6 +120,9 @@ _SIGS = {
     "nek_fcg_workspace_bytes": ([_I64, _I, _I], ctypes.c_size_t),
     "nek_fcg_solve": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _P, _D, _I, _I, _D, _P, ctypes.POINTER(NekFcgInfo),
                        _P], _I),
+    "nek_fcg_trunc_workspace_bytes": ([_I64, _I, _I, _I], ctypes.c_size_t),
+    "nek_fcg_solve_trunc": ([_P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _P, _D, _I, _I, _I, _D, _P,
+                             ctypes.POINTER(NekFcgInfo), _P], _I),
     "nek_tune_ax": ([_I, _I64, _I, _P, _P, _P, _P, _P, _P, _P], _I),
     "nek_set_ax_epb": ([_I, _I, _I], _I),
     "nek_get_ax_epb": ([_I, _I], _I),
@@ -413,6 +418,11 @@ def net_prep(nelt, nx, r, minv, xin, scale, stream=None):
                                                _stream(stream)))
 
 
+def net_target(nelt, nx, xs, xk, scale, target, stream=None):
+    _check("nek_net_target", load().nek_net_target(nelt, nx, _ptr(xs), _ptr(xk), _ptr(scale), _ptr(target),
+                                                   _stream(stream)))
+
+
 def net_apply(nelt, nx, theta, xin, scale, c, z, stream=None):
     _check("nek_net_apply", load().nek_net_apply(nelt, nx, _ptr(theta), _ptr(xin), _ptr(scale), _ptr(c), _ptr(z),
                                                  _stream(stream)))
@@ -449,15 +459,23 @@ def adam_step(n, theta, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, 
 
 
 def fcg_solve(gs, nelt, nx, D, G, Gff, m, minv, theta, f, x, tol=1e-8, max_iter=5000, stag_window=100,
-              stag_factor=0.5, workspace=None, stream=None):
+              stag_factor=0.5, workspace=None, stream=None, truncation=1):
+    """Truncated flexible CG, FCG(truncation) (nek_fcg_solve_trunc); truncation = 1 is nek_fcg_solve."""
     info = NekFcgInfo()
-    st = load().nek_fcg_solve(gs.handle, nelt, nx, _ptr(D), _ptr(G), _ptr(Gff), _ptr(m), _ptr(minv), _ptr(theta),
-                              _ptr(f), _ptr(x), float(tol), int(max_iter), int(stag_window), float(stag_factor),
-                              _ptr(workspace), ctypes.byref(info), _stream(stream))
+    st = load().nek_fcg_solve_trunc(gs.handle, nelt, nx, _ptr(D), _ptr(G), _ptr(Gff), _ptr(m), _ptr(minv),
+                                    _ptr(theta), _ptr(f), _ptr(x), float(tol), int(max_iter), int(truncation),
+                                    int(stag_window), float(stag_factor), _ptr(workspace), ctypes.byref(info),
+                                    _stream(stream))
     if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
-        raise NekError("nek_fcg_solve", st)
+        raise NekError("nek_fcg_solve_trunc", st)
     return dict(status=st, iters=info.iters, relres=info.relres, fell_back_at=info.fell_back_at,
                 net_applications=info.net_applications, net_ms=info.net_ms, kernel_launches=info.kernel_launches)
+
+
+def residual(gs: GsPlan, nelt, nx, D, G, Gff, m, f, x, r, stream=None):
+    """r = mask.(f - dssum(AX x)) (nek_residual)."""
+    _check("nek_residual", load().nek_residual(gs.handle, nelt, nx, _ptr(D), _ptr(G), _ptr(Gff), _ptr(m), _ptr(f),
+                                               _ptr(x), _ptr(r), _stream(stream)))
 
 
 def cg_workspace_bytes(nelt, nx, need_minv=True) -> int:
