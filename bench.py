@@ -70,6 +70,8 @@ def parse():
                     help="problems of the batched block (nelt log-uniform in [8,4096])")
     ap.add_argument("--learned", action="store_true", help="add the learned-preconditioner block to --extras")
     ap.add_argument("--learned-meshes", type=int, default=200)
+    ap.add_argument("--net-elems", type=int, default=13824,
+                    help="elements of the --extras net block (network inference rates, random weights)")
     ap.add_argument("--learned-epochs", type=int, default=30)
     ap.add_argument("--lvec", action="store_true", help="add the unique-node (L-vector) block to --extras")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
@@ -79,7 +81,7 @@ def parse():
     ap.add_argument("--ax", default="ff", choices=["fp64", "ff"],
                     help="AX operator inside the solve: native FP64 or FP64-accurate float-float")
     args = ap.parse_args()
-    names = {"native", "sweep", "solve", "mixed", "learned", "batch", "lvec"}
+    names = {"native", "sweep", "solve", "mixed", "learned", "batch", "lvec", "net"}
     ex = args.extras.strip().lower()
     sel = set(names) if ex == "all" else set() if ex in ("none", "") else {s.strip() for s in ex.split(",")}
     if sel - names:
@@ -482,8 +484,9 @@ def batch_block(torch, nprob, tol=1e-8):
 
 
 def net_apply_rates(torch, theta, mesh, reps=20):
-    """One network application over every element of `mesh`: FP32 CUDA-core form against the BF16
-    tensor-core form (mma.sync), in points/s and useful TFLOP/s (16 416 flop per point)."""
+    """One network application over every element of `mesh`: the FP32 CUDA-core form and the two BF16
+    tensor-core forms (warp-level mma.sync, tcgen05), in points/s and useful TFLOP/s (16 416 flop per
+    point)."""
     import numpy as np
 
     from paper_2011_04981_gb300 import nekax
@@ -497,7 +500,8 @@ def net_apply_rates(torch, theta, mesh, reps=20):
     flop_pt = 2 * (2 * 16 * 27 + 16 * 16 * 27 + 16 * 27)
     _, bf16_peak = peaks_bf16()
     out = {"elements": n, "flop_per_point": flop_pt}
-    for name, fn in (("fp32_cuda_cores", nekax.net_apply), ("bf16_tensor_cores", nekax.net_apply_bf16)):
+    for name, fn in (("fp32_cuda_cores", nekax.net_apply), ("bf16_mma_sync", nekax.net_apply_bf16_mma),
+                     ("bf16_tcgen05", nekax.net_apply_bf16)):
         fn(n, 8, theta, xin, sc, c, z)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -509,9 +513,28 @@ def net_apply_rates(torch, theta, mesh, reps=20):
         t = e0.elapsed_time(e1) / reps / 1e3
         tf = n * 512 * flop_pt / t / 1e12
         out[name] = {"ms": t * 1e3, "gpts": n * 512 / t / 1e9, "tflops": tf}
-    out["bf16_tensor_cores"]["frac_of_bf16_peak"] = out["bf16_tensor_cores"]["tflops"] / bf16_peak
-    out["speedup"] = out["fp32_cuda_cores"]["ms"] / out["bf16_tensor_cores"]["ms"]
+    for name in ("bf16_mma_sync", "bf16_tcgen05"):
+        out[name]["frac_of_bf16_peak"] = out[name]["tflops"] / bf16_peak
+    out["speedup_tcgen05_vs_mma_sync"] = out["bf16_mma_sync"]["ms"] / out["bf16_tcgen05"]["ms"]
     return out
+
+
+def net_block(torch, nelt):
+    """Inference rates of the three network forms on nelt elements with random weights and inputs (the
+    network's cost does not depend on the values)."""
+    import numpy as np
+
+    from paper_2011_04981_gb300 import nekax
+
+    th = torch.from_numpy(np.random.default_rng(1).normal(scale=0.1, size=nekax.net_param_count())
+                          .astype(np.float32)).to("cuda")
+
+    class _M:
+        pass
+
+    m = _M()
+    m.nelt = nelt
+    return net_apply_rates(torch, th, m)
 
 
 def peaks_bf16():
@@ -757,6 +780,8 @@ def run_native(args):
         line["ax_sweep"] = _guard("sweep", lambda: ax_sweep(torch, tune=args.tune))
     if "learned" in ex:
         line["learned"] = _guard("learned", lambda: learned_block(torch, args.learned_meshes, args.learned_epochs))
+    if "net" in ex:
+        line["net_apply"] = _guard("net", lambda: net_block(torch, args.net_elems))
     if "batch" in ex and args.batch > 0:
         del ws, staging
         torch.cuda.empty_cache()

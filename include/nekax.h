@@ -373,12 +373,22 @@ nek_status nek_net_target(int64_t nelt, int nx, const double* xs, const double* 
 nek_status nek_net_apply(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
                          const double* c, double* z, void* stream);
 
-/* Same as nek_net_apply on the tensor cores: the network input and the two
- * hidden activations are rounded to BF16 (nearest even) before each
- * convolution, products are exact and sums FP32 (mma.sync m16n8k16, BF16 x
- * BF16 -> FP32).  Same arguments and errors.  nek_fcg_solve uses this form. */
+/* Same as nek_net_apply on the 5th-generation tensor cores (tcgen05): each
+ * 3x3x3 convolution is an implicit GEMM of 128 x 16 x 16 MMAs per tap with the
+ * activations and weights in shared memory and the FP32 accumulators in tensor
+ * memory.  The network input and the two hidden activations are rounded to BF16
+ * (nearest even) before each convolution, products are exact and sums FP32.
+ * Same arguments and errors; xin 4-byte, c and z 8-byte aligned.  A bounded wait
+ * inside the kernel that runs out (about 2 s) writes NaN into its element's z and
+ * sets a flag that nek_fcg_solve_trunc reports as NEK_ERR_TIMEOUT.
+ * nek_fcg_solve(_trunc) uses this form. */
 nek_status nek_net_apply_bf16(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
                               const double* c, double* z, void* stream);
+
+/* The same network and rounding on the warp-level tensor-core MMA (mma.sync
+ * m16n8k16, BF16 x BF16 -> FP32), kept for comparison with the tcgen05 form. */
+nek_status nek_net_apply_bf16_mma(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
+                                  const double* c, double* z, void* stream);
 
 /* Training on a batch of `batch` samples (xin [batch][2][512], target
  * [batch][512]): loss = mean_b |y_b - t_b|^2/|t_b|^2 (device float, nullable)

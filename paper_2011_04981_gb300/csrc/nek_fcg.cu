@@ -22,8 +22,9 @@
 
 namespace nek {
 
-nek_status launch_net_apply_tc(int64_t nelt, const float* theta, const float* xin, const float* scale,
-                               const double* c, double* z, cudaStream_t s);
+nek_status launch_net_apply_tc5(int64_t nelt, const float* theta, const float* xin, const float* scale,
+                                const double* c, double* z, cudaStream_t s);
+nek_status net_tc5_take_timeout(bool* timed_out);
 nek_status launch_net_apply(int64_t nelt, const float* theta, const float* xin, const float* scale, const double* c,
                             double* z, cudaStream_t s);
 nek_status launch_net_prep(int64_t nelt, const double* r, const double* minv, float* xin, float* scale,
@@ -297,7 +298,7 @@ nek_status nek_fcg_solve_trunc(const nek_gs* gs, int64_t nelt, int nx, const dou
             }
             if (timed) cudaEventRecord(e0, s);
             nek_status sp = launch_net_prep(nelt, L.r, mv, L.xin, L.scale, s);
-            if (sp == NEK_OK) sp = launch_net_apply_tc(nelt, theta, L.xin, L.scale, gs->d_c, L.z, s);
+            if (sp == NEK_OK) sp = launch_net_apply_tc5(nelt, theta, L.xin, L.scale, gs->d_c, L.z, s);
             if (sp == NEK_OK) sp = pcg::dssum<double>(gs, L.z, s);
             if (timed) cudaEventRecord(e1, s);
             if (sp != NEK_OK) return sp;
@@ -380,6 +381,11 @@ done:
         }
     }
     for (auto& e : nev) cudaEventDestroy(e);
+    if (net_apps > 0) {  // a bounded wait inside the network kernel that ran out
+        bool to = false;
+        if (cudaStreamSynchronize(s) == cudaSuccess && net_tc5_take_timeout(&to) == NEK_OK && to)
+            st = NEK_ERR_TIMEOUT;
+    }
     if (info) {
         info->iters = it;
         info->relres = h.relres;

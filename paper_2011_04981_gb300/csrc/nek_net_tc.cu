@@ -1,4 +1,6 @@
-// Learned-preconditioner inference on the tensor cores (BF16 in, FP32 accumulate).
+// Learned-preconditioner inference on the warp-level tensor-core MMA (mma.sync;
+// BF16 in, FP32 accumulate): nek_net_apply_bf16_mma, kept beside the tcgen05
+// form of nek_net_apply_bf16 (nek_net_tc5.cu) for comparison.
 //
 // Each 3x3x3 convolution of the per-element network is an implicit GEMM:
 // rows = the 512 points of the element, K = 16 input channels per tap (the two
@@ -238,8 +240,8 @@ using namespace nek;
 
 extern "C" {
 
-nek_status nek_net_apply_bf16(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
-                              const double* c, double* z, void* stream)
+nek_status nek_net_apply_bf16_mma(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
+                                  const double* c, double* z, void* stream)
 {
     if (nx != NXN) return NEK_ERR_UNSUPPORTED_NX;
     if (nelt < 0) return NEK_ERR_INVALID_ARG;

@@ -111,6 +111,7 @@ _SIGS = {
     "nek_net_target": ([_I64, _I, _P, _P, _P, _P, _P], _I),
     "nek_net_apply": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_apply_bf16": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
+    "nek_net_apply_bf16_mma": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_train_workspace_bytes": ([_I], ctypes.c_size_t),
     "nek_net_forward_batch": ([_I, _P, _P, _P, _P, _P], _I),
     "nek_net_train_grad": ([_I, _P, _P, _P, _P, _P, _P, _P], _I),
@@ -431,6 +432,11 @@ def net_apply(nelt, nx, theta, xin, scale, c, z, stream=None):
 def net_apply_bf16(nelt, nx, theta, xin, scale, c, z, stream=None):
     _check("nek_net_apply_bf16", load().nek_net_apply_bf16(nelt, nx, _ptr(theta), _ptr(xin), _ptr(scale), _ptr(c),
                                                            _ptr(z), _stream(stream)))
+
+
+def net_apply_bf16_mma(nelt, nx, theta, xin, scale, c, z, stream=None):
+    _check("nek_net_apply_bf16_mma", load().nek_net_apply_bf16_mma(nelt, nx, _ptr(theta), _ptr(xin), _ptr(scale),
+                                                                   _ptr(c), _ptr(z), _stream(stream)))
 
 
 def net_train_workspace_bytes(batch):

@@ -154,6 +154,8 @@ def test_apply_bf16_tensor_cores_match_oracle():
     thd = torch.from_numpy(th.astype(np.float32)).to(DEV)
     z = torch.full_like(rd, float("nan"))
     nekax.net_apply_bf16(mesh.nelt, 8, thd, xin, sc, c, z)
+    zm = torch.full_like(rd, float("nan"))
+    nekax.net_apply_bf16_mma(mesh.nelt, 8, thd, xin, sc, c, zm)
     z32 = torch.empty_like(rd)
     nekax.net_apply(mesh.nelt, 8, thd, xin, sc, c, z32)
     torch.cuda.synchronize()
@@ -165,7 +167,9 @@ def test_apply_bf16_tensor_cores_match_oracle():
     assert np.all(np.isfinite(zz))
     assert _rel(zz, yb) <= 5e-4  # against the same rounding points: FP32-sum level (norm-wise, extra)
     # element by element against the unrounded network, with the BF16 roundings in the bound
-    for label, got, u_act, u in (("apply_bf16 (tensor cores)", zz, U_BF16, U_TC),
+    assert _rel(zm.cpu().numpy(), yb) <= 5e-4
+    for label, got, u_act, u in (("apply_bf16 (tcgen05)", zz, U_BF16, U_TC),
+                                 ("apply_bf16_mma (mma.sync)", zm.cpu().numpy(), U_BF16, U_TC),
                                  ("apply (FP32)", z32.cpu().numpy(), 0.0, 2.0 ** -24)):
         y, _, worst = onet.forward_bound(th, xh, u_act=u_act, u=u, mode="worst")
         _, _, rms = onet.forward_bound(th, xh, u_act=u_act, u=u, mode="rms")
@@ -173,6 +177,35 @@ def test_apply_bf16_tensor_cores_match_oracle():
         extra = 3 * 2.0 ** -24 * np.abs(yf * s)
         _check_elementwise(label, got, yf * s, worst[5][:, 0].reshape(n, 512) * np.abs(s) + extra,
                            np.sqrt((rms[5][:, 0].reshape(n, 512) * s) ** 2 + extra ** 2))
+
+
+def test_apply_bf16_many_elements_every_element_checked():
+    """More elements than the tcgen05 kernel's persistent grid (3 CTAs per SM), so every CTA runs several
+    elements through the same shared-memory grid and tensor memory; every output of every element against
+    the oracle's bound, and the two tensor-core forms against each other."""
+    n = 1000
+    rng = np.random.default_rng(31)
+    th = _theta(32)
+    thd = torch.from_numpy(th.astype(np.float32)).to(DEV)
+    x = rng.normal(size=(n, 2, 512)).astype(np.float32)
+    sc = rng.uniform(0.5, 2.0, size=n).astype(np.float32)
+    cc = np.where(rng.uniform(size=(n, 512)) < 0.3, 0.5, 1.0)
+    xd, scd, cd = (torch.from_numpy(a).to(DEV) for a in (x, sc, cc))
+    z = torch.full((n, 512), float("nan"), dtype=torch.float64, device=DEV)
+    zm = torch.full_like(z, float("nan"))
+    nekax.net_apply_bf16(n, 8, thd, xd, scd, cd, z)
+    nekax.net_apply_bf16_mma(n, 8, thd, xd, scd, cd, zm)
+    torch.cuda.synchronize()
+    s = sc.astype(np.float64)[:, None] * cc
+    xh = x.astype(np.float64).reshape(n, 2, 8, 8, 8)
+    y, _, worst = onet.forward_bound(th, xh, u_act=U_BF16, u=U_TC, mode="worst")
+    _, _, rms = onet.forward_bound(th, xh, u_act=U_BF16, u=U_TC, mode="rms")
+    yf = y[:, 0].reshape(n, 512)
+    extra = 3 * 2.0 ** -24 * np.abs(yf * s)
+    w = worst[5][:, 0].reshape(n, 512) * np.abs(s) + extra
+    r = np.sqrt((rms[5][:, 0].reshape(n, 512) * s) ** 2 + extra ** 2)
+    _check_elementwise("apply_bf16 (tcgen05), 1000 elements", z.cpu().numpy(), yf * s, w, r)
+    _check_elementwise("apply_bf16_mma, 1000 elements", zm.cpu().numpy(), yf * s, w, r)
 
 
 def test_adam_matches_oracle():
