@@ -335,7 +335,10 @@ nek_status nek_batch_jacobi_minv(const nek_batch* b, const double* G, const uint
  * (the batch's G split by nek_geom_ff) is given, else nek_ax.  After one eager
  * iteration, iters_per_graph (> 0) iterations are captured into a CUDA graph
  * and replayed until every problem has stopped or max_iter is reached (0 = no
- * graph).  iters_host, relres_host, status_host: HOST arrays of nprob entries,
+ * graph; < 0 = the rest of the solve as ONE graph launch: the iteration is the
+ * body of a conditional WHILE node whose condition a kernel at the end of the
+ * body sets on the device from the count of unfinished problems and the
+ * iteration budget, so the host waits once, for the end of the solve).  iters_host, relres_host, status_host: HOST arrays of nprob entries,
  * nullable.  Returns NEK_OK if all problems converged (or tol_rel == 0),
  * NEK_ERR_NOT_CONVERGED / NEK_ERR_BREAKDOWN if any did not.  Synchronous.
  */

@@ -17,7 +17,11 @@
 // iteration count are exactly those of a solve on its own.  One iteration for
 // all problems is about ten kernels; `iters_per_graph` iterations are captured
 // once into a CUDA graph and replayed, with a device counter of unfinished
-// problems read back after each replay.
+// problems read back after each replay.  With iters_per_graph < 0 the whole
+// solve is one graph launch: the iteration is the body of a conditional WHILE
+// node, and a one-thread kernel at the end of the body sets the loop condition
+// from the device's count of unfinished problems and an iteration counter, so
+// the host neither waits nor launches anything until the solve has finished.
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -236,6 +240,19 @@ __global__ void kb_beta(int nprob, const int* __restrict__ pch, const double* __
     }
 }
 
+// Loop control of the one-launch solve (end of the WHILE body): counts the
+// iteration and keeps looping while problems are unfinished and the iteration
+// budget lasts.
+__global__ void kb_loop_ctl(cudaGraphConditionalHandle h, const int* __restrict__ active, int* __restrict__ iters,
+                            int budget)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int n = *iters + 1;
+        *iters = n;
+        cudaGraphSetConditional(h, (*active > 0 && n < budget) ? 1u : 0u);
+    }
+}
+
 // per-problem convergence test, kept separate from kb_beta so the tolerance is
 // a kernel argument of the captured graph; pdone[p] = 1 once p has finished
 // (the operator then skips p's elements)
@@ -371,7 +388,7 @@ BLayout b_layout(char* base, const nek_batch* b, bool need_minv)
     L.parts = reinterpret_cast<double*>(take(sizeof(double) * 2 * (size_t)b->nchunks));
     L.edot = reinterpret_cast<double*>(take(sizeof(double) * std::max<int64_t>(b->nelt_total, 1)));
     L.sc = reinterpret_cast<BScal*>(take(sizeof(BScal) * (size_t)b->nprob));
-    L.active = reinterpret_cast<int*>(take(sizeof(int) * 4));
+    L.active = reinterpret_cast<int*>(take(sizeof(int) * 4));  // [0] unfinished problems, [1] loop iterations
     L.pdone = reinterpret_cast<uint8_t*>(take(static_cast<size_t>(b->nprob)));
     L.flags = reinterpret_cast<uint8_t*>(take(static_cast<size_t>(b->npts)));
     L.bytes = off;
@@ -593,6 +610,7 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
     int it_done = 0, launches = 0, graph_launches = 0;
     int active = 0;
     const int per_graph = iters_per_graph > 0 ? iters_per_graph : 0;
+    bool device_loop = false;  // the one-launch solve ran (or there was nothing left to run)
 
     // Per group, the elements before ax_first[g] belong to finished problems only,
     // and the operator is launched from there on.  With the problems of a group
@@ -695,9 +713,62 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
         it_done = 1;
         launches += iter_launches;
     }
-    if (per_graph > 0 && it_done < max_iter)
+    if (iters_per_graph < 0 && it_done < max_iter) {
+        device_loop = true;
+        // the remaining iterations in one graph launch (device-side WHILE loop)
+        if ((st = check_cuda(cudaMemcpyAsync(&active, L.active, sizeof(int), cudaMemcpyDeviceToHost, s))) != NEK_OK)
+            goto done;
+        if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
+        if (active > 0) {
+            int body_launches = 0;
+            if ((st = check_cuda(cudaMemsetAsync(L.active + 1, 0, sizeof(int), s))) != NEK_OK) goto done;
+            if ((st = check_cuda(cudaGraphCreate(&graph, 0))) != NEK_OK) goto done;
+            cudaGraphConditionalHandle cond;
+            if ((st = check_cuda(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault))) !=
+                NEK_OK)
+                goto done;
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = cond;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            if ((st = check_cuda(cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp))) != NEK_OK) goto done;
+            {
+                cudaStream_t cs = nullptr;
+                st = check_cuda(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+                if (st == NEK_OK)
+                    st = check_cuda(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr,
+                                                                  0, cudaStreamCaptureModeThreadLocal));
+                if (st == NEK_OK) {
+                    st = one_iteration(cs);
+                    body_launches = iter_launches + 1;
+                    if (st == NEK_OK) {
+                        kb_loop_ctl<<<1, 32, 0, cs>>>(cond, L.active, L.active + 1, max_iter - it_done);
+                        st = check_launch();
+                    }
+                    cudaGraph_t body = nullptr;
+                    cudaError_t ce = cudaStreamEndCapture(cs, &body);
+                    if (st == NEK_OK) st = check_cuda(ce);
+                }
+                if (cs) cudaStreamDestroy(cs);
+            }
+            if (st != NEK_OK) goto done;
+            if ((st = check_cuda(cudaGraphInstantiate(&gexec, graph, 0))) != NEK_OK) goto done;
+            if ((st = check_cuda(cudaGraphLaunch(gexec, s))) != NEK_OK) goto done;
+            int loops = 0;
+            if ((st = check_cuda(cudaMemcpyAsync(&loops, L.active + 1, sizeof(int), cudaMemcpyDeviceToHost, s))) !=
+                NEK_OK)
+                goto done;
+            if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
+            it_done += loops;
+            launches += loops * body_launches;
+            graph_launches = 1;
+        }
+    }
+    if (!device_loop && per_graph > 0 && it_done < max_iter)
         if ((st = capture()) != NEK_OK) goto done;
-    while (it_done < max_iter) {
+    while (!device_loop && it_done < max_iter) {
         if ((st = check_cuda(cudaMemcpyAsync(&active, L.active, sizeof(int), cudaMemcpyDeviceToHost, s))) != NEK_OK)
             goto done;
         if ((st = check_cuda(cudaMemcpyAsync(hdone.data(), L.pdone, static_cast<size_t>(np),

@@ -660,6 +660,15 @@ def test_batch_graph_replay_is_bit_identical_to_eager():
     assert r1["graph_launches"] == 0 and r2["graph_launches"] > 0
     assert np.array_equal(r1["iters"], r2["iters"])
     assert torch.equal(x1, x2)
+    # the whole solve as one graph launch (device-side WHILE loop): the same iterates and counts
+    x3 = torch.full_like(x1, float("nan"))
+    r3 = B.solve(x3, tol=1e-9, max_iter=3000, iters_per_graph=-1)
+    assert r3["graph_launches"] == 1 and r3["iterations_run"] == r1["iterations_run"], (r3, r1)
+    assert np.array_equal(r1["iters"], r3["iters"])
+    assert torch.equal(x1, x3)
+    # an iteration budget that ends the device loop before convergence
+    r4 = B.solve(x3, tol=1e-9, max_iter=12, iters_per_graph=-1)
+    assert r4["status"] == nekax.ERR_NOT_CONVERGED and r4["iterations_run"] == 12
     zero_pos = B.order.index(2)
     assert r1["iters"][zero_pos] == 0
     assert float(B.split(x1)[2].abs().max()) == 0.0
