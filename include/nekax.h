@@ -388,6 +388,18 @@ nek_status nek_net_apply(int64_t nelt, int nx, const float* theta, const float* 
 nek_status nek_net_apply_bf16(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,
                               const double* c, double* z, void* stream);
 
+/* Self-test of the bounded waits of nek_net_apply_bf16's kernel: runs it on two
+ * elements (zero weights and inputs, so z = 0) with every mbarrier wait bounded
+ * by wait_us microseconds (1 .. 2e6).  force_timeout != 0 makes the mbarrier
+ * expect one arrival more than the kernel's MMAs ever give, so every wait runs
+ * out: the kernel must then set its flag, write NaN into its element's output,
+ * free its tensor memory and return.  *timed_out receives whether the flag was
+ * set.  Returns NEK_ERR_TIMEOUT when it was (and the output was poisoned),
+ * NEK_OK when the kernel finished normally, NEK_ERR_CUDA if the flag and the
+ * output disagree.  No paper counterpart: failure detection of the library.
+ * Allocates and synchronises the device; for tests. */
+nek_status nek_net_tc_selftest(int force_timeout, int64_t wait_us, int* timed_out);
+
 /* The same network and rounding on the warp-level tensor-core MMA (mma.sync
  * m16n8k16, BF16 x BF16 -> FP32), kept for comparison with the tcgen05 form. */
 nek_status nek_net_apply_bf16_mma(int64_t nelt, int nx, const float* theta, const float* xin, const float* scale,

@@ -42,6 +42,7 @@ namespace nek {
 namespace {
 
 constexpr int NP = 512, CIN = 2, CH = 16;
+constexpr int NPARAM_TC5 = CH * CIN * 27 + CH + CH * CH * 27 + CH + CH * 27 + 1;
 constexpr int OW1 = 0, OB1 = OW1 + CH * CIN * 27, OW2 = OB1 + CH, OB2 = OW2 + CH * CH * 27, OW3 = OB2 + CH,
               OB3 = OW3 + CH * 27;
 constexpr int NT5 = 128;            // 4 warps: one per 32-lane TMEM sub-partition
@@ -50,7 +51,7 @@ constexpr int kHalfBytes = kLines * 10 * 16;  // one K half of the activation gr
 constexpr int kTapBytes = 512;      // B operand of one tap: 16 rows (n) x 16 channels (k), two K halves
 constexpr int kTiles = 5;           // 80 padded output lines / 16
 constexpr uint32_t kTmemCols = 128; // 5 tiles x 16 columns, rounded up to a power of two
-constexpr long long kWaitNs = 2000000000LL;
+constexpr long long kWaitNs = 2000000000LL;  // default bound of every mbarrier wait
 
 // 32-bit instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
 // A and B BF16 (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0),
@@ -111,7 +112,7 @@ __device__ __forceinline__ long long global_ns()
 // within kWaitNs.  Each try may suspend the thread (up to the hint, 20 us) until
 // the phase completes, so waiting threads do not take issue slots from the
 // other CTAs on the SM; the clock is read every 64 tries.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long wait_ns)
 {
     const long long t0 = global_ns();
     for (int tries = 1;; tries++) {
@@ -124,7 +125,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
             : "r"(mbar), "r"(parity), "r"(20000)
             : "memory");
         if (done) return true;
-        if ((tries & 63) == 0 && global_ns() - t0 > kWaitNs) return false;
+        if ((tries & 63) == 0 && global_ns() - t0 > wait_ns) return false;
     }
 }
 
@@ -150,10 +151,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 // Byte offset of grid row (i', j', k') in one K half.
 __device__ __forceinline__ int grid_row(int ip, int jp, int kp) { return 16 * (10 * (10 * kp + jp + 1) + ip); }
 
+// arrivals: arrivals the mbarrier expects per phase (1: the commit of the MMAs;
+// the self-test passes 2, which no phase ever gets, so every wait runs out).
 __global__ void __launch_bounds__(NT5, 3) k_net_apply_tc5(int64_t nelt, const float* __restrict__ theta,
                                                          const float* __restrict__ xin,
                                                          const float* __restrict__ scale,
-                                                         const double* __restrict__ c, double* __restrict__ z)
+                                                         const double* __restrict__ c, double* __restrict__ z,
+                                                         long long wait_ns, int arrivals)
 {
     extern __shared__ __align__(128) unsigned char raw5[];
     Tc5Smem& S = *reinterpret_cast<Tc5Smem*>(raw5);
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(NT5, 3) k_net_apply_tc5(int64_t nelt, const fl
     }
     if (tid == 0) {
         S.b3[0] = __bfloat162float(__float2bfloat16_rn(theta[OB3]));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&S.mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&S.mbar)), "r"(arrivals) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(NT5, 3) k_net_apply_tc5(int64_t nelt, const fl
                 }
                 __syncwarp();
             }
-            bool ok = mbar_wait_bounded(mbar, parity);
+            bool ok = mbar_wait_bounded(mbar, parity, wait_ns);
             if (__syncthreads_or(!ok)) {
                 // a wait ran out: flag it, poison the element's output, wait once more for the MMAs in
                 // flight, then leave the element loop (TMEM is freed below)
@@ -248,7 +252,7 @@ __global__ void __launch_bounds__(NT5, 3) k_net_apply_tc5(int64_t nelt, const fl
                     atomicExch(&g_net_tc5_timeout, 1);
                     z[e * NP] = __longlong_as_double(0x7FF8000000000000LL);
                 }
-                mbar_wait_bounded(mbar, parity);
+                mbar_wait_bounded(mbar, parity, wait_ns);
                 break;
             }
             parity ^= 1u;
@@ -305,16 +309,22 @@ int sm_count()
 
 }  // namespace
 
-nek_status launch_net_apply_tc5(int64_t nelt, const float* theta, const float* xin, const float* scale,
-                                const double* c, double* z, cudaStream_t s)
+nek_status launch_net_apply_tc5_ex(int64_t nelt, const float* theta, const float* xin, const float* scale,
+                                   const double* c, double* z, cudaStream_t s, long long wait_ns, int arrivals)
 {
     static std::atomic<uint64_t> configured{0};
     nek_status st = ensure_dyn_smem(k_net_apply_tc5, sizeof(Tc5Smem), configured);
     if (st != NEK_OK) return st;
     const int64_t cap = 3 * (int64_t)sm_count();
     const int grid = static_cast<int>(nelt < cap ? nelt : cap);
-    k_net_apply_tc5<<<grid, NT5, sizeof(Tc5Smem), s>>>(nelt, theta, xin, scale, c, z);
+    k_net_apply_tc5<<<grid, NT5, sizeof(Tc5Smem), s>>>(nelt, theta, xin, scale, c, z, wait_ns, arrivals);
     return check_launch();
+}
+
+nek_status launch_net_apply_tc5(int64_t nelt, const float* theta, const float* xin, const float* scale,
+                                const double* c, double* z, cudaStream_t s)
+{
+    return launch_net_apply_tc5_ex(nelt, theta, xin, scale, c, z, s, kWaitNs, 1);
 }
 
 // Reads and clears the flag that a bounded wait of the kernel ran out (synchronous).
@@ -342,6 +352,41 @@ nek_status nek_net_apply_bf16(int64_t nelt, int nx, const float* theta, const fl
     if (!theta || !xin || !scale || !c || !z || !is_aligned(xin, 4) || !is_aligned(z, 8) || !is_aligned(c, 8))
         return NEK_ERR_INVALID_ARG;
     return launch_net_apply_tc5(nelt, theta, xin, scale, c, z, static_cast<cudaStream_t>(stream));
+}
+
+nek_status nek_net_tc_selftest(int force_timeout, int64_t wait_us, int* timed_out)
+{
+    if (!timed_out || wait_us < 1 || wait_us > 2000000) return NEK_ERR_INVALID_ARG;
+    *timed_out = 0;
+    bool stale = false;
+    nek_status st = net_tc5_take_timeout(&stale);  // clear a flag left by an earlier call
+    if (st != NEK_OK) return st;
+    // two elements with zero weights and inputs: z = 0 unless the wait ran out (then z[0] is NaN)
+    const int64_t ne = 2;
+    float* buf = nullptr;
+    double* dbuf = nullptr;
+    const size_t nf = NPARAM_TC5 + ne * CIN * NP + ne;
+    if ((st = check_cuda(cudaMalloc(&buf, sizeof(float) * nf))) != NEK_OK) return NEK_ERR_NOMEM;
+    if ((st = check_cuda(cudaMalloc(&dbuf, sizeof(double) * 2 * ne * NP))) != NEK_OK) {
+        cudaFree(buf);
+        return NEK_ERR_NOMEM;
+    }
+    st = check_cuda(cudaMemset(buf, 0, sizeof(float) * nf));
+    if (st == NEK_OK) st = check_cuda(cudaMemset(dbuf, 0, sizeof(double) * 2 * ne * NP));
+    if (st == NEK_OK)
+        st = launch_net_apply_tc5_ex(ne, buf, buf + NPARAM_TC5, buf + NPARAM_TC5 + ne * CIN * NP, dbuf,
+                                     dbuf + ne * NP, nullptr, wait_us * 1000LL, force_timeout ? 2 : 1);
+    if (st == NEK_OK) st = check_cuda(cudaDeviceSynchronize());
+    bool to = false;
+    if (st == NEK_OK) st = net_tc5_take_timeout(&to);
+    double z0 = 0.0;
+    if (st == NEK_OK) st = check_cuda(cudaMemcpy(&z0, dbuf + ne * NP, sizeof(double), cudaMemcpyDeviceToHost));
+    cudaFree(buf);
+    cudaFree(dbuf);
+    if (st != NEK_OK) return st;
+    *timed_out = to ? 1 : 0;
+    if (to != (z0 != z0)) return NEK_ERR_CUDA;  // the flag and the poisoned output must agree
+    return to ? NEK_ERR_TIMEOUT : NEK_OK;
 }
 
 }  // extern "C"

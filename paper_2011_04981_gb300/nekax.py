@@ -112,6 +112,7 @@ _SIGS = {
     "nek_net_apply": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_apply_bf16": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_apply_bf16_mma": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
+    "nek_net_tc_selftest": ([_I, _I64, ctypes.POINTER(_I)], _I),
     "nek_net_train_workspace_bytes": ([_I], ctypes.c_size_t),
     "nek_net_forward_batch": ([_I, _P, _P, _P, _P, _P], _I),
     "nek_net_train_grad": ([_I, _P, _P, _P, _P, _P, _P, _P], _I),
