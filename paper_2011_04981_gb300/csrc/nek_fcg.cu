@@ -84,28 +84,38 @@ __global__ void kf_jacobi(int64_t n, const double* __restrict__ minv, const doub
         z[q] = minv[q] * r[q];
 }
 
-// z <- mask.z; partials of <z, W_i> for the window's slots (parts[i * nb + block])
+// z <- mask.z; partials of <z, W_i> for the window's M slots (parts[i * nb + block]).
+// M is a template parameter so that the M loads of a point are independent
+// registers and all in flight together.
+template <int M>
 __global__ void __launch_bounds__(NT) kf_zdots(int64_t n, const double* __restrict__ c,
                                                const uint8_t* __restrict__ mask, double* __restrict__ z,
                                                const double* __restrict__ Wbase, int64_t stride, Window win,
                                                double* __restrict__ parts)
 {
     __shared__ double sh[NT / 32];
-    double acc[kMaxTrunc];
+    const double* W[M > 0 ? M : 1];
 #pragma unroll
-    for (int i = 0; i < kMaxTrunc; i++) acc[i] = 0.0;
+    for (int i = 0; i < M; i++) W[i] = Wbase + win.slot[i] * stride;
+    double acc[M > 0 ? M : 1];
+#pragma unroll
+    for (int i = 0; i < M; i++) acc[i] = 0.0;
     for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += (int64_t)gridDim.x * NT) {
         double zq = z[q];
+        const double cq = c[q];
+        double wv[M > 0 ? M : 1];
+#pragma unroll
+        for (int i = 0; i < M; i++) wv[i] = W[i][q];
         if (!mask[q]) {
             zq = 0.0;
             z[q] = 0.0;
         }
-        const double cz = c[q] * zq;
+        const double cz = cq * zq;
 #pragma unroll
-        for (int i = 0; i < kMaxTrunc; i++)
-            if (i < win.n) acc[i] += cz * Wbase[win.slot[i] * stride + q];
+        for (int i = 0; i < M; i++) acc[i] += cz * wv[i];
     }
-    for (int i = 0; i < win.n; i++) {
+#pragma unroll
+    for (int i = 0; i < M; i++) {
         const double t = block_sum<NT>(acc[i], sh);
         if (threadIdx.x == 0) parts[i * gridDim.x + blockIdx.x] = t;
     }
@@ -121,21 +131,45 @@ __global__ void __launch_bounds__(NT) kf_betas(const double* __restrict__ parts,
     }
 }
 
-// P_cur = z - sum_i beta_i P_i
+// P_cur = z - sum_i beta_i P_i (the window's M directions)
+template <int M>
 __global__ void kf_p(int64_t n, const double* __restrict__ z, double* __restrict__ Pbase, int64_t stride, int cur,
                      Window win, const FScal* __restrict__ sc)
 {
-    double beta[kMaxTrunc];
+    double beta[M > 0 ? M : 1];
+    const double* P[M > 0 ? M : 1];
 #pragma unroll
-    for (int i = 0; i < kMaxTrunc; i++) beta[i] = i < win.n ? sc->beta[i] : 0.0;
+    for (int i = 0; i < M; i++) {
+        beta[i] = sc->beta[i];
+        P[i] = Pbase + win.slot[i] * stride;
+    }
     double* pc = Pbase + cur * stride;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        double pv[M > 0 ? M : 1];
+#pragma unroll
+        for (int i = 0; i < M; i++) pv[i] = P[i][q];
         double v = z[q];
 #pragma unroll
-        for (int i = 0; i < kMaxTrunc; i++)
-            if (i < win.n) v = fma(-beta[i], Pbase[win.slot[i] * stride + q], v);
+        for (int i = 0; i < M; i++) v = fma(-beta[i], pv[i], v);
         pc[q] = v;
     }
+}
+
+// The window-length dispatch of kf_zdots and kf_p (0 <= win.n <= kMaxTrunc).
+template <int M>
+nek_status window_kernels(int64_t n, int nb, int sb, const double* c, const uint8_t* mask, double* z,
+                          double* P, double* W, int64_t stride, int cur, const Window& win, double* parts,
+                          FScal* sc, cudaStream_t s, int* launches)
+{
+    if constexpr (M < kMaxTrunc) {
+        if (win.n != M)
+            return window_kernels<M + 1>(n, nb, sb, c, mask, z, P, W, stride, cur, win, parts, sc, s, launches);
+    }
+    kf_zdots<M><<<nb, NT, 0, s>>>(n, c, mask, z, W, stride, win, parts);
+    if (M > 0) kf_betas<<<1, NT, 0, s>>>(parts, nb, win, sc);
+    kf_p<M><<<sb, 256, 0, s>>>(n, z, P, stride, cur, win, sc);
+    *launches += M > 0 ? 3 : 2;
+    return check_launch();
 }
 
 // w <- mask.w; partials <p,w> and <p,r>
@@ -335,14 +369,9 @@ nek_status nek_fcg_solve_trunc(const nek_gs* gs, int64_t nelt, int nx, const dou
         Window win{};
         win.n = have;
         for (int i = 0; i < have; i++) win.slot[i] = ((it - 1 - i) % (m + 1) + (m + 1)) % (m + 1);
-        kf_zdots<<<nb, NT, 0, s>>>(n, gs->d_c, mask, L.z, L.W, L.stride, win, L.parts);
-        launches += 1;
-        if (have > 0) {
-            kf_betas<<<1, NT, 0, s>>>(L.parts, nb, win, L.sc);
-            launches += 1;
-        }
-        kf_p<<<sb, 256, 0, s>>>(n, L.z, L.P, L.stride, cur, win, L.sc);
-        launches += 1;
+        if ((st = window_kernels<0>(n, nb, sb, gs->d_c, mask, L.z, L.P, L.W, L.stride, cur, win, L.parts, L.sc, s,
+                                     &launches)) != NEK_OK)
+            goto done;
         double* p = L.P + cur * L.stride;
         double* w = L.W + cur * L.stride;
         st = Gff ? launch_ax_ff(nelt, nx, D, Gff, p, w, s) : launch_ax_fp64(nelt, nx, D, G, p, w, s);

@@ -99,47 +99,52 @@ __device__ __forceinline__ void conv_2pts(const float* xin, const float* sW, con
 
 // ------------------------------------------------------------------ prep
 // xin[e][0][p] = r/rms(r), xin[e][1][p] = (minv r)/rms(minv r); scale[e] = rms(minv r).
-__global__ void __launch_bounds__(NP) k_net_prep(int64_t nelt, const double* __restrict__ r,
-                                                 const double* __restrict__ minv, float* __restrict__ xin,
-                                                 float* __restrict__ scale)
+// One warp per element: lane l holds points l + 32 q (q = 0..15, coalesced), sums
+// its FP64 squares, the warp sums the lanes with a fixed shuffle tree, and lane 0
+// forms the two RMS values and their reciprocals (FP64 square root and division
+// on one lane); no block-wide barrier, so the warps of a CTA work on different
+// elements independently.
+constexpr int kPrepWarps = 8;
+
+__global__ void __launch_bounds__(32 * kPrepWarps) k_net_prep(int64_t nelt, const double* __restrict__ r,
+                                                               const double* __restrict__ minv,
+                                                               float* __restrict__ xin, float* __restrict__ scale)
 {
-    __shared__ double sh[2][NP / 32];
-    __shared__ double sinv[2];
-    const int p = threadIdx.x, lane = p & 31;
-    for (int64_t e = blockIdx.x; e < nelt; e += gridDim.x) {
-        const double rv = r[e * NP + p];
-        const double jv = minv[e * NP + p] * rv;
-        double a = rv * rv, b = jv * jv;
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = (int64_t)blockIdx.x * kPrepWarps + (threadIdx.x >> 5); e < nelt;
+         e += (int64_t)gridDim.x * kPrepWarps) {
+        double rv[NP / 32], jv[NP / 32];
+#pragma unroll
+        for (int q = 0; q < NP / 32; q++) {
+            const int64_t o = e * NP + lane + 32 * q;
+            rv[q] = r[o];
+            jv[q] = minv[o] * rv[q];
+        }
+        double a = 0.0, b = 0.0;
+#pragma unroll
+        for (int q = 0; q < NP / 32; q++) {
+            a += rv[q] * rv[q];
+            b += jv[q] * jv[q];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
         }
+        double ia = 0.0, ib = 0.0;
         if (lane == 0) {
-            sh[0][p >> 5] = a;
-            sh[1][p >> 5] = b;
+            const double ra = sqrt(a / NP), rb = sqrt(b / NP);
+            ia = ra > 0.0 ? 1.0 / ra : 0.0;
+            ib = rb > 0.0 ? 1.0 / rb : 0.0;
+            scale[e] = (float)rb;
         }
-        __syncthreads();
-        // one warp finishes the sums, the square roots and the reciprocals (FP64
-        // division and square root are long sequences on GB300's FP64 pipe)
-        if (p < 32) {
-            double sa = lane < NP / 32 ? sh[0][lane] : 0.0, sb = lane < NP / 32 ? sh[1][lane] : 0.0;
+        ia = __shfl_sync(0xffffffffu, ia, 0);
+        ib = __shfl_sync(0xffffffffu, ib, 0);
 #pragma unroll
-            for (int o = 8; o > 0; o >>= 1) {
-                sa += __shfl_xor_sync(0xffffffffu, sa, o);
-                sb += __shfl_xor_sync(0xffffffffu, sb, o);
-            }
-            if (lane == 0) {
-                const double ra = sqrt(sa / NP), rb = sqrt(sb / NP);
-                sinv[0] = ra > 0.0 ? 1.0 / ra : 0.0;
-                sinv[1] = rb > 0.0 ? 1.0 / rb : 0.0;
-                scale[e] = (float)rb;
-            }
+        for (int q = 0; q < NP / 32; q++) {
+            xin[(e * CIN + 0) * NP + lane + 32 * q] = (float)(rv[q] * ia);
+            xin[(e * CIN + 1) * NP + lane + 32 * q] = (float)(jv[q] * ib);
         }
-        __syncthreads();
-        xin[(e * CIN + 0) * NP + p] = (float)(rv * sinv[0]);
-        xin[(e * CIN + 1) * NP + p] = (float)(jv * sinv[1]);
-        __syncthreads();  // sh and sinv are reused by the next element
     }
 }
 
@@ -550,7 +555,8 @@ __global__ void k_net_target(int64_t n, const double* __restrict__ xs, const dou
 nek_status launch_net_prep(int64_t nelt, const double* r, const double* minv, float* xin, float* scale,
                            cudaStream_t s)
 {
-    k_net_prep<<<static_cast<int>(nelt < 152 * 8 ? nelt : 152 * 8), NP, 0, s>>>(nelt, r, minv, xin, scale);
+    const int64_t nb = (nelt + kPrepWarps - 1) / kPrepWarps;
+    k_net_prep<<<static_cast<int>(nb < 152 * 16 ? nb : 152 * 16), 32 * kPrepWarps, 0, s>>>(nelt, r, minv, xin, scale);
     return check_launch();
 }
 
