@@ -160,8 +160,9 @@ __device__ __forceinline__ void line_apply(const float* __restrict__ M, const fl
 // registers; the pointwise G product runs on the t-lines; phase 2 sums the
 // r- and s-contributions through shared memory and adds the t-contribution in
 // registers before the store.
-// ENERGY: edot[e] = sum over the element's points of u w (products and sums in
-// FP64), which the inner solve uses for <p,w> (see nek_pcg.cuh).
+// ENERGY: edot[e] = sum over the element's points of u w (each thread's nx
+// terms summed in FP32, the element's threads in FP64), which the inner solve
+// uses for <p,w> (see nek_pcg.cuh).
 template <class S, int NX, int EPB, bool ENERGY>
 __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const double* __restrict__ D,
                                                           const S* __restrict__ Glp,
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const dou
         for (int o = 0; o < NX; o++) ue[b * N2 + o * NX + a] += os[o];
     }
     __syncthreads();
-    double energy = 0.0;
+    float energy = 0.f;  // this thread's nx terms u w in FP32, then FP64 across the element
     if (active) {
         float ot[NX];
         line_apply<NX>(sDT, wt, ot);
@@ -293,10 +294,11 @@ __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const dou
             const int p = k * N2 + b * NX + a;
             const float wv = (ue[p] + ot[k]) * scale;
             we[p] = wv;
-            if constexpr (ENERGY) energy = fma(pcg::to_f64(__ldg(ug + p)), pcg::to_f64(wv), energy);
+            if constexpr (ENERGY) energy = fmaf(__ldg(ug + p), wv, energy);
         }
     }
-    if constexpr (ENERGY) element_sums<N2, EPB>(energy, reinterpret_cast<double*>(sR), edot + e0, ne);
+    if constexpr (ENERGY)
+        element_sums<N2, EPB>(pcg::to_f64(energy), reinterpret_cast<double*>(sR), edot + e0, ne);
 }
 
 template <class S, int NX, bool ENERGY>
