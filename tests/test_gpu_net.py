@@ -268,6 +268,24 @@ def test_fcg_truncated_jacobi_mode_matches_pcg(m):
     assert L.nek_fcg_trunc_workspace_bytes(mesh.nelt, 8, 0, 8) > L.nek_fcg_trunc_workspace_bytes(mesh.nelt, 8, 0, 1)
 
 
+def test_fcg_truncated_with_network_falls_back_and_converges():
+    """FCG(8) with a network that is no preconditioner (random small weights) and a short stagnation
+    window: it hands over to Jacobi, empties its direction window, and still reaches the tolerance
+    (checked by the oracle's residual)."""
+    mesh = inputs.box_mesh(4, 3, 3, 8, perturb=0.15, seed=13)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=14)
+    fd = torch.from_numpy(f).to(DEV)
+    x = torch.full_like(fd, float("nan"))
+    th = torch.from_numpy(_theta(15, scale=0.05).astype(np.float32)).to(DEV)
+    r = nekax.fcg_solve(P.gs, mesh.nelt, 8, P.D, P.G, P.prepare_ff(), P.mask, P.minv, th, fd, x, tol=1e-8,
+                        max_iter=20000, stag_window=20, stag_factor=0.01, truncation=8)
+    assert r["status"] == nekax.OK, r
+    assert r["fell_back_at"] > 0 and r["net_applications"] == r["fell_back_at"], r
+    assert Pr.residual(f, x.cpu().numpy()) <= 1e-8 * 1.001
+
+
 def test_residual_and_net_target_match_oracle():
     mesh = inputs.box_mesh(3, 2, 2, 8, perturb=0.15, seed=9)
     P = DeviceProblem(mesh, DEV)

@@ -526,6 +526,13 @@ def test_cg_host_buffers_same_as_device_solve():
         rh = P.cg_host(fh, xh, tol=1e-9, max_iter=500, ax_impl=nekax.AX_FF, staging=stg)
         assert rh["status"] == rd["status"] == nekax.OK and rh["iters"] == rd["iters"]
         assert torch.equal(xh, xd.cpu())
+    # NOT_CONVERGED still copies the last iterate back
+    xh = torch.full_like(torch.from_numpy(f.copy()), float("nan")).pin_memory()
+    xd5 = torch.empty_like(xd)
+    r5 = P.cg(_t(f), xd5, tol=1e-12, max_iter=5, ax_impl=nekax.AX_FF)
+    rh5 = P.cg_host(torch.from_numpy(f.copy()).pin_memory(), xh, tol=1e-12, max_iter=5, ax_impl=nekax.AX_FF)
+    assert r5["status"] == rh5["status"] == nekax.ERR_NOT_CONVERGED and rh5["iters"] == 5
+    assert torch.equal(xh, xd5.cpu())
     L = nekax.load()
     A = 0x10000
     args = [P.gs.handle, mesh.nelt, nx, A, A, A, A, A, A, 0.0, 1, None, None, None, None, None, None]
@@ -666,9 +673,28 @@ def test_batch_graph_replay_is_bit_identical_to_eager():
     assert r3["graph_launches"] == 1 and r3["iterations_run"] == r1["iterations_run"], (r3, r1)
     assert np.array_equal(r1["iters"], r3["iters"])
     assert torch.equal(x1, x3)
-    # an iteration budget that ends the device loop before convergence
-    r4 = B.solve(x3, tol=1e-9, max_iter=12, iters_per_graph=-1)
-    assert r4["status"] == nekax.ERR_NOT_CONVERGED and r4["iterations_run"] == 12
     zero_pos = B.order.index(2)
     assert r1["iters"][zero_pos] == 0
     assert float(B.split(x1)[2].abs().max()) == 0.0
+    # an iteration budget that ends the device loop before convergence
+    r4 = B.solve(x3, tol=1e-9, max_iter=12, iters_per_graph=-1)
+    assert r4["status"] == nekax.ERR_NOT_CONVERGED and r4["iterations_run"] == 12
+
+
+def test_batch_one_launch_native_fp64_operator():
+    """The one-launch batched solve with the native FP64 operator (its <p,w> pass instead of element
+    energies): the same iterates as eager launches, and per-problem parity with the oracle."""
+    from paper_2011_04981_gb300.problem import DeviceBatch
+
+    meshes, fields = _batch_case(seed=20)
+    B = DeviceBatch(meshes, fields, DEV, ff=False)
+    x1 = torch.empty((B.npts,), dtype=torch.float64, device=DEV)
+    x2 = torch.full_like(x1, float("nan"))
+    r1 = B.solve(x1, tol=1e-9, max_iter=3000, iters_per_graph=0)
+    r2 = B.solve(x2, tol=1e-9, max_iter=3000, iters_per_graph=-1)
+    assert r1["status"] == r2["status"] == nekax.OK and r2["graph_launches"] == 1
+    assert np.array_equal(r1["iters"], r2["iters"]) and torch.equal(x1, x2)
+    xs = B.split(x2.cpu().numpy())
+    for q, m in enumerate(meshes):
+        Pr = ref.Problem(m)
+        assert Pr.residual(fields[q], xs[q].reshape(m.nelt, -1)) <= 1e-9 * 1.001
