@@ -60,7 +60,7 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 template <int NA>
-__device__ __forceinline__ void chunk_reduce(double (&acc)[NA], double* parts, int nchunks)
+__device__ __forceinline__ void chunk_reduce(double (&acc)[NA], double* parts, int nchunks, int cid)
 {
     __shared__ double sh[NA][BT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -75,7 +75,7 @@ __device__ __forceinline__ void chunk_reduce(double (&acc)[NA], double* parts, i
         for (int a = 0; a < NA; a++) {
             double t = lane < BT / 32 ? sh[a][lane] : 0.0;
             t = warp_sum(t);
-            if (lane == 0) parts[a * nchunks + blockIdx.x] = t;
+            if (lane == 0) parts[a * nchunks + cid] = t;
         }
     }
 }
@@ -102,7 +102,14 @@ __global__ void __launch_bounds__(BT) kb_init(const int64_t* __restrict__ ch_beg
             acc[1] += rq * rq;
         }
     }
-    chunk_reduce<2>(acc, parts, nchunks);
+    chunk_reduce<2>(acc, parts, nchunks, blockIdx.x);
+}
+
+// Chunk of block b: clist[b] when the host passes a compacted list of the
+// chunks of unfinished problems, else b.
+__device__ __forceinline__ int chunk_of(const int32_t* __restrict__ clist)
+{
+    return clist ? clist[blockIdx.x] : static_cast<int>(blockIdx.x);
 }
 
 // one warp per problem: sums its partials [c0, c1) in order
@@ -146,10 +153,11 @@ __global__ void __launch_bounds__(BT) kb_pw(const int64_t* __restrict__ ch_begin
                                             int nchunks, const uint8_t* __restrict__ flags,
                                             const double* __restrict__ p,
                                             double* __restrict__ w, double* __restrict__ parts,
-                                            const BScal* __restrict__ sc)
+                                            const BScal* __restrict__ sc, const int32_t* __restrict__ clist)
 {
-    if (bhalted(sc[ch_prob[blockIdx.x]])) return;
-    const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
+    const int c = chunk_of(clist);
+    if (bhalted(sc[ch_prob[c]])) return;
+    const int64_t a = ch_begin[c], b = ch_begin[c + 1];
     double acc[1] = {0.0};
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
         const uint8_t fq = flags[q];
@@ -157,7 +165,7 @@ __global__ void __launch_bounds__(BT) kb_pw(const int64_t* __restrict__ ch_begin
         const double wq = w[q];  // read-only: kb_update applies the mask
         if ((fq & (pcg::kFree | pcg::kOwner)) == (pcg::kFree | pcg::kOwner)) acc[0] += pq * wq;
     }
-    chunk_reduce<1>(acc, parts, nchunks);
+    chunk_reduce<1>(acc, parts, nchunks, c);
 }
 
 // pw from the chunk partials of kb_pw or, with edot, from the element energies
@@ -196,12 +204,14 @@ __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_b
                                                 const int32_t* __restrict__ ch_prob, int nchunks,
                                                 const uint8_t* __restrict__ flags, const double* __restrict__ minv,
                                                 const double* __restrict__ w, double* __restrict__ r,
-                                                double* __restrict__ parts, const BScal* __restrict__ sc)
+                                                double* __restrict__ parts, const BScal* __restrict__ sc,
+                                                const int32_t* __restrict__ clist)
 {
-    const BScal& s = sc[ch_prob[blockIdx.x]];
+    const int c = chunk_of(clist);
+    const BScal& s = sc[ch_prob[c]];
     if (bhalted(s)) return;
     const double alpha = s.alpha;
-    const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
+    const int64_t a = ch_begin[c], b = ch_begin[c + 1];
     double acc[2] = {0.0, 0.0};
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
         const uint8_t fq = flags[q];
@@ -215,7 +225,7 @@ __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_b
             acc[1] += rq * zq;
         }
     }
-    chunk_reduce<2>(acc, parts, nchunks);
+    chunk_reduce<2>(acc, parts, nchunks, c);
 }
 
 __global__ void kb_beta(int nprob, const int* __restrict__ pch, const double* __restrict__ parts, int nchunks,
@@ -277,21 +287,23 @@ __global__ void kb_test(int nprob, double tol, BScal* __restrict__ sc, int* __re
 __global__ void __launch_bounds__(BT) kb_dssum(const int64_t* __restrict__ gch_begin,
                                                const int32_t* __restrict__ gch_prob, const uint8_t* __restrict__ pdone,
                                                const int32_t* __restrict__ off, const int32_t* __restrict__ mem,
-                                               double* __restrict__ v)
+                                               double* __restrict__ v, const int32_t* __restrict__ glist)
 {
-    if (pdone[gch_prob[blockIdx.x]]) return;
-    pcg::dssum_groups<double>(gch_begin[blockIdx.x], gch_begin[blockIdx.x + 1], threadIdx.x, BT, off, mem, v);
+    const int g = chunk_of(glist);
+    if (pdone[gch_prob[g]]) return;
+    pcg::dssum_groups<double>(gch_begin[g], gch_begin[g + 1], threadIdx.x, BT, off, mem, v);
 }
 
 __global__ void __launch_bounds__(BT) kb_p(const int64_t* __restrict__ ch_begin, const int32_t* __restrict__ ch_prob,
                                            const double* __restrict__ minv, const double* __restrict__ r,
                                            double* __restrict__ x, double* __restrict__ p,
-                                           const BScal* __restrict__ sc)
+                                           const BScal* __restrict__ sc, const int32_t* __restrict__ clist)
 {
-    const BScal& s = sc[ch_prob[blockIdx.x]];
+    const int c = chunk_of(clist);
+    const BScal& s = sc[ch_prob[c]];
     const bool do_x = s.xpend != 0, do_p = !bhalted(s);
     const double alpha = s.alpha, beta = s.beta;
-    const int64_t a = ch_begin[blockIdx.x], b = ch_begin[blockIdx.x + 1];
+    const int64_t a = ch_begin[c], b = ch_begin[c + 1];
     if (do_x && do_p) {
         for (int64_t q = a + threadIdx.x; q < b; q += BT) {
             const double pq = p[q];
@@ -354,6 +366,7 @@ struct nek_batch {
     int ngchunks;         // chunks of the gather-scatter groups, each within one problem
     int64_t* d_gch_begin; // ngchunks+1: first group of each chunk
     int32_t* d_gch_prob;  // ngchunks: problem of each chunk
+    std::vector<int32_t> h_ch_prob, h_gch_prob;  // the same two maps on the host
 };
 
 using namespace nek;
@@ -368,6 +381,8 @@ struct BLayout {
     int* active;
     uint8_t* pdone;  // nprob: 1 once a problem has finished (converged or broken down)
     uint8_t* flags;  // npts: owner / free byte per point (inner-product weights and the mask)
+    int32_t* clist;  // nchunks: chunks of the unfinished problems, for the vector kernels
+    int32_t* glist;  // ngchunks: the same for the gather-scatter chunks
     size_t bytes;
 };
 
@@ -391,6 +406,8 @@ BLayout b_layout(char* base, const nek_batch* b, bool need_minv)
     L.active = reinterpret_cast<int*>(take(sizeof(int) * 4));  // [0] unfinished problems, [1] loop iterations
     L.pdone = reinterpret_cast<uint8_t*>(take(static_cast<size_t>(b->nprob)));
     L.flags = reinterpret_cast<uint8_t*>(take(static_cast<size_t>(b->npts)));
+    L.clist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * std::max(b->nchunks, 1)));
+    L.glist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * std::max(b->ngchunks, 1)));
     L.bytes = off;
     return L;
 }
@@ -487,6 +504,8 @@ nek_status nek_batch_create(int nprob, const int64_t* nelt, const int* nx, const
         if (b->gs->ngroups != gtot) throw 3;  // the plan's grouping must be the one counted above
         gch_begin.push_back(gtot);
         b->ngchunks = static_cast<int>(gch_prob.size());
+        b->h_ch_prob = ch_prob;
+        b->h_gch_prob = gch_prob;
         if ((st = check_cuda(cudaMalloc(&b->d_gch_begin, sizeof(int64_t) * gch_begin.size()))) != NEK_OK) throw 3;
         if ((st = check_cuda(cudaMalloc(&b->d_gch_prob, sizeof(int32_t) * std::max<size_t>(gch_prob.size(), 1)))) !=
             NEK_OK)
@@ -611,12 +630,20 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
     int active = 0;
     const int per_graph = iters_per_graph > 0 ? iters_per_graph : 0;
     bool device_loop = false;  // the one-launch solve ran (or there was nothing left to run)
+    bool lists_changed = false;
 
     // Per group, the elements before ax_first[g] belong to finished problems only,
     // and the operator is launched from there on.  With the problems of a group
     // ordered by size (the larger need more iterations), the launches shrink as
     // the small ones finish; ax_first is advanced at graph boundaries.
     std::vector<int64_t> ax_first(b->groups.size(), 0);
+    // The vector kernels and dssum run over compacted lists of the chunks of the
+    // problems still going (L.clist / L.glist), rebuilt by the host at graph
+    // boundaries; until the first rebuild (and in the one-launch solve) every
+    // chunk is launched and the finished problems' blocks return at once.
+    bool use_lists = false;
+    int n_act = nc, n_gact = b->ngchunks;
+    std::vector<int32_t> h_clist, h_glist;
     int iter_launches = 0;  // launches enqueued by the last one_iteration
     auto one_iteration = [&](cudaStream_t ss) -> nek_status {
         iter_launches = 0;
@@ -632,17 +659,19 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
             if (sa != NEK_OK) return sa;
             iter_launches++;
         }
-        if (b->ngchunks > 0)
-            kb_dssum<<<b->ngchunks, BT, 0, ss>>>(b->d_gch_begin, b->d_gch_prob, L.pdone, b->gs->d_offsets,
-                                                 b->gs->d_members, L.w);
+        const int32_t* cl = use_lists ? L.clist : nullptr;
+        const int32_t* gl = use_lists ? L.glist : nullptr;
+        if (n_gact > 0)
+            kb_dssum<<<n_gact, BT, 0, ss>>>(b->d_gch_begin, b->d_gch_prob, L.pdone, b->gs->d_offsets,
+                                            b->gs->d_members, L.w, gl);
         // the float-float operator writes element energies, which give <p,w> (no kb_pw pass)
-        if (!Gff) kb_pw<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, L.p, L.w, L.parts, L.sc);
+        if (!Gff) kb_pw<<<n_act, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, L.p, L.w, L.parts, L.sc, cl);
         kb_alpha<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, L.sc, L.active, b->d_pel, Gff ? L.edot : nullptr);
-        kb_update<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, L.w, L.r, L.parts, L.sc);
+        kb_update<<<n_act, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, nc, L.flags, mv, L.w, L.r, L.parts, L.sc, cl);
         kb_beta<<<wblocks, 256, 0, ss>>>(np, b->d_pch, L.parts, nc, L.sc, L.active);
         kb_test<<<(np + 255) / 256, 256, 0, ss>>>(np, tol_rel, L.sc, L.active, L.pdone);
-        kb_p<<<nc, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, mv, L.r, x, L.p, L.sc);
-        iter_launches += (b->ngchunks > 0 ? 1 : 0) + (Gff ? 0 : 1) + 5;
+        kb_p<<<n_act, BT, 0, ss>>>(b->d_ch_begin, b->d_ch_prob, mv, L.r, x, L.p, L.sc, cl);
+        iter_launches += (n_gact > 0 ? 1 : 0) + (Gff ? 0 : 1) + 5;
         return check_launch();
     };
     int graph_iter_launches = 0;  // launches in one replay of the captured graph
@@ -692,6 +721,35 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
             }
         }
         return shrunk;
+    };
+    // Rebuilds the chunk lists from the finished problems (hdone).  Only when
+    // either list is an eighth or more shorter than the one in use are both
+    // uploaded, and the graph is then recaptured with the new grid sizes, so a
+    // graph never runs with a list other than the one it was captured for.
+    auto shrink_lists = [&]() -> nek_status {
+        h_clist.clear();
+        h_glist.clear();
+        for (int c = 0; c < nc; c++)
+            if (!hdone[b->h_ch_prob[c]]) h_clist.push_back(c);
+        for (int g = 0; g < b->ngchunks; g++)
+            if (!hdone[b->h_gch_prob[g]]) h_glist.push_back(g);
+        const int na = static_cast<int>(h_clist.size()), ng = static_cast<int>(h_glist.size());
+        if (na > n_act - std::max(1, n_act / 8) && ng > n_gact - std::max(1, n_gact / 8)) return NEK_OK;
+        if (na > 0) {
+            nek_status r = check_cuda(cudaMemcpyAsync(L.clist, h_clist.data(), sizeof(int32_t) * na,
+                                                      cudaMemcpyHostToDevice, s));
+            if (r != NEK_OK) return r;
+        }
+        if (ng > 0) {
+            nek_status r = check_cuda(cudaMemcpyAsync(L.glist, h_glist.data(), sizeof(int32_t) * ng,
+                                                      cudaMemcpyHostToDevice, s));
+            if (r != NEK_OK) return r;
+        }
+        n_act = na;
+        n_gact = ng;
+        use_lists = true;
+        lists_changed = true;
+        return NEK_OK;
     };
 
     if (!minv) {
@@ -776,7 +834,9 @@ nek_status nek_batch_cg_solve(const nek_batch* b, const double* G, const float* 
             goto done;
         if ((st = check_cuda(cudaStreamSynchronize(s))) != NEK_OK) goto done;
         if (active <= 0) break;
-        if (advance_windows() && gexec)
+        lists_changed = false;
+        if ((st = shrink_lists()) != NEK_OK) goto done;
+        if ((advance_windows() || lists_changed) && gexec)
             if ((st = capture()) != NEK_OK) goto done;
         if (gexec && it_done + per_graph <= max_iter) {
             if ((st = check_cuda(cudaGraphLaunch(gexec, s))) != NEK_OK) goto done;
