@@ -184,16 +184,17 @@ def traffic_from_profile(nx, nelt, which="fp64"):
         return None
 
 
-def _oracle_pcg_samples(nx, budget_s, samples=1, lib_path=None, max_iters=200):
-    """Time the oracle (as it stands) on a bounded sample of the workload: Jacobi-PCG iterations on a
-    12x12x12-element box of the same family (same nx, perturbation and seed recipe).  Returns the mesh's
-    point count and one (iterations, seconds) pair per sample."""
+def _oracle_pcg_samples(nx, budget_s, samples=1, lib_path=None, max_iters=200, elems=12):
+    """Time the oracle (as it stands) on a bounded sample of the workload: Jacobi-PCG iterations on an
+    elems^3-element box of the same family (same nx, perturbation and seed recipe), as many per sample as
+    fit in budget_s (at most max_iters).  Returns the mesh's point count and one (iterations, seconds)
+    pair per sample."""
     import contextlib
 
     from oracle import ref
     from paper_2011_04981_gb300 import inputs
 
-    e = 12
+    e = elems
     mesh = inputs.box_mesh(e, e, e, nx, perturb=0.1, seed=1)
     P = ref.Problem(mesh)
     f = inputs.random_global_field(mesh, seed=2)
@@ -211,20 +212,21 @@ def _oracle_pcg_samples(nx, budget_s, samples=1, lib_path=None, max_iters=200):
     return mesh.npts, out
 
 
-def cpu_baseline(nx, iters_budget_s=15.0, threads=1, samples=1, warmup=0):
+def cpu_baseline(nx, iters_budget_s=15.0, threads=1, samples=1, warmup=0, elems=12, max_iters=None):
     """The oracle's rate on `threads` host threads: 1 = the default build in this process; more = its
     -fopenmp build (same operations, independent loops split over threads) in a child process with
     OMP_NUM_THREADS set, so that its OpenMP runtime is not the one PyTorch loaded.  `warmup` untimed
     samples come first; the result's 'per_sample' lists (iterations, seconds) of each timed sample."""
     if threads <= 1:
-        npts, smp = _oracle_pcg_samples(nx, iters_budget_s, warmup + samples)
+        npts, smp = _oracle_pcg_samples(nx, iters_budget_s, warmup + samples, elems=elems,
+                                        max_iters=max_iters or 200)
         smp = smp[warmup:]
         build = "single-threaded C oracle"
     else:
         env = dict(os.environ, OMP_NUM_THREADS=str(threads), OMP_PROC_BIND="false")
         cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-baseline-only", "--cpu-threads", str(threads),
                "--nx", str(nx), "--cpu-seconds", str(iters_budget_s), "--steps", str(samples), "--warmup",
-               str(warmup)]
+               str(warmup), "--elems", str(elems), "--iters", str(max_iters or 4000)]
         r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=60 + 4 * iters_budget_s * samples)
         lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
         if r.returncode != 0 or not lines:
@@ -237,8 +239,8 @@ def cpu_baseline(nx, iters_budget_s=15.0, threads=1, samples=1, warmup=0):
     its = sum(i for i, _ in smp)
     secs = sum(s for _, s in smp)
     return {"value": npts * its / secs / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "%d x %d Jacobi-PCG iterations on a 12x12x12-element deformed box, nx=%d (%d points), %s, "
-                      "%.1f s" % (len(smp), smp[0][0], nx, npts, build, secs),
+            "sample": "%d x %d Jacobi-PCG iterations on a %dx%dx%d-element deformed box, nx=%d (%d points), %s, "
+                      "%.1f s" % (len(smp), smp[0][0], elems, elems, elems, nx, npts, build, secs),
             "seconds": secs, "per_sample": smp, "host": host_cpu()}
 
 
@@ -251,7 +253,7 @@ def cpu_baseline_child(args):
         print(json.dumps({"unavailable": "no OpenMP-capable C compiler on this host"}))
         return 0
     npts, smp = _oracle_pcg_samples(args.nx, args.cpu_seconds or 15.0, max(1, args.steps + args.warmup), so,
-                                    max_iters=4000)
+                                    max_iters=args.iters, elems=args.elems)
     print(json.dumps({"npts": npts, "samples": smp[args.warmup:], "threads": args.cpu_threads}))
     return 0
 
@@ -286,26 +288,31 @@ def max_over_ranks(dist, values, device):
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     """The oracle on the host's cores (all of them, through its -fopenmp build; one if that build is not
-    available), each step a bounded sample of the workload."""
+    available) on the benchmark's own workload: Jacobi-PCG on the same elems^3 box at the same nx, each
+    step as many iterations (up to --iters) as fit in its share of about two minutes."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     budget = args.cpu_seconds if args.cpu_seconds else max(3.0, 120.0 / max(1, args.steps + args.warmup))
     threads = os.cpu_count() or 1
-    cb = cpu_baseline(args.nx, budget, threads=threads, samples=args.steps, warmup=args.warmup) \
-        if threads > 1 else None
+    kw = dict(samples=args.steps, warmup=args.warmup, elems=args.elems, max_iters=args.iters)
+    cb = cpu_baseline(args.nx, budget, threads=threads, **kw) if threads > 1 else None
     if cb is None or "unavailable" in cb:
         threads = 1
-        cb = cpu_baseline(args.nx, budget, threads=1, samples=args.steps, warmup=args.warmup)
+        cb = cpu_baseline(args.nx, budget, threads=1, **kw)
     steps = cb["per_sample"]
-    npts = 12 ** 3 * args.nx ** 3
+    e = args.elems
+    npts = e ** 3 * args.nx ** 3
     tot_s = sum(s for _, s in steps)
     value = npts * sum(i for i, _ in steps) / tot_s / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_s / len(steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "Jacobi-PCG iterations, deformed box, nx=%d, FP64 (oracle sample)" % args.nx,
-                       "elements": 12 ** 3, "nx": args.nx},
+            "config": {"workload": "Jacobi-PCG, %d PCG iterations per step (AX+dssum+mask+dots+updates), "
+                                   "%dx%dx%d deformed box (perturbation 0.1 h), nx=%d, FP64, the C oracle on %d host "
+                                   "threads" % (steps[0][0], e, e, e, args.nx, threads),
+                       "elements": e ** 3, "nx": args.nx, "points": npts, "iters_per_step": steps[0][0],
+                       "parallelism": "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": cb["sample"],
                              "host": cb.get("host")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
