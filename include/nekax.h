@@ -137,6 +137,38 @@ nek_status nek_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, co
 nek_status nek_ax_ff_energy(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                             double* edot, void* stream);
 
+/*
+ * w = AX(u) to FP64 accuracy with the contractions on the tensor cores
+ * (tcgen05 BF16 MMAs, FP32 tensor-memory accumulators): the operator of
+ * Section II-B, Listing 1.  Per element, u and then the pointwise products
+ * G (ur, us, ut) are scaled to the element's largest magnitude and split into
+ * six 8-bit BF16 digits each (D likewise); every digit product is summed
+ * exactly, level by level, by the tensor cores, and the levels are recombined
+ * into float pairs on the CUDA cores; the G product is float-float.  Same
+ * arguments, layouts and alignment as nek_ax_ff (Gff from nek_geom_ff); nx
+ * even and at most 10, else NEK_ERR_UNSUPPORTED_NX.  The result matches the
+ * FP64 operator to ~1e-14 relative in the max norm of each element (the error
+ * scales with the element's largest |u|: parts of an element far below it keep
+ * less relative accuracy); the same range caveats as nek_ax_ff.  Every wait of
+ * the kernel on its tensor-core work is bounded (~2 s); one that runs out
+ * leaves NaN in the outputs of the elements it had not finished (see
+ * nek_ax_oz_selftest).  Async on stream.
+ */
+nek_status nek_ax_oz(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+                     void* stream);
+
+/* Self-test of the bounded waits of nek_ax_oz's kernel: runs it on three nx = 4
+ * elements (zero D, G and u, so w = 0) with every mbarrier wait bounded by
+ * wait_us microseconds (1 .. 2e6).  force_timeout != 0 makes the mbarrier
+ * expect one arrival more than the kernel's MMAs ever give, so every wait runs
+ * out: the kernel must then set its flag, write NaN into its elements' outputs,
+ * free its tensor memory and return.  *timed_out receives whether the flag was
+ * set.  Returns NEK_ERR_TIMEOUT when it was (and the output was poisoned),
+ * NEK_OK when the kernel finished normally, NEK_ERR_CUDA if the flag and the
+ * output disagree.  No paper counterpart: failure detection of the library.
+ * Allocates and synchronises the device; for tests. */
+nek_status nek_ax_oz_selftest(int force_timeout, int64_t wait_us, int* timed_out);
+
 /* ------------------------------------------------------------ tuning ---
  * The AX kernels group elements into CTAs; the group size (1, 2 or 4 elements
  * per CTA where threads and shared memory allow) changes only occupancy, never

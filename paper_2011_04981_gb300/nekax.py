@@ -113,6 +113,8 @@ _SIGS = {
     "nek_net_apply_bf16": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_apply_bf16_mma": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_tc_selftest": ([_I, _I64, ctypes.POINTER(_I)], _I),
+    "nek_ax_oz": ([_I64, _I, _P, _P, _P, _P, _P], _I),
+    "nek_ax_oz_selftest": ([_I, _I64, ctypes.POINTER(_I)], _I),
     "nek_net_train_workspace_bytes": ([_I], ctypes.c_size_t),
     "nek_net_forward_batch": ([_I, _P, _P, _P, _P, _P], _I),
     "nek_net_train_grad": ([_I, _P, _P, _P, _P, _P, _P, _P], _I),
@@ -234,6 +236,18 @@ def geom_ff(nelt, nx, G, Gff, stream=None):
 
 def ax_ff(nelt, nx, D, Gff, u, w, stream=None):
     _check("nek_ax_ff", load().nek_ax_ff(nelt, nx, _ptr(D), _ptr(Gff), _ptr(u), _ptr(w), _stream(stream)))
+
+
+def ax_oz(nelt, nx, D, Gff, u, w, stream=None):
+    """w = AX u to FP64 accuracy with the contractions on the tensor cores (BF16 digits)."""
+    _check("nek_ax_oz", load().nek_ax_oz(nelt, nx, _ptr(D), _ptr(Gff), _ptr(u), _ptr(w), _stream(stream)))
+
+
+def ax_oz_selftest(force_timeout, wait_us):
+    """(status, timed_out) of the operator kernel's bounded-wait self-test."""
+    t = ctypes.c_int(0)
+    st = load().nek_ax_oz_selftest(int(force_timeout), int(wait_us), ctypes.byref(t))
+    return st, t.value
 
 
 def ax_ff_energy(nelt, nx, D, Gff, u, w, edot, stream=None):

@@ -50,6 +50,9 @@ class DeviceProblem:
     def ax_ff(self, u, w, stream=None):
         nekax.ax_ff(self.nelt, self.nx, self.D, self.prepare_ff(), u, w, stream)
 
+    def ax_oz(self, u, w, stream=None):
+        nekax.ax_oz(self.nelt, self.nx, self.D, self.prepare_ff(), u, w, stream)
+
     def cg(self, f, x, tol=1e-8, max_iter=1000, workspace=None, check_every=1, time_ax=False, stream=None,
            ax_impl=nekax.AX_FP64):
         Gff = self.prepare_ff() if ax_impl == nekax.AX_FF else None

@@ -70,6 +70,25 @@ def test_ax_rejects_bad_arguments_before_launch(lib):
     assert L.nek_ax(4, 8, A16, A16, A16, A16 + 4096, None) == nekax.ERR_INVALID_ARG
 
 
+def test_ax_oz_rejects_bad_arguments_before_launch(lib):
+    A16 = 0x10000  # 16-byte aligned fake addresses, never dereferenced
+    L = lib
+    for nx in (1, 3, 9, 11, 12, 16, 17):  # even nx up to 10 only
+        assert L.nek_ax_oz(4, nx, A16, A16, A16, A16 * 2, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_ax_oz(-1, 8, A16, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_oz(0, 8, None, None, None, None, None) == nekax.OK  # empty input is a no-op
+    assert L.nek_ax_oz(4, 8, None, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_oz(4, 8, A16, None, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_oz(4, 8, A16, A16 + 8, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # Gff misaligned
+    assert L.nek_ax_oz(4, 8, A16, A16, A16 + 4, A16 * 2, None) == nekax.ERR_INVALID_ARG  # u misaligned
+    assert L.nek_ax_oz(4, 8, A16, A16, A16, A16 * 2 + 4, None) == nekax.ERR_INVALID_ARG  # w misaligned
+    assert L.nek_ax_oz(4, 8, A16, A16, A16, A16 + 4096, None) == nekax.ERR_INVALID_ARG  # u and w overlap
+    t = ctypes.c_int(0)
+    assert L.nek_ax_oz_selftest(1, 0, ctypes.byref(t)) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_oz_selftest(1, 2000001, ctypes.byref(t)) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_oz_selftest(1, 100, None) == nekax.ERR_INVALID_ARG
+
+
 def test_other_entry_points_reject_bad_arguments(lib):
     L = lib
     A16 = 0x10000
