@@ -138,23 +138,32 @@ nek_status nek_ax_ff_energy(int64_t nelt, int nx, const double* D, const float* 
                             double* edot, void* stream);
 
 /*
+ * Geometric factors split into float pairs for nek_ax_oz (device, async): the
+ * values of nek_geom_ff with two adjacent points interleaved,
+ * Goz[e][q][c] = (hi of G[e][2q][c], hi of G[e][2q+1][c], lo of G[e][2q][c],
+ * lo of G[e][2q+1][c]) for c = 0..5 (48 bytes per point).  nx as nek_ax_oz;
+ * G: device, 8-byte aligned; Goz: device, 16-byte aligned, must not overlap G.
+ */
+nek_status nek_geom_oz(int64_t nelt, int nx, const double* G, float* Goz, void* stream);
+
+/*
  * w = AX(u) to FP64 accuracy with the contractions on the tensor cores
  * (tcgen05 BF16 MMAs, FP32 tensor-memory accumulators): the operator of
  * Section II-B, Listing 1.  Per element, u and then the pointwise products
  * G (ur, us, ut) are scaled to the element's largest magnitude and split into
  * six 8-bit BF16 digits each (D likewise); every digit product is summed
  * exactly, level by level, by the tensor cores, and the levels are recombined
- * into float pairs on the CUDA cores; the G product is float-float.  Same
- * arguments, layouts and alignment as nek_ax_ff (Gff from nek_geom_ff); nx
- * even and at most 10, else NEK_ERR_UNSUPPORTED_NX.  The result matches the
- * FP64 operator to ~1e-14 relative in the max norm of each element (the error
- * scales with the element's largest |u|: parts of an element far below it keep
- * less relative accuracy); the same range caveats as nek_ax_ff.  Every wait of
- * the kernel on its tensor-core work is bounded (~2 s); one that runs out
- * leaves NaN in the outputs of the elements it had not finished (see
+ * into float pairs on the CUDA cores; the G product is float-float.  Layouts
+ * as nek_ax except Goz (from nek_geom_oz); u and w device, 16-byte aligned, no
+ * overlap; nx even and at most 10, else NEK_ERR_UNSUPPORTED_NX.  The result
+ * matches the FP64 operator to ~1e-14 relative in the max norm of each element
+ * (the error scales with the element's largest |u|: parts of an element far
+ * below it keep less relative accuracy); the same range caveats as nek_ax_ff.
+ * Every wait of the kernel on its tensor-core work is bounded (~2 s); one that
+ * runs out leaves NaN in the outputs of the elements it had not finished (see
  * nek_ax_oz_selftest).  Async on stream.
  */
-nek_status nek_ax_oz(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+nek_status nek_ax_oz(int64_t nelt, int nx, const double* D, const float* Goz, const double* u, double* w,
                      void* stream);
 
 /* Self-test of the bounded waits of nek_ax_oz's kernel: runs it on three nx = 4

@@ -27,10 +27,12 @@
 //     digits and two zeros, so a point's digits are written as one 16-byte
 //     store per direction.  K-adjacent core matrices are 144 bytes apart
 //     (128 + 16) so that a warp's stores spread over the banks.
-//   B: row n = (output index o, level L), K = (l, a): p_{L-a} of D[o][l]
-//     (D[l][o] in phase 2), zero where L - a is not a digit index.
-//   Accumulator (TMEM): lane = line, column 8 o + L = level L of output o on
-//     the line; the three directions side by side (24 NX of 256 columns).
+//   B: row n = 16 (o / 2) + 2 L + (o mod 2) for output index o and level L,
+//     K = (l, a): p_{L-a} of D[o][l] (D[l][o] in phase 2), zero where L - a is
+//     not a digit index.  Two outputs of one level sit in adjacent columns, so
+//     one 16-column TMEM load gives both lanes of a packed f32x2 operand.
+//   Accumulator (TMEM): lane = line, column n as above; the three directions
+//     side by side (24 NX of 256 columns).
 //
 // Recombination of one output from its exact levels x_0..x_7: with
 // sigma = 1.5 * 2^k and 2^(k-1) above every partial sum,
@@ -43,15 +45,24 @@
 // exactly, then one TwoSum gives the output pair.  The result carries about
 // 2^-47 of the element's scale, like the float-float kernel.
 //
-// Stages per element (128 threads; thread m reads TMEM lane m, the line m of
-// every direction): the u digits (point-strided, two points per packed f32x2
-// lane pair), phase-1 MMAs (one thread issues, committed to an mbarrier),
-// recombination into a float-pair exchange array (over the A buffers, whose
-// MMAs have completed), the G product (point-strided), its pairs renormalised
-// by TwoSum (the digit bound needs |low| <= ulp(high) / 2, which cancellation
-// among the three products can break), the digits of wr, ws, wt, phase-2 MMAs, recombination, and the sum of the three directions written
-// as doubles.  CTAs are persistent (two per SM, bound by the 256 TMEM columns
-// each takes) and hold the B matrices of D for the whole launch.
+// Work split (256 threads): every point-wise stage works on pairs of adjacent
+// points (p, p + 1) in the two lanes of packed f32x2 operations, so vector
+// loads give packed operands directly: u as two doubles, G in the pair-
+// interleaved layout of nek_geom_oz, the exchange arrays likewise.  Thread
+// lanes read TMEM lanes 32 (warp mod 4) + lane, the line of every direction;
+// the two warps that share a lane range take alternate 16-column chunks.  For
+// the s and t lines, adjacent lines hold adjacent points, so the two TMEM
+// lanes of a point pair swap one value each (a shuffle) and store whole pairs.
+//
+// Stages per element: the u digits, phase-1 MMAs (one thread issues,
+// committed to an mbarrier), recombination into the exchange array (over the
+// A buffers, whose MMAs have completed), the G product with its pairs
+// renormalised by TwoSum (the digit bound needs |low| <= ulp(high) / 2, which
+// cancellation among the three products can break), the digits of wr, ws, wt,
+// phase-2 MMAs, recombination, and the sum of the three directions written as
+// doubles.  CTAs are persistent (two per SM, bound by the 256 TMEM columns
+// each takes) and hold the B matrices of D for the whole launch; G of the
+// element and u of the next one are prefetched into L2.
 //
 // Every mbarrier wait is bounded (~2 s of global time).  A wait that runs out
 // sets a device flag, writes NaN into every output of the CTA's remaining
@@ -67,7 +78,7 @@ namespace nek {
 
 namespace {
 
-constexpr int kNT = 128;               // 4 warps: one per 32-lane TMEM sub-partition
+constexpr int kNT = 256;               // 8 warps; warps w and w + 4 share TMEM lanes 32 (w mod 4) ..
 constexpr int kLbo = 144;              // A: bytes between K-adjacent core matrices
 constexpr uint32_t kTmemCols = 256;
 constexpr long long kWaitNs = 2000000000LL;
@@ -77,15 +88,18 @@ __device__ int g_ax_oz_timeout = 0;    // set by a bounded wait that ran out
 template <int NX>
 struct Oz {
     static_assert(NX % 2 == 0 && NX >= 2 && NX <= 10, "even nx up to 10");
-    static constexpr int N2 = NX * NX, N3 = N2 * NX;
+    static constexpr int N2 = NX * NX, N3 = N2 * NX, NPP = N3 / 2;
     static constexpr int NCOL = 8 * NX;        // MMA N and TMEM columns per direction
     static constexpr int KSTEP = NX / 2;       // MMAs per direction (K = 8 NX, 16 per MMA)
     static constexpr int SBO = NX * kLbo;      // A: bytes between 8-row groups
     static constexpr int ABYTES = 16 * SBO;    // A: 128 rows of one direction
     static constexpr int BSBO = NX * 128;      // B: bytes between 8-row groups
     static constexpr int BBYTES = NX * NX * 128;
-    static constexpr int NPAIR = (N3 + 2 * kNT - 1) / (2 * kNT);  // point pairs per thread
+    static constexpr int NPR = (NPP + kNT - 1) / kNT;  // point pairs per thread
     static constexpr uint32_t IDESC = tc5::idesc_bf16_f32(128, NCOL);
+    // exchange arrays over the A buffers: phase 1 [3][NPP] float4, phase 2 [3][NPP] float4 + [3][NPP] float2
+    static_assert(3 * NPP * 24 <= 3 * ABYTES, "exchange fits over the A buffers");
+    static_assert(3 * ABYTES <= 16 * 65536, "digit-row offsets / 16 fit 16 bits");
 };
 
 struct OzMisc {
@@ -93,7 +107,8 @@ struct OzMisc {
     uint32_t tmem;
     int ed;            // D < 2^ed
     float sig[2];      // recombination offsets of phase 1 and phase 2
-    float red[2][4];   // per-warp maxima: [0] |u|, [1] |wr|, |ws|, |wt|
+    float red[2][8];   // per-warp maxima: [0] |u|, [1] |wr|, |ws|, |wt|
+    int flag[2];       // a wait of phase 1 / phase 2 ran out
     double rs[10], cs[10];  // absolute row / column sums of D
 };
 
@@ -150,7 +165,7 @@ __device__ __forceinline__ float spl<float>(float x) { return x; }
 template <>
 __device__ __forceinline__ float2 spl<float2>(float x) { return make_float2(x, x); }
 
-// y + yl (|y + yl| < ~1, yl below ulp(y)) -> q_0..q_5 on the grids 2^-8, ..., 2^-48:
+// y + yl (|y + yl| < ~1, |yl| <= ulp(y) / 2) -> q_0..q_5 on the grids 2^-8, ..., 2^-48:
 // round-to-grid by adding and subtracting 1.5 * 2^(23 - 8(a+1)); the remainders are exact.
 template <class T>
 __device__ __forceinline__ void digits6(T y, T yl, T (&q)[6])
@@ -176,9 +191,11 @@ __device__ __forceinline__ uint32_t bf16_pair(float lo, float hi)
 {
     return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
-__device__ __forceinline__ uint4 digit_row(float q0, float q1, float q2, float q3, float q4, float q5)
+// The 16-byte digit rows of the two points of a packed pair.
+__device__ __forceinline__ void digit_rows(const float2 (&q)[6], uint4& r0, uint4& r1)
 {
-    return make_uint4(bf16_pair(q0, q1), bf16_pair(q2, q3), bf16_pair(q4, q5), 0u);
+    r0 = make_uint4(bf16_pair(q[0].x, q[1].x), bf16_pair(q[2].x, q[3].x), bf16_pair(q[4].x, q[5].x), 0u);
+    r1 = make_uint4(bf16_pair(q[0].y, q[1].y), bf16_pair(q[2].y, q[3].y), bf16_pair(q[4].y, q[5].y), 0u);
 }
 
 // |m| < 2^return (0 for m == 0); m >= 0.
@@ -201,18 +218,21 @@ __device__ __forceinline__ double widen_scaled(float f, int X)
     return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
-// Max over the CTA of non-negative v (one barrier); red: 4 floats of shared memory.
+// Max over the CTA of non-negative v (one barrier); red: 8 floats of shared memory.
 __device__ __forceinline__ float block_max(float v, float* red)
 {
     const unsigned x = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(v));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = __uint_as_float(x);
     __syncthreads();
-    return fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+    float m = red[0];
+#pragma unroll
+    for (int q = 1; q < kNT / 32; q++) m = fmaxf(m, red[q]);
+    return m;
 }
 
 // Byte offset of (row, chunk) in one direction's A buffer.
 template <int NX>
-__device__ __forceinline__ int a_off(int row, int chunk)
+__host__ __device__ constexpr int a_off(int row, int chunk)
 {
     return (row >> 3) * Oz<NX>::SBO + chunk * kLbo + (row & 7) * 16;
 }
@@ -235,52 +255,99 @@ __device__ __forceinline__ void recombine(const float2 (&x)[8], float2 sig, floa
     s = add2(x[4], s);
 }
 
-// Thread m (< NX^2) reads its TMEM lane (line m of every direction) and
-// recombines the 3 NX outputs: phase 1 stores float pairs X2[d][point], phase 2
-// (hi, E, s, 0) in X4[d][point].  Warps with no line return at once
-// (warp-uniform); the others load their lanes whole.
-template <int NX, bool PHASE2>
+// Recombine this lane's TMEM lane m (line m of every direction) into the exchange
+// arrays, indexed by point pair: phase 1 XA[d][pp] = (S(p), S(p+1), lo(p), lo(p+1)),
+// phase 2 XA[d][pp] = (hi, hi, E, E) and XS[d][pp] = (s, s).  The two warps of a
+// lane range take alternate 32-column blocks (HALF: which), one TMEM wait per
+// block; warps whose lanes hold no line return at once (warp-uniform).
+template <int NX, bool PHASE2, int HALF>
 __device__ __forceinline__ void readout(uint32_t lane_addr, float sig, unsigned char* __restrict__ X, int m)
 {
     using C = Oz<NX>;
-    constexpr int N2 = C::N2, N3 = C::N3;
+    constexpr int N2 = C::N2, NPP = C::NPP, NCOL = C::NCOL;
+    constexpr int NCH = 3 * NCOL / 16;  // 16-column chunks over the three directions
     if ((m & ~31) >= N2) return;
     const float2 s2 = sp2(sig);
-    float2* X2 = reinterpret_cast<float2*>(X);
-    float4* X4 = reinterpret_cast<float4*>(X);
+    float4* XA = reinterpret_cast<float4*>(X);
+    float* XAf = reinterpret_cast<float*>(X);
+    float* XSf = reinterpret_cast<float*>(X + 3 * NPP * 16);
+    const bool valid = m < N2;
+    // lane m's lines: r (j,k) = m; s (i,k) = m; t (i,j) = m
+    const int pr = NX * m, ps = (m % NX) + N2 * (m / NX), pt = m;
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
+    for (int ch = HALF; ch < NCH; ch += 2) {
+        const int d = (16 * ch) / NCOL, o = 2 * (((16 * ch) % NCOL) / 16);  // outputs o, o + 1 of direction d
+        uint32_t r[16];
+        tc5::tmem_ld16(lane_addr + (uint32_t)(16 * ch), r);
+        float2 x[8];
 #pragma unroll
-        for (int c = 0; c < NX / 2; c++) {
-            uint32_t r[16];
-            tc5::tmem_ld16(lane_addr + (uint32_t)(d * C::NCOL + 16 * c), r);
-            if (m < N2) {
-                float2 x[8];
-#pragma unroll
-                for (int L = 0; L < 8; L++) x[L] = make_float2(__uint_as_float(r[L]), __uint_as_float(r[8 + L]));
-                float2 hi, E, sm;
-                recombine(x, s2, hi, E, sm);
-                const int o = 2 * c;
-                // points of outputs o and o + 1 on line m
-                const int p = d == 0 ? o + NX * m : d == 1 ? (m % NX) + N2 * (m / NX) + NX * o : m + N2 * o;
-                const int step = d == 0 ? 1 : d == 1 ? NX : N2;
-                if (!PHASE2) {
-                    // Fast2Sum(hi, E) -> (S, T); the pair (S, T + s)
-                    const float2 S = add2(hi, E);
-                    const float2 lo = add2(sub2(E, sub2(S, hi)), sm);
-                    if (d == 0) {
-                        *reinterpret_cast<float4*>(X2 + p) = make_float4(S.x, lo.x, S.y, lo.y);
-                    } else {
-                        X2[d * N3 + p] = make_float2(S.x, lo.x);
-                        X2[d * N3 + p + step] = make_float2(S.y, lo.y);
-                    }
-                } else {
-                    X4[d * N3 + p] = make_float4(hi.x, E.x, sm.x, 0.f);
-                    X4[d * N3 + p + step] = make_float4(hi.y, E.y, sm.y, 0.f);
-                }
+        for (int L = 0; L < 8; L++) x[L] = make_float2(__uint_as_float(r[2 * L]), __uint_as_float(r[2 * L + 1]));
+        float2 hi, E, sm;
+        recombine(x, s2, hi, E, sm);
+        float2 A0, A1;  // phase 1: S, lo; phase 2: hi, E
+        if (!PHASE2) {
+            // Fast2Sum(hi, E) -> (S, T); the pair (S, T + s)
+            A0 = add2(hi, E);
+            A1 = add2(sub2(E, sub2(A0, hi)), sm);
+        } else {
+            A0 = hi;
+            A1 = E;
+        }
+        if (!valid) continue;
+        if (d == 0) {
+            // line (j,k) = m: outputs o, o + 1 are the two points of pair (o + NX m) / 2
+            const int pp = (o + pr) >> 1;
+            XA[pp] = make_float4(A0.x, A0.y, A1.x, A1.y);
+            if (PHASE2) reinterpret_cast<float2*>(XSf)[pp] = sm;
+        } else {
+            // s: points (i, o, k), (i, o + 1, k); t: points (i, j, o), (i, j, o + 1); each is lane i mod 2 of its
+            // pair
+            const int p0 = d == 1 ? ps + NX * o : pt + N2 * o;
+            const int p1 = p0 + (d == 1 ? NX : N2);
+            const int b0 = 4 * (d * NPP + (p0 >> 1)) + (p0 & 1), b1 = 4 * (d * NPP + (p1 >> 1)) + (p1 & 1);
+            XAf[b0] = A0.x;
+            XAf[b0 + 2] = A1.x;
+            XAf[b1] = A0.y;
+            XAf[b1 + 2] = A1.y;
+            if (PHASE2) {
+                XSf[2 * (d * NPP + (p0 >> 1)) + (p0 & 1)] = sm.x;
+                XSf[2 * (d * NPP + (p1 >> 1)) + (p1 & 1)] = sm.y;
             }
         }
     }
+}
+
+// One thread waits for the commit of the MMAs; a barrier hands the outcome to the CTA.
+__device__ __forceinline__ bool cta_wait_mma(uint32_t mbar, uint32_t parity, long long wait_ns, int* flag)
+{
+    if (threadIdx.x == 0) *flag = tc5::mbar_wait_bounded(mbar, parity, wait_ns) ? 0 : 1;
+    __syncthreads();
+    return *flag == 0;
+}
+
+// Stage 1: element e's u as float pairs of this thread's point pairs (lane .x: point 2 pp, .y: 2 pp + 1)
+// and the element's exponent bound (one barrier).
+template <int NX>
+__device__ __forceinline__ int load_u(const double* __restrict__ u, int64_t e, int tid, float2 (&uh)[Oz<NX>::NPR],
+                                      float2 (&ul)[Oz<NX>::NPR], float* red)
+{
+    using C = Oz<NX>;
+    const double2* ue = reinterpret_cast<const double2*>(u + e * C::N3);
+    float mu = 0.f;
+#pragma unroll
+    for (int q = 0; q < C::NPR; q++) {
+        const int pp = tid + kNT * q;
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (pp < C::NPP) {
+            const double2 v = ue[pp];
+            a = split_double(v.x);
+            b = split_double(v.y);
+        }
+        uh[q] = make_float2(a.x, b.x);
+        ul[q] = make_float2(a.y, b.y);
+        mu = fmaxf(mu, fmaxf(fabsf(a.x), fabsf(b.x)));
+    }
+    return exp_bound(block_max(mu, red));
 }
 
 template <int NX>
@@ -299,21 +366,24 @@ __device__ __forceinline__ void issue_phase(uint32_t tmem, uint32_t a_base, uint
     tc5::mma_commit(mbar);
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // arrivals: arrivals the mbarrier expects per phase (1: the commit of the MMAs;
 // 2 never completes, which the self-test uses to make every wait run out).
 template <int NX>
 __global__ void __launch_bounds__(kNT, 2)
-    k_ax_oz(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Gff,
+    k_ax_oz(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Goz,
             const double* __restrict__ u, double* __restrict__ w, long long wait_ns, int arrivals)
 {
     using C = Oz<NX>;
-    constexpr int N2 = C::N2, N3 = C::N3, NPAIR = C::NPAIR;
+    constexpr int N2 = C::N2, N3 = C::N3, NPP = C::NPP, NPR = C::NPR;
     extern __shared__ __align__(128) unsigned char oz_raw[];
-    unsigned char* A = oz_raw;                        // [3][ABYTES] digit rows; between MMAs the exchange X
+    unsigned char* A = oz_raw;                        // [3][ABYTES] digit rows; between MMAs the exchange arrays
     unsigned char* B1 = A + 3 * C::ABYTES;            // phase 1: digits of D
     unsigned char* B2 = B1 + C::BBYTES;               // phase 2: digits of D^T
     OzMisc& M = *reinterpret_cast<OzMisc*>(B2 + C::BBYTES);
-    const float2* X = reinterpret_cast<const float2*>(A);  // phase-1 exchange: [3][N3] float pairs
+    const float4* XA = reinterpret_cast<const float4*>(A);
+    const float2* XS = reinterpret_cast<const float2*>(A + 3 * NPP * 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     // ---- set-up: D's exponent bound, recombination offsets, the B matrices, mbarrier, TMEM
@@ -359,8 +429,10 @@ __global__ void __launch_bounds__(kNT, 2)
             for (int a = 0; a < 8; a++) v[a] = (a < 6 && L - a >= 0 && L - a < 6) ? __fmul_rn(p[L - a], 65536.f) : 0.f;
             const uint4 row = make_uint4(bf16_pair(v[0], v[1]), bf16_pair(v[2], v[3]), bf16_pair(v[4], v[5]),
                                          bf16_pair(v[6], v[7]));
-            *reinterpret_cast<uint4*>(B1 + r * C::BSBO + c * 128 + L * 16) = row;  // n = (o = r, L), K = (l = c, a)
-            *reinterpret_cast<uint4*>(B2 + c * C::BSBO + r * 128 + L * 16) = row;  // n = (o = c, L), K = (l = r, a)
+            // phase 1: output o = r, K chunk l = c; phase 2: o = c, l = r
+            const int n1 = 16 * (r >> 1) + 2 * L + (r & 1), n2 = 16 * (c >> 1) + 2 * L + (c & 1);
+            *reinterpret_cast<uint4*>(B1 + (n1 >> 3) * C::BSBO + c * 128 + (n1 & 7) * 16) = row;
+            *reinterpret_cast<uint4*>(B2 + (n2 >> 3) * C::BSBO + r * 128 + (n2 & 7) * 16) = row;
         }
     }
     if (warp == 0) tc5::tmem_alloc(&M.tmem, kTmemCols);
@@ -371,44 +443,51 @@ __global__ void __launch_bounds__(kNT, 2)
     const uint32_t tmem = M.tmem;
     const uint32_t mbar = tc5::smem_u32(&M.mbar);
     const uint32_t a_base = tc5::smem_u32(A), b1 = tc5::smem_u32(B1), b2 = tc5::smem_u32(B2);
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+    const int m = 32 * (warp & 3) + lane, half = warp >> 2;  // TMEM lane (= line) of this thread
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const int ed = M.ed;
     const float sig1 = M.sig[0], sig2 = M.sig[1];
+    // this thread's point pairs pp = tid + kNT q (points 2 pp, 2 pp + 1: i even, i + 1 on the same lines
+    // of the r direction): byte offsets / 16 of their digit rows in the three A buffers, two to a word
+    uint32_t offw[NPR][3];
+#pragma unroll
+    for (int q = 0; q < NPR; q++) {
+        const int pp = tid + kNT * q;
+        const int p = 2 * (pp < NPP ? pp : 0);
+        const int i = p % NX, j = (p / NX) % NX, k = p / N2;
+        const int o[6] = {a_off<NX>(j + NX * k, i), a_off<NX>(j + NX * k, i + 1),
+                          C::ABYTES + a_off<NX>(i + NX * k, j), C::ABYTES + a_off<NX>(i + 1 + NX * k, j),
+                          2 * C::ABYTES + a_off<NX>(i + NX * j, k), 2 * C::ABYTES + a_off<NX>(i + 1 + NX * j, k)};
+#pragma unroll
+        for (int d = 0; d < 3; d++) offw[q][d] = (uint32_t)(o[2 * d] >> 4) | ((uint32_t)(o[2 * d + 1] >> 4) << 16);
+    }
     uint32_t parity = 0;
+    // stage 1 of the first element: u as float pairs of point pairs, the element's exponent bound
+    float2 uh[NPR], ul[NPR];
+    int eu = 0;
+    if ((int64_t)blockIdx.x < nelt) {
+        for (int q = tid; q < (48 * N3 + 127) / 128; q += kNT)
+            prefetch_l2(reinterpret_cast<const unsigned char*>(Goz + blockIdx.x * (int64_t)NPP * 6) + 128 * q);
+        eu = load_u<NX>(u, blockIdx.x, tid, uh, ul, M.red[0]);
+    }
 
     for (int64_t e = blockIdx.x; e < nelt; e += gridDim.x) {
-        const double* ue = u + e * N3;
-        const float4* Ge = Gff + e * (int64_t)N3 * 3;
-        // ---- stage 1: u as float pairs (lane .x: point p0, .y: p1 = p0 + 128)
-        float2 uh[NPAIR], ul[NPAIR];
-        float mu = 0.f;
-#pragma unroll
-        for (int r = 0; r < NPAIR; r++) {
-            const int p0 = tid + 2 * kNT * r, p1 = p0 + kNT;
-            const float2 a = p0 < N3 ? split_double(ue[p0]) : make_float2(0.f, 0.f);
-            const float2 b = p1 < N3 ? split_double(ue[p1]) : make_float2(0.f, 0.f);
-            uh[r] = make_float2(a.x, b.x);
-            ul[r] = make_float2(a.y, b.y);
-            mu = fmaxf(mu, fmaxf(fabsf(a.x), fabsf(b.x)));
-        }
-        const int eu = exp_bound(block_max(mu, M.red[0]));
+        const float4* Ge = Goz + e * (int64_t)NPP * 6;
+        const int64_t en = e + gridDim.x;  // this CTA's next element
         // ---- stage 2: u's digit rows into the three A buffers
         {
             const float2 su = sp2(pow2f(-eu));
 #pragma unroll
-            for (int r = 0; r < NPAIR; r++) {
-                float2 q[6];
-                digits6(mul2(uh[r], su), mul2(ul[r], su), q);
+            for (int q = 0; q < NPR; q++) {
+                if (tid + kNT * q < NPP) {
+                    float2 dg[6];
+                    digits6(mul2(uh[q], su), mul2(ul[q], su), dg);
+                    uint4 r0, r1;
+                    digit_rows(dg, r0, r1);
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const int p = tid + 2 * kNT * r + kNT * h;
-                    if (p < N3) {
-                        const uint4 row = h ? digit_row(q[0].y, q[1].y, q[2].y, q[3].y, q[4].y, q[5].y)
-                                            : digit_row(q[0].x, q[1].x, q[2].x, q[3].x, q[4].x, q[5].x);
-                        const int i = p % NX, j = (p / NX) % NX, k = p / N2;
-                        *reinterpret_cast<uint4*>(A + a_off<NX>(j + NX * k, i)) = row;
-                        *reinterpret_cast<uint4*>(A + C::ABYTES + a_off<NX>(i + NX * k, j)) = row;
-                        *reinterpret_cast<uint4*>(A + 2 * C::ABYTES + a_off<NX>(i + NX * j, k)) = row;
+                    for (int d = 0; d < 3; d++) {
+                        *reinterpret_cast<uint4*>(A + ((offw[q][d] & 0xFFFFu) << 4)) = r0;
+                        *reinterpret_cast<uint4*>(A + ((offw[q][d] >> 16) << 4)) = r1;
                     }
                 }
             }
@@ -422,74 +501,73 @@ __global__ void __launch_bounds__(kNT, 2)
             if (lane == 0) issue_phase<NX>(tmem, a_base, b1, mbar);
             __syncwarp();
         }
-        bool ok = tc5::mbar_wait_bounded(mbar, parity, wait_ns);
-        if (__syncthreads_or(!ok)) goto timed_out;
+        // while the MMAs run: G of the first point pair into registers, u of the next element into L2
+        float4 g0[6];
+        if (tid < NPP) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) g0[c] = __ldg(Ge + 6 * tid + c);
+        }
+        if (en < nelt)
+            for (int q = tid; q < (8 * N3 + 127) / 128; q += kNT)
+                prefetch_l2(reinterpret_cast<const unsigned char*>(u + en * N3) + 128 * q);
+        if (!cta_wait_mma(mbar, parity, wait_ns, &M.flag[0])) goto timed_out;
         parity ^= 1u;
         tc5::fence_after();
-        // ---- stage 3: levels -> float pairs ur, us, ut in X (the A buffers are free again)
-        readout<NX, false>(lane_addr, sig1, A, tid);
+        // ---- stage 3: levels -> (S, lo) pairs of ur, us, ut in XA (the A buffers are free again)
+        if (half)
+            readout<NX, false, 1>(lane_addr, sig1, A, m);
+        else
+            readout<NX, false, 0>(lane_addr, sig1, A, m);
         tc5::fence_before();
         __syncthreads();
-        // ---- stage 4: (wr, ws, wt) = G (ur, us, ut) in float-float
+        // ---- stage 4: (wr, ws, wt) = G (ur, us, ut) in float-float, renormalised
         {
-            float2 wh[3][NPAIR], wl[3][NPAIR];
+            float2 wh[3][NPR], wl[3][NPR];
             float mw = 0.f;
 #pragma unroll
-            for (int r = 0; r < NPAIR; r++) {
-                const int p0 = tid + 2 * kNT * r, p1 = p0 + kNT;
-                float2 a[3][2];  // [direction][lane]: (hi, lo) of ur, us, ut
-                float4 g[3][2];
+            for (int q = 0; q < NPR; q++) {
+                const int pp = tid + kNT * q;
+                if (pp < NPP) {
+                    float4 x[3], g[6];
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
-                    const int p = h ? p1 : p0;
-                    const bool v = p < N3;
+                    for (int d = 0; d < 3; d++) x[d] = XA[d * NPP + pp];
+#pragma unroll
+                    for (int c = 0; c < 6; c++) g[c] = q == 0 ? g0[c] : __ldg(Ge + 6 * pp + c);
+                    // g[c] = (G_c hi of p, p + 1; G_c lo of p, p + 1); x[d] = (S of p, p + 1; lo of p, p + 1)
+#define OZ_H(v) make_float2((v).x, (v).y)
+#define OZ_L(v) make_float2((v).z, (v).w)
+                    df_dot3_2(OZ_H(g[0]), OZ_L(g[0]), OZ_H(x[0]), OZ_L(x[0]), OZ_H(g[1]), OZ_L(g[1]), OZ_H(x[1]),
+                              OZ_L(x[1]), OZ_H(g[2]), OZ_L(g[2]), OZ_H(x[2]), OZ_L(x[2]), wh[0][q], wl[0][q]);
+                    df_dot3_2(OZ_H(g[1]), OZ_L(g[1]), OZ_H(x[0]), OZ_L(x[0]), OZ_H(g[3]), OZ_L(g[3]), OZ_H(x[1]),
+                              OZ_L(x[1]), OZ_H(g[4]), OZ_L(g[4]), OZ_H(x[2]), OZ_L(x[2]), wh[1][q], wl[1][q]);
+                    df_dot3_2(OZ_H(g[2]), OZ_L(g[2]), OZ_H(x[0]), OZ_L(x[0]), OZ_H(g[4]), OZ_L(g[4]), OZ_H(x[1]),
+                              OZ_L(x[1]), OZ_H(g[5]), OZ_L(g[5]), OZ_H(x[2]), OZ_L(x[2]), wh[2][q], wl[2][q]);
+#undef OZ_H
+#undef OZ_L
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
-                        a[d][h] = v ? X[d * N3 + p] : make_float2(0.f, 0.f);
-                        g[d][h] = v ? __ldg(Ge + 3 * p + d) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        // renormalise: after cancellation among the three products the low part can exceed
+                        // ulp(high), and the digits need |low| <= ulp(high) / 2 to stay within 8 bits
+                        two_sum2(wh[d][q], wl[d][q], wh[d][q], wl[d][q]);
+                        mw = fmaxf(mw, fmaxf(fabsf(wh[d][q].x), fabsf(wh[d][q].y)));
                     }
                 }
-                // G factors g0..g5 as (hi, lo) pairs: g[0] = (g0h, g0l, g1h, g1l), g[1] = (g2, g3), g[2] = (g4, g5)
-                const float2 g0h = make_float2(g[0][0].x, g[0][1].x), g0l = make_float2(g[0][0].y, g[0][1].y);
-                const float2 g1h = make_float2(g[0][0].z, g[0][1].z), g1l = make_float2(g[0][0].w, g[0][1].w);
-                const float2 g2h = make_float2(g[1][0].x, g[1][1].x), g2l = make_float2(g[1][0].y, g[1][1].y);
-                const float2 g3h = make_float2(g[1][0].z, g[1][1].z), g3l = make_float2(g[1][0].w, g[1][1].w);
-                const float2 g4h = make_float2(g[2][0].x, g[2][1].x), g4l = make_float2(g[2][0].y, g[2][1].y);
-                const float2 g5h = make_float2(g[2][0].z, g[2][1].z), g5l = make_float2(g[2][0].w, g[2][1].w);
-                const float2 rh = make_float2(a[0][0].x, a[0][1].x), rl = make_float2(a[0][0].y, a[0][1].y);
-                const float2 sh = make_float2(a[1][0].x, a[1][1].x), sl = make_float2(a[1][0].y, a[1][1].y);
-                const float2 th = make_float2(a[2][0].x, a[2][1].x), tl = make_float2(a[2][0].y, a[2][1].y);
-                df_dot3_2(g0h, g0l, rh, rl, g1h, g1l, sh, sl, g2h, g2l, th, tl, wh[0][r], wl[0][r]);
-                df_dot3_2(g1h, g1l, rh, rl, g3h, g3l, sh, sl, g4h, g4l, th, tl, wh[1][r], wl[1][r]);
-                df_dot3_2(g2h, g2l, rh, rl, g4h, g4l, sh, sl, g5h, g5l, th, tl, wh[2][r], wl[2][r]);
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    // renormalise: after cancellation among the three products the low part can exceed
-                    // ulp(high), and the digits need |low| <= ulp(high) / 2 to stay within 8 bits
-                    two_sum2(wh[d][r], wl[d][r], wh[d][r], wl[d][r]);
-                    mw = fmaxf(mw, fmaxf(fabsf(wh[d][r].x), fabsf(wh[d][r].y)));
-                }
             }
-            const int ew = exp_bound(block_max(mw, M.red[1]));  // after this barrier X is no longer read
+            const int ew = exp_bound(block_max(mw, M.red[1]));  // after this barrier XA is no longer read
+            const int eu_e = eu;  // stage 1 of the next element replaces eu below
             // ---- stage 5: digit rows of wr -> A_r, ws -> A_s, wt -> A_t
             const float2 sw = sp2(pow2f(-ew));
 #pragma unroll
-            for (int r = 0; r < NPAIR; r++) {
+            for (int q = 0; q < NPR; q++) {
+                if (tid + kNT * q < NPP) {
 #pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    float2 q[6];
-                    digits6(mul2(wh[d][r], sw), mul2(wl[d][r], sw), q);
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const int p = tid + 2 * kNT * r + kNT * h;
-                        if (p < N3) {
-                            const uint4 row = h ? digit_row(q[0].y, q[1].y, q[2].y, q[3].y, q[4].y, q[5].y)
-                                                : digit_row(q[0].x, q[1].x, q[2].x, q[3].x, q[4].x, q[5].x);
-                            const int i = p % NX, j = (p / NX) % NX, k = p / N2;
-                            const int row_d = d == 0 ? j + NX * k : d == 1 ? i + NX * k : i + NX * j;
-                            const int chunk = d == 0 ? i : d == 1 ? j : k;
-                            *reinterpret_cast<uint4*>(A + d * C::ABYTES + a_off<NX>(row_d, chunk)) = row;
-                        }
+                    for (int d = 0; d < 3; d++) {
+                        float2 dg[6];
+                        digits6(mul2(wh[d][q], sw), mul2(wl[d][q], sw), dg);
+                        uint4 r0, r1;
+                        digit_rows(dg, r0, r1);
+                        *reinterpret_cast<uint4*>(A + ((offw[q][d] & 0xFFFFu) << 4)) = r0;
+                        *reinterpret_cast<uint4*>(A + ((offw[q][d] >> 16) << 4)) = r1;
                     }
                 }
             }
@@ -502,29 +580,43 @@ __global__ void __launch_bounds__(kNT, 2)
                 if (lane == 0) issue_phase<NX>(tmem, a_base, b2, mbar);
                 __syncwarp();
             }
-            ok = tc5::mbar_wait_bounded(mbar, parity, wait_ns);
-            if (__syncthreads_or(!ok)) goto timed_out;
+            // while the MMAs run: stage 1 of the next element, and its G into L2
+            if (en < nelt) {
+                for (int q = tid; q < (48 * N3 + 127) / 128; q += kNT)
+                    prefetch_l2(reinterpret_cast<const unsigned char*>(Goz + en * (int64_t)NPP * 6) + 128 * q);
+                eu = load_u<NX>(u, en, tid, uh, ul, M.red[0]);
+            }
+            if (!cta_wait_mma(mbar, parity, wait_ns, &M.flag[1])) goto timed_out;
             parity ^= 1u;
             tc5::fence_after();
-            // ---- stage 6: levels -> float pairs of the three direction sums in X
-            readout<NX, true>(lane_addr, sig2, A, tid);
+            // ---- stage 6: levels -> (hi, E, s) of the three directions in XA, XS
+            if (half)
+                readout<NX, true, 1>(lane_addr, sig2, A, m);
+            else
+                readout<NX, true, 0>(lane_addr, sig2, A, m);
             tc5::fence_before();
             __syncthreads();
             // ---- stage 7: w = (his + Es + ss of the three directions) * 2^(eu + ew + 2 ed - 32); the his
             // and the Es sum exactly, TwoSum joins them
-            const int xs = eu + ew + 2 * ed - 32;
-            const float4* X4 = reinterpret_cast<const float4*>(A);
-            double* we = w + e * N3;
-            for (int p = tid; p < N3; p += kNT) {
-                const float4 a = X4[p], b = X4[N3 + p], c = X4[2 * N3 + p];
-                const float H = __fadd_rn(__fadd_rn(a.x, b.x), c.x);
-                const float Es = __fadd_rn(__fadd_rn(a.y, b.y), c.y);
-                const float ss = __fadd_rn(__fadd_rn(a.z, b.z), c.z);
-                const float S = __fadd_rn(H, Es);
-                const float bb = __fsub_rn(S, H);
-                const float T = __fadd_rn(__fsub_rn(H, __fsub_rn(S, bb)), __fsub_rn(Es, bb));
-                we[p] = __dadd_rn(widen_scaled(S, xs), widen_scaled(__fadd_rn(T, ss), xs));
+            const int xs = eu_e + ew + 2 * ed - 32;
+            double2* we = reinterpret_cast<double2*>(w + e * N3);
+#pragma unroll
+            for (int q = 0; q < NPR; q++) {
+                const int pp = tid + kNT * q;
+                if (pp < NPP) {
+                    const float4 a = XA[pp], b = XA[NPP + pp], c = XA[2 * NPP + pp];
+                    const float2 sa = XS[pp], sb = XS[NPP + pp], sc = XS[2 * NPP + pp];
+                    const float2 H = add2(add2(make_float2(a.x, a.y), make_float2(b.x, b.y)), make_float2(c.x, c.y));
+                    const float2 Es = add2(add2(make_float2(a.z, a.w), make_float2(b.z, b.w)), make_float2(c.z, c.w));
+                    const float2 ss = add2(add2(sa, sb), sc);
+                    float2 S, T;
+                    two_sum2(H, Es, S, T);
+                    const float2 lo = add2(T, ss);
+                    we[pp] = make_double2(__dadd_rn(widen_scaled(S.x, xs), widen_scaled(lo.x, xs)),
+                                          __dadd_rn(widen_scaled(S.y, xs), widen_scaled(lo.y, xs)));
+                }
             }
+            __syncthreads();  // the exchange arrays are read before the next element's digits overwrite them
         }
         continue;
     timed_out:
@@ -533,13 +625,26 @@ __global__ void __launch_bounds__(kNT, 2)
         if (tid == 0) atomicExch(&g_ax_oz_timeout, 1);
         for (int64_t e2 = e; e2 < nelt; e2 += gridDim.x)
             for (int p = tid; p < N3; p += kNT) w[e2 * N3 + p] = __longlong_as_double(0x7FF8000000000000LL);
-        tc5::mbar_wait_bounded(mbar, parity, wait_ns);
+        if (tid == 0) tc5::mbar_wait_bounded(mbar, parity, wait_ns);
+        __syncthreads();
         break;
     }
     tc5::fence_before();
     __syncthreads();
     tc5::fence_after();
     if (warp == 0) tc5::tmem_dealloc(tmem, kTmemCols);
+}
+
+// G (FP64, [e][p][6]) -> pairs of points interleaved: Goz[e][pp][c] = (hi of G_c at
+// points 2 pp and 2 pp + 1, lo at the same two points), split as split_double does.
+__global__ void k_g_to_oz(int64_t nq, const double* __restrict__ G, float4* __restrict__ Goz)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pp = q / 6;
+        const int c = (int)(q - 6 * pp);
+        const float2 a = split_double(G[12 * pp + c]), b = split_double(G[12 * pp + 6 + c]);
+        Goz[q] = make_float4(a.x, b.x, a.y, b.y);
+    }
 }
 
 int oz_sm_count()
@@ -557,7 +662,7 @@ int oz_sm_count()
 }
 
 template <int NX>
-nek_status launch_oz_nx(int64_t nelt, const double* D, const float* Gff, const double* u, double* w,
+nek_status launch_oz_nx(int64_t nelt, const double* D, const float* Goz, const double* u, double* w,
                         cudaStream_t s, long long wait_ns, int arrivals)
 {
     static std::atomic<uint64_t> configured{0};
@@ -566,7 +671,7 @@ nek_status launch_oz_nx(int64_t nelt, const double* D, const float* Gff, const d
     if (st != NEK_OK) return st;
     const int64_t cap = 2 * (int64_t)oz_sm_count();
     const int grid = static_cast<int>(nelt < cap ? nelt : cap);
-    k_ax_oz<NX><<<grid, kNT, smem, s>>>(nelt, D, reinterpret_cast<const float4*>(Gff), u, w, wait_ns, arrivals);
+    k_ax_oz<NX><<<grid, kNT, smem, s>>>(nelt, D, reinterpret_cast<const float4*>(Goz), u, w, wait_ns, arrivals);
     return check_launch();
 }
 
@@ -574,15 +679,15 @@ nek_status launch_oz_nx(int64_t nelt, const double* D, const float* Gff, const d
 
 bool ax_oz_supported(int nx) { return nx >= 2 && nx <= 10 && nx % 2 == 0; }
 
-nek_status launch_ax_oz_ex(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+nek_status launch_ax_oz_ex(int64_t nelt, int nx, const double* D, const float* Goz, const double* u, double* w,
                            cudaStream_t s, long long wait_ns, int arrivals)
 {
     switch (nx) {
-        case 2: return launch_oz_nx<2>(nelt, D, Gff, u, w, s, wait_ns, arrivals);
-        case 4: return launch_oz_nx<4>(nelt, D, Gff, u, w, s, wait_ns, arrivals);
-        case 6: return launch_oz_nx<6>(nelt, D, Gff, u, w, s, wait_ns, arrivals);
-        case 8: return launch_oz_nx<8>(nelt, D, Gff, u, w, s, wait_ns, arrivals);
-        case 10: return launch_oz_nx<10>(nelt, D, Gff, u, w, s, wait_ns, arrivals);
+        case 2: return launch_oz_nx<2>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
+        case 4: return launch_oz_nx<4>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
+        case 6: return launch_oz_nx<6>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
+        case 8: return launch_oz_nx<8>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
+        case 10: return launch_oz_nx<10>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
 }
@@ -604,18 +709,33 @@ using namespace nek;
 
 extern "C" {
 
-nek_status nek_ax_oz(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
+nek_status nek_geom_oz(int64_t nelt, int nx, const double* G, float* Goz, void* stream)
+{
+    if (!ax_oz_supported(nx)) return NEK_ERR_UNSUPPORTED_NX;
+    if (nelt < 0) return NEK_ERR_INVALID_ARG;
+    if (nelt == 0) return NEK_OK;
+    if (!G || !Goz || !is_aligned(G, 8) || !is_aligned(Goz, 16)) return NEK_ERR_INVALID_ARG;
+    const int64_t npts = nelt * (int64_t)nx * nx * nx;
+    if (ranges_overlap(G, sizeof(double) * 6 * npts, Goz, sizeof(float) * 12 * npts)) return NEK_ERR_INVALID_ARG;
+    const int64_t nq = npts / 2 * 6;
+    const int64_t nb = (nq + 255) / 256;
+    const int blocks = static_cast<int>(nb < 152 * 32 ? nb : 152 * 32);
+    k_g_to_oz<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(nq, G, reinterpret_cast<float4*>(Goz));
+    return check_launch();
+}
+
+nek_status nek_ax_oz(int64_t nelt, int nx, const double* D, const float* Goz, const double* u, double* w,
                      void* stream)
 {
     if (!ax_oz_supported(nx)) return NEK_ERR_UNSUPPORTED_NX;
     if (nelt < 0) return NEK_ERR_INVALID_ARG;
     if (nelt == 0) return NEK_OK;
-    if (!D || !Gff || !u || !w || !is_aligned(D, 8) || !is_aligned(Gff, 16) || !is_aligned(u, 8) ||
-        !is_aligned(w, 8))
+    if (!D || !Goz || !u || !w || !is_aligned(D, 8) || !is_aligned(Goz, 16) || !is_aligned(u, 16) ||
+        !is_aligned(w, 16))
         return NEK_ERR_INVALID_ARG;
     const int64_t npts = nelt * (int64_t)nx * nx * nx;
     if (ranges_overlap(u, sizeof(double) * npts, w, sizeof(double) * npts)) return NEK_ERR_INVALID_ARG;
-    return launch_ax_oz_ex(nelt, nx, D, Gff, u, w, static_cast<cudaStream_t>(stream), kWaitNs, 1);
+    return launch_ax_oz_ex(nelt, nx, D, Goz, u, w, static_cast<cudaStream_t>(stream), kWaitNs, 1);
 }
 
 nek_status nek_ax_oz_selftest(int force_timeout, int64_t wait_us, int* timed_out)

@@ -114,6 +114,7 @@ _SIGS = {
     "nek_net_apply_bf16_mma": ([_I64, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_net_tc_selftest": ([_I, _I64, ctypes.POINTER(_I)], _I),
     "nek_ax_oz": ([_I64, _I, _P, _P, _P, _P, _P], _I),
+    "nek_geom_oz": ([_I64, _I, _P, _P, _P], _I),
     "nek_ax_oz_selftest": ([_I, _I64, ctypes.POINTER(_I)], _I),
     "nek_net_train_workspace_bytes": ([_I], ctypes.c_size_t),
     "nek_net_forward_batch": ([_I, _P, _P, _P, _P, _P], _I),
@@ -238,9 +239,14 @@ def ax_ff(nelt, nx, D, Gff, u, w, stream=None):
     _check("nek_ax_ff", load().nek_ax_ff(nelt, nx, _ptr(D), _ptr(Gff), _ptr(u), _ptr(w), _stream(stream)))
 
 
-def ax_oz(nelt, nx, D, Gff, u, w, stream=None):
+def geom_oz(nelt, nx, G, Goz, stream=None):
+    """G split into float pairs, two adjacent points interleaved (the layout nek_ax_oz reads)."""
+    _check("nek_geom_oz", load().nek_geom_oz(nelt, nx, _ptr(G), _ptr(Goz), _stream(stream)))
+
+
+def ax_oz(nelt, nx, D, Goz, u, w, stream=None):
     """w = AX u to FP64 accuracy with the contractions on the tensor cores (BF16 digits)."""
-    _check("nek_ax_oz", load().nek_ax_oz(nelt, nx, _ptr(D), _ptr(Gff), _ptr(u), _ptr(w), _stream(stream)))
+    _check("nek_ax_oz", load().nek_ax_oz(nelt, nx, _ptr(D), _ptr(Goz), _ptr(u), _ptr(w), _stream(stream)))
 
 
 def ax_oz_selftest(force_timeout, wait_us):

@@ -30,6 +30,7 @@ class DeviceProblem:
         self.gs = nekax.GsPlan(self.nelt, self.nx, mesh.glo_num)
         self.mask = torch.from_numpy(np.ascontiguousarray(mesh.mask)).to(self.device)
         self.Gff = None
+        self.Goz = None
         self.minv = None
         if build_minv:
             self.minv = torch.empty((self.nelt, self.nx ** 3), dtype=torch.float64, device=self.device)
@@ -50,8 +51,17 @@ class DeviceProblem:
     def ax_ff(self, u, w, stream=None):
         nekax.ax_ff(self.nelt, self.nx, self.D, self.prepare_ff(), u, w, stream)
 
+    def prepare_oz(self):
+        """Split G into the pair-interleaved float-pair layout used by nek_ax_oz (48 B per point)."""
+        import torch
+
+        if self.Goz is None:
+            self.Goz = torch.empty((self.nelt, self.nx ** 3, 12), dtype=torch.float32, device=self.device)
+            nekax.geom_oz(self.nelt, self.nx, self.G, self.Goz)
+        return self.Goz
+
     def ax_oz(self, u, w, stream=None):
-        nekax.ax_oz(self.nelt, self.nx, self.D, self.prepare_ff(), u, w, stream)
+        nekax.ax_oz(self.nelt, self.nx, self.D, self.prepare_oz(), u, w, stream)
 
     def cg(self, f, x, tol=1e-8, max_iter=1000, workspace=None, check_every=1, time_ax=False, stream=None,
            ax_impl=nekax.AX_FP64):

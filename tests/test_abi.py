@@ -80,8 +80,13 @@ def test_ax_oz_rejects_bad_arguments_before_launch(lib):
     assert L.nek_ax_oz(4, 8, None, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
     assert L.nek_ax_oz(4, 8, A16, None, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
     assert L.nek_ax_oz(4, 8, A16, A16 + 8, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # Gff misaligned
-    assert L.nek_ax_oz(4, 8, A16, A16, A16 + 4, A16 * 2, None) == nekax.ERR_INVALID_ARG  # u misaligned
-    assert L.nek_ax_oz(4, 8, A16, A16, A16, A16 * 2 + 4, None) == nekax.ERR_INVALID_ARG  # w misaligned
+    assert L.nek_ax_oz(4, 8, A16, A16, A16 + 8, A16 * 2, None) == nekax.ERR_INVALID_ARG  # u not 16-byte aligned
+    assert L.nek_ax_oz(4, 8, A16, A16, A16, A16 * 2 + 8, None) == nekax.ERR_INVALID_ARG  # w not 16-byte aligned
+    assert L.nek_geom_oz(4, 7, A16, A16 * 2, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_geom_oz(-1, 8, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_geom_oz(0, 8, None, None, None) == nekax.OK
+    assert L.nek_geom_oz(4, 8, A16, A16 * 2 + 8, None) == nekax.ERR_INVALID_ARG  # Goz misaligned
+    assert L.nek_geom_oz(4, 8, A16, A16 + 64, None) == nekax.ERR_INVALID_ARG  # overlap
     assert L.nek_ax_oz(4, 8, A16, A16, A16, A16 + 4096, None) == nekax.ERR_INVALID_ARG  # u and w overlap
     t = ctypes.c_int(0)
     assert L.nek_ax_oz_selftest(1, 0, ctypes.byref(t)) == nekax.ERR_INVALID_ARG

@@ -44,10 +44,10 @@ def _case(nx, nelt, seed, perturb=0.2):
 
 def _run(nx, D, G, u):
     nelt = u.shape[0]
-    Gff = torch.empty((nelt, nx ** 3, 12), dtype=torch.float32, device=DEV)
-    nekax.geom_ff(nelt, nx, _t(G), Gff)
+    Goz = torch.empty((nelt, nx ** 3, 12), dtype=torch.float32, device=DEV)
+    nekax.geom_oz(nelt, nx, _t(G), Goz)
     wd = torch.full((nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
-    nekax.ax_oz(nelt, nx, _t(D), Gff, _t(u), wd)
+    nekax.ax_oz(nelt, nx, _t(D), Goz, _t(u), wd)
     torch.cuda.synchronize()
     return wd.cpu().numpy()
 
@@ -123,6 +123,21 @@ def test_ax_oz_full_size_sampled():
     xi, rho, D = ref.gll(nx)
     G = ref.geom(mesh.corners[sample], nx, xi, rho)
     assert _rel(wn[sample], ref.ax(D, G, u[sample])) <= TOL_AX
+
+
+def test_geom_oz_is_the_float_float_split_interleaved_by_point_pairs():
+    nx = 6
+    mesh = inputs.box_mesh(3, 2, 1, nx, perturb=0.2, seed=4)
+    G = ref.geom(mesh.corners, nx)
+    Gd = _t(G)
+    Gff = torch.empty((mesh.nelt, nx ** 3, 12), dtype=torch.float32, device=DEV)
+    Goz = torch.empty_like(Gff)
+    nekax.geom_ff(mesh.nelt, nx, Gd, Gff)
+    nekax.geom_oz(mesh.nelt, nx, Gd, Goz)
+    torch.cuda.synchronize()
+    f = Gff.cpu().numpy().reshape(mesh.nelt, nx ** 3 // 2, 2, 6, 2)  # [e][pair][point][c][hi/lo]
+    z = Goz.cpu().numpy().reshape(mesh.nelt, nx ** 3 // 2, 6, 2, 2)  # [e][pair][c][hi/lo][point]
+    assert np.array_equal(z, f.transpose(0, 1, 3, 4, 2))
 
 
 def test_ax_oz_bounded_wait_runs_out_and_reports():
