@@ -350,6 +350,7 @@ __device__ __forceinline__ int load_u(const double* __restrict__ u, int64_t e, i
     return exp_bound(block_max(mu, red));
 }
 
+// Issued by the whole of warp 0 (converged); lane 0 alone issues each MMA and the commit.
 template <int NX>
 __device__ __forceinline__ void issue_phase(uint32_t tmem, uint32_t a_base, uint32_t b_base, uint32_t mbar)
 {
@@ -360,10 +361,10 @@ __device__ __forceinline__ void issue_phase(uint32_t tmem, uint32_t a_base, uint
         const uint64_t bd = tc5::smem_desc(b_base, 128, C::BSBO);
 #pragma unroll
         for (int s = 0; s < C::KSTEP; s++)
-            tc5::mma_bf16(tmem + (uint32_t)(d * C::NCOL), ad + (uint64_t)((2 * s * kLbo) >> 4),
-                          bd + (uint64_t)((2 * s * 128) >> 4), C::IDESC, s > 0 ? 1u : 0u);
+            tc5::mma_bf16_lane0(tmem + (uint32_t)(d * C::NCOL), ad + (uint64_t)((2 * s * kLbo) >> 4),
+                                bd + (uint64_t)((2 * s * 128) >> 4), C::IDESC, s > 0 ? 1u : 0u);
     }
-    tc5::mma_commit(mbar);
+    tc5::mma_commit_lane0(mbar);
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
@@ -498,7 +499,7 @@ __global__ void __launch_bounds__(kNT, 2)
         __syncthreads();
         tc5::fence_after();
         if (warp == 0) {
-            if (lane == 0) issue_phase<NX>(tmem, a_base, b1, mbar);
+            issue_phase<NX>(tmem, a_base, b1, mbar);
             __syncwarp();
         }
         // while the MMAs run: G of the first point pair into registers, u of the next element into L2
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(kNT, 2)
             __syncthreads();
             tc5::fence_after();
             if (warp == 0) {
-                if (lane == 0) issue_phase<NX>(tmem, a_base, b2, mbar);
+                issue_phase<NX>(tmem, a_base, b2, mbar);
                 __syncwarp();
             }
             // while the MMAs run: stage 1 of the next element, and its G into L2

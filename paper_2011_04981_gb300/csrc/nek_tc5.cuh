@@ -47,6 +47,31 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
+// The same MMA issued by lane 0 of a converged warp: every lane computes the
+// (warp-uniform) operands and executes the instruction, lane 0's predicate
+// alone is true, so the operands can stay in the warp's uniform registers.
+__device__ __forceinline__ void mma_bf16_lane0(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                               uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred pe, pa;\n\t.reg .u32 ln;\n\t"
+        "mov.u32 ln, %%laneid;\n\t"
+        "setp.eq.u32 pe, ln, 0;\n\t"
+        "setp.ne.b32 pa, %4, 0;\n\t"
+        "@pe tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+// tcgen05.commit by lane 0 of a converged warp (the lane that issued the MMAs above).
+__device__ __forceinline__ void mma_commit_lane0(uint32_t mbar)
+{
+    asm volatile(
+        "{\n\t.reg .pred pe;\n\t.reg .u32 ln;\n\t"
+        "mov.u32 ln, %%laneid;\n\t"
+        "setp.eq.u32 pe, ln, 0;\n\t"
+        "@pe tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(mbar)
+        : "memory");
+}
+
 // The mbarrier gets one arrival once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint32_t mbar)
 {
