@@ -55,8 +55,10 @@ typedef enum {
 typedef enum {
     NEK_AX_FP64 = 0,      /* nek_ax: native FP64 */
     NEK_AX_FF = 1,        /* nek_ax_ff: FP64-accurate float-float on the FP32 pipes; needs Gff */
-    NEK_AX_FF_ENERGY = 2  /* nek_ax_ff's element-energy form (nek_ax_ff_energy and the solves):
+    NEK_AX_FF_ENERGY = 2, /* nek_ax_ff's element-energy form (nek_ax_ff_energy and the solves):
                              for nek_set_ax_epb / nek_get_ax_epb only */
+    NEK_AX_OZ = 3         /* nek_ax_oz: FP64-accurate with the contractions on the tensor cores; needs
+                             the split of nek_geom_oz; even nx up to 10 */
 } nek_ax_impl;
 
 /* Opaque gather-scatter plan (see nek_gs_create). */
@@ -539,7 +541,9 @@ typedef struct {
     int ax_launches;     /* out: number of AX launches */
     int kernel_launches; /* out: kernels this call enqueued */
     int ax_impl;         /* nek_ax_impl; default NEK_AX_FP64 */
-    const float* Gff;    /* device, from nek_geom_ff, required for NEK_AX_FF */
+    const float* Gff;    /* device, 16-byte aligned: from nek_geom_ff, required for NEK_AX_FF; from
+                            nek_geom_oz, required for NEK_AX_OZ (which also needs minv, when given,
+                            16-byte aligned) */
 } nek_cg_opts;
 
 nek_status nek_cg_solve(const nek_gs* gs, int64_t nelt, int nx, const double* D, const double* G,

@@ -85,6 +85,16 @@ constexpr long long kWaitNs = 2000000000LL;
 
 __device__ int g_ax_oz_timeout = 0;    // set by a bounded wait that ran out
 
+// Modes: the plain operator; with element energies u_e . w_e; with the CG direction update on the input
+// (x += alpha p, p = minv r + beta p, the operator applied to the new p) and the energies p_e . w_e.
+constexpr int kOzPlain = 0, kOzEnergy = 1, kOzDir = 2;
+
+// The direction update's scalars, read once per launch.
+struct OzDir {
+    double alpha, beta;
+    bool dx, dp;  // x is updated; p is replaced
+};
+
 template <int NX>
 struct Oz {
     static_assert(NX % 2 == 0 && NX >= 2 && NX <= 10, "even nx up to 10");
@@ -110,6 +120,7 @@ struct OzMisc {
     float red[2][8];   // per-warp maxima: [0] |u|, [1] |wr|, |ws|, |wt|
     int flag[2];       // a wait of phase 1 / phase 2 ran out
     double rs[10], cs[10];  // absolute row / column sums of D
+    double esum[8];         // per-warp parts of an element's energy
 };
 
 template <int NX>
@@ -325,23 +336,57 @@ __device__ __forceinline__ bool cta_wait_mma(uint32_t mbar, uint32_t parity, lon
     return *flag == 0;
 }
 
-// Stage 1: element e's u as float pairs of this thread's point pairs (lane .x: point 2 pp, .y: 2 pp + 1)
-// and the element's exponent bound (one barrier).
-template <int NX>
+// Stage 1: element e's input as float pairs of this thread's point pairs (lane .x: point 2 pp, .y: 2 pp + 1)
+// and the element's exponent bound (one barrier).  With the direction update the input is the new p: each
+// point does x += alpha p (old p) and p = minv r + beta p with the operations of the CG's own update, and
+// writes both back.
+template <int NX, int MODE>
 __device__ __forceinline__ int load_u(const double* __restrict__ u, int64_t e, int tid, float2 (&uh)[Oz<NX>::NPR],
-                                      float2 (&ul)[Oz<NX>::NPR], float* red)
+                                      float2 (&ul)[Oz<NX>::NPR], float* red, const DirUpdate& dir, const OzDir& dv)
 {
     using C = Oz<NX>;
-    const double2* ue = reinterpret_cast<const double2*>(u + e * C::N3);
+    constexpr int NPR = C::NPR;
+    const int64_t first = e * C::N3;
+    double2 v[NPR];
+    if constexpr (MODE == kOzDir) {
+        // all loads before the first store (the arrays may alias as far as the compiler knows)
+        double2* p2 = reinterpret_cast<double2*>(dir.p + first);
+        double2* x2 = reinterpret_cast<double2*>(dir.x + first);
+        double2 rv[NPR], mv[NPR], xv[NPR];
+#pragma unroll
+        for (int q = 0; q < NPR; q++) {
+            const int pp = tid + kNT * q < C::NPP ? tid + kNT * q : 0;
+            v[q] = p2[pp];
+            rv[q] = reinterpret_cast<const double2*>(dir.r + first)[pp];
+            mv[q] = reinterpret_cast<const double2*>(dir.minv + first)[pp];
+            xv[q] = dv.dx ? x2[pp] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int q = 0; q < NPR; q++) {
+            const int pp = tid + kNT * q;
+            if (pp < C::NPP) {
+                if (dv.dx) x2[pp] = make_double2(fma(dv.alpha, v[q].x, xv[q].x), fma(dv.alpha, v[q].y, xv[q].y));
+                if (dv.dp) {
+                    v[q] = make_double2(fma(dv.beta, v[q].x, mv[q].x * rv[q].x),
+                                        fma(dv.beta, v[q].y, mv[q].y * rv[q].y));
+                    p2[pp] = v[q];
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NPR; q++) {
+            const int pp = tid + kNT * q < C::NPP ? tid + kNT * q : 0;
+            v[q] = __ldg(reinterpret_cast<const double2*>(u + first) + pp);
+        }
+    }
     float mu = 0.f;
 #pragma unroll
-    for (int q = 0; q < C::NPR; q++) {
-        const int pp = tid + kNT * q;
+    for (int q = 0; q < NPR; q++) {
         float2 a = make_float2(0.f, 0.f), b = a;
-        if (pp < C::NPP) {
-            const double2 v = ue[pp];
-            a = split_double(v.x);
-            b = split_double(v.y);
+        if (tid + kNT * q < C::NPP) {
+            a = split_double(v[q].x);
+            b = split_double(v[q].y);
         }
         uh[q] = make_float2(a.x, b.x);
         ul[q] = make_float2(a.y, b.y);
@@ -371,10 +416,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 
 // arrivals: arrivals the mbarrier expects per phase (1: the commit of the MMAs;
 // 2 never completes, which the self-test uses to make every wait run out).
-template <int NX>
+template <int NX, int MODE>
 __global__ void __launch_bounds__(kNT, 2)
     k_ax_oz(int64_t nelt, const double* __restrict__ D, const float4* __restrict__ Goz,
-            const double* __restrict__ u, double* __restrict__ w, long long wait_ns, int arrivals)
+            const double* __restrict__ u, double* __restrict__ w, double* __restrict__ edot, DirUpdate dir,
+            long long wait_ns, int arrivals)
 {
     using C = Oz<NX>;
     constexpr int N2 = C::N2, N3 = C::N3, NPP = C::NPP, NPR = C::NPR;
@@ -448,6 +494,13 @@ __global__ void __launch_bounds__(kNT, 2)
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     const int ed = M.ed;
     const float sig1 = M.sig[0], sig2 = M.sig[1];
+    OzDir dv{0.0, 0.0, false, false};
+    if constexpr (MODE == kOzDir) {
+        dv.alpha = dir.sc->alpha;
+        dv.beta = dir.sc->beta;
+        dv.dx = dir.sc->xpend != 0;
+        dv.dp = !(dir.sc->done || dir.sc->status != NEK_OK);
+    }
     // this thread's point pairs pp = tid + kNT q (points 2 pp, 2 pp + 1: i even, i + 1 on the same lines
     // of the r direction): byte offsets / 16 of their digit rows in the three A buffers, two to a word
     uint32_t offw[NPR][3];
@@ -469,7 +522,7 @@ __global__ void __launch_bounds__(kNT, 2)
     if ((int64_t)blockIdx.x < nelt) {
         for (int q = tid; q < (48 * N3 + 127) / 128; q += kNT)
             prefetch_l2(reinterpret_cast<const unsigned char*>(Goz + blockIdx.x * (int64_t)NPP * 6) + 128 * q);
-        eu = load_u<NX>(u, blockIdx.x, tid, uh, ul, M.red[0]);
+        eu = load_u<NX, MODE>(u, blockIdx.x, tid, uh, ul, M.red[0], dir, dv);
     }
 
     for (int64_t e = blockIdx.x; e < nelt; e += gridDim.x) {
@@ -508,9 +561,17 @@ __global__ void __launch_bounds__(kNT, 2)
 #pragma unroll
             for (int c = 0; c < 6; c++) g0[c] = __ldg(Ge + 6 * tid + c);
         }
-        if (en < nelt)
-            for (int q = tid; q < (8 * N3 + 127) / 128; q += kNT)
-                prefetch_l2(reinterpret_cast<const unsigned char*>(u + en * N3) + 128 * q);
+        if (en < nelt) {
+            const double* nxt = MODE == kOzDir ? dir.p : u;
+            for (int q = tid; q < (8 * N3 + 127) / 128; q += kNT) {
+                prefetch_l2(reinterpret_cast<const unsigned char*>(nxt + en * N3) + 128 * q);
+                if constexpr (MODE == kOzDir) {
+                    prefetch_l2(reinterpret_cast<const unsigned char*>(dir.r + en * N3) + 128 * q);
+                    prefetch_l2(reinterpret_cast<const unsigned char*>(dir.minv + en * N3) + 128 * q);
+                    if (dv.dx) prefetch_l2(reinterpret_cast<const unsigned char*>(dir.x + en * N3) + 128 * q);
+                }
+            }
+        }
         if (!cta_wait_mma(mbar, parity, wait_ns, &M.flag[0])) goto timed_out;
         parity ^= 1u;
         tc5::fence_after();
@@ -585,7 +646,7 @@ __global__ void __launch_bounds__(kNT, 2)
             if (en < nelt) {
                 for (int q = tid; q < (48 * N3 + 127) / 128; q += kNT)
                     prefetch_l2(reinterpret_cast<const unsigned char*>(Goz + en * (int64_t)NPP * 6) + 128 * q);
-                eu = load_u<NX>(u, en, tid, uh, ul, M.red[0]);
+                eu = load_u<NX, MODE>(u, en, tid, uh, ul, M.red[0], dir, dv);
             }
             if (!cta_wait_mma(mbar, parity, wait_ns, &M.flag[1])) goto timed_out;
             parity ^= 1u;
@@ -601,6 +662,7 @@ __global__ void __launch_bounds__(kNT, 2)
             // and the Es sum exactly, TwoSum joins them
             const int xs = eu_e + ew + 2 * ed - 32;
             double2* we = reinterpret_cast<double2*>(w + e * N3);
+            double energy = 0.0;  // this thread's part of the element's input . w, in a fixed order
 #pragma unroll
             for (int q = 0; q < NPR; q++) {
                 const int pp = tid + kNT * q;
@@ -613,11 +675,32 @@ __global__ void __launch_bounds__(kNT, 2)
                     float2 S, T;
                     two_sum2(H, Es, S, T);
                     const float2 lo = add2(T, ss);
-                    we[pp] = make_double2(__dadd_rn(widen_scaled(S.x, xs), widen_scaled(lo.x, xs)),
-                                          __dadd_rn(widen_scaled(S.y, xs), widen_scaled(lo.y, xs)));
+                    const double2 wv = make_double2(__dadd_rn(widen_scaled(S.x, xs), widen_scaled(lo.x, xs)),
+                                                    __dadd_rn(widen_scaled(S.y, xs), widen_scaled(lo.y, xs)));
+                    we[pp] = wv;
+                    if constexpr (MODE != kOzPlain) {
+                        // the input at the two points: u, or the p this thread wrote in stage 1
+                        const double2 iv = MODE == kOzDir ? reinterpret_cast<const double2*>(dir.p + e * N3)[pp]
+                                                          : __ldg(reinterpret_cast<const double2*>(u + e * N3) + pp);
+                        energy = fma(iv.x, wv.x, energy);
+                        energy = fma(iv.y, wv.y, energy);
+                    }
                 }
             }
+            if constexpr (MODE != kOzPlain) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) energy += __shfl_xor_sync(0xFFFFFFFFu, energy, o);
+                if (lane == 0) M.esum[warp] = energy;
+            }
             __syncthreads();  // the exchange arrays are read before the next element's digits overwrite them
+            if constexpr (MODE != kOzPlain) {
+                if (tid == 0) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int q = 0; q < kNT / 32; q++) t += M.esum[q];
+                    edot[e] = t;
+                }
+            }
         }
         continue;
     timed_out:
@@ -662,18 +745,29 @@ int oz_sm_count()
     return n;
 }
 
-template <int NX>
-nek_status launch_oz_nx(int64_t nelt, const double* D, const float* Goz, const double* u, double* w,
-                        cudaStream_t s, long long wait_ns, int arrivals)
+template <int NX, int MODE>
+nek_status launch_oz_mode(int64_t nelt, const double* D, const float* Goz, const double* u, double* w, double* edot,
+                          const DirUpdate& dir, cudaStream_t s, long long wait_ns, int arrivals)
 {
     static std::atomic<uint64_t> configured{0};
     constexpr size_t smem = oz_smem_bytes<NX>();
-    nek_status st = ensure_dyn_smem(k_ax_oz<NX>, smem, configured);
+    nek_status st = ensure_dyn_smem(k_ax_oz<NX, MODE>, smem, configured);
     if (st != NEK_OK) return st;
     const int64_t cap = 2 * (int64_t)oz_sm_count();
     const int grid = static_cast<int>(nelt < cap ? nelt : cap);
-    k_ax_oz<NX><<<grid, kNT, smem, s>>>(nelt, D, reinterpret_cast<const float4*>(Goz), u, w, wait_ns, arrivals);
+    k_ax_oz<NX, MODE><<<grid, kNT, smem, s>>>(nelt, D, reinterpret_cast<const float4*>(Goz), u, w, edot, dir, wait_ns,
+                                              arrivals);
     return check_launch();
+}
+
+template <int NX>
+nek_status launch_oz_nx(int64_t nelt, const double* D, const float* Goz, const double* u, double* w, double* edot,
+                        const DirUpdate* dir, cudaStream_t s, long long wait_ns, int arrivals)
+{
+    if (dir) return launch_oz_mode<NX, kOzDir>(nelt, D, Goz, u, w, edot, *dir, s, wait_ns, arrivals);
+    const DirUpdate none{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (edot) return launch_oz_mode<NX, kOzEnergy>(nelt, D, Goz, u, w, edot, none, s, wait_ns, arrivals);
+    return launch_oz_mode<NX, kOzPlain>(nelt, D, Goz, u, w, nullptr, none, s, wait_ns, arrivals);
 }
 
 }  // namespace
@@ -681,16 +775,22 @@ nek_status launch_oz_nx(int64_t nelt, const double* D, const float* Goz, const d
 bool ax_oz_supported(int nx) { return nx >= 2 && nx <= 10 && nx % 2 == 0; }
 
 nek_status launch_ax_oz_ex(int64_t nelt, int nx, const double* D, const float* Goz, const double* u, double* w,
-                           cudaStream_t s, long long wait_ns, int arrivals)
+                           cudaStream_t s, long long wait_ns, int arrivals, double* edot, const DirUpdate* dir)
 {
     switch (nx) {
-        case 2: return launch_oz_nx<2>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
-        case 4: return launch_oz_nx<4>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
-        case 6: return launch_oz_nx<6>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
-        case 8: return launch_oz_nx<8>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
-        case 10: return launch_oz_nx<10>(nelt, D, Goz, u, w, s, wait_ns, arrivals);
+        case 2: return launch_oz_nx<2>(nelt, D, Goz, u, w, edot, dir, s, wait_ns, arrivals);
+        case 4: return launch_oz_nx<4>(nelt, D, Goz, u, w, edot, dir, s, wait_ns, arrivals);
+        case 6: return launch_oz_nx<6>(nelt, D, Goz, u, w, edot, dir, s, wait_ns, arrivals);
+        case 8: return launch_oz_nx<8>(nelt, D, Goz, u, w, edot, dir, s, wait_ns, arrivals);
+        case 10: return launch_oz_nx<10>(nelt, D, Goz, u, w, edot, dir, s, wait_ns, arrivals);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
+}
+
+nek_status launch_ax_oz(int64_t nelt, int nx, const double* D, const float* Goz, const double* u, double* w,
+                        cudaStream_t s, double* edot, const DirUpdate* dir)
+{
+    return launch_ax_oz_ex(nelt, nx, D, Goz, u, w, s, kWaitNs, 1, edot, dir);
 }
 
 // Reads and clears the flag that a bounded wait of the kernel ran out (synchronous).
@@ -736,7 +836,7 @@ nek_status nek_ax_oz(int64_t nelt, int nx, const double* D, const float* Goz, co
         return NEK_ERR_INVALID_ARG;
     const int64_t npts = nelt * (int64_t)nx * nx * nx;
     if (ranges_overlap(u, sizeof(double) * npts, w, sizeof(double) * npts)) return NEK_ERR_INVALID_ARG;
-    return launch_ax_oz_ex(nelt, nx, D, Goz, u, w, static_cast<cudaStream_t>(stream), kWaitNs, 1);
+    return launch_ax_oz(nelt, nx, D, Goz, u, w, static_cast<cudaStream_t>(stream), nullptr, nullptr);
 }
 
 nek_status nek_ax_oz_selftest(int force_timeout, int64_t wait_us, int* timed_out)
@@ -760,7 +860,8 @@ nek_status nek_ax_oz_selftest(int force_timeout, int64_t wait_us, int* timed_out
     if (st == NEK_OK) st = check_cuda(cudaMemset(gff, 0, sizeof(float) * 12 * ne * n3));
     double* w = dbuf + nx * nx + ne * n3;
     if (st == NEK_OK)
-        st = launch_ax_oz_ex(ne, nx, dbuf, gff, dbuf + nx * nx, w, nullptr, wait_us * 1000LL, force_timeout ? 2 : 1);
+        st = launch_ax_oz_ex(ne, nx, dbuf, gff, dbuf + nx * nx, w, nullptr, wait_us * 1000LL, force_timeout ? 2 : 1,
+                             nullptr, nullptr);
     if (st == NEK_OK) st = check_cuda(cudaDeviceSynchronize());
     bool to = false;
     if (st == NEK_OK) st = ax_oz_take_timeout(&to);

@@ -145,8 +145,10 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
     const bool time_ax = opts && opts->time_ax;
     const int ax_impl = opts ? opts->ax_impl : NEK_AX_FP64;
     const float* Gff = opts ? opts->Gff : nullptr;
-    if (ax_impl != NEK_AX_FP64 && ax_impl != NEK_AX_FF) return NEK_ERR_INVALID_ARG;
-    if (ax_impl == NEK_AX_FF && (!Gff || !is_aligned(Gff, 16))) return NEK_ERR_INVALID_ARG;
+    if (ax_impl != NEK_AX_FP64 && ax_impl != NEK_AX_FF && ax_impl != NEK_AX_OZ) return NEK_ERR_INVALID_ARG;
+    if (ax_impl == NEK_AX_OZ && !ax_oz_supported(nx)) return NEK_ERR_UNSUPPORTED_NX;
+    if (ax_impl != NEK_AX_FP64 && (!Gff || !is_aligned(Gff, 16))) return NEK_ERR_INVALID_ARG;
+    if (ax_impl == NEK_AX_OZ && minv && !is_aligned(minv, 16)) return NEK_ERR_INVALID_ARG;
     if (opts) {
         opts->ax_ms_total = 0.0;
         opts->ax_launches = 0;
@@ -192,12 +194,14 @@ nek_status nek_cg_solve_ex(const nek_gs* gs, int64_t nelt, int nx, const double*
     }
     // The float-float operator also writes element energies, which replace the
     // solve's <p,w> pass.
-    const bool energies = ax_impl == NEK_AX_FF;
-    pcg::ElementEnergies ee{edot, nelt, ax_ff_dir_supported(nx)};  // and the direction update, where compiled
+    const bool energies = ax_impl != NEK_AX_FP64;
+    // and the direction update, where compiled
+    pcg::ElementEnergies ee{edot, nelt, ax_impl == NEK_AX_OZ ? ax_oz_supported(nx) : ax_ff_dir_supported(nx)};
     if (st == NEK_OK) {
         auto ax = [&](const double* p, double* w, double* ed, const DirUpdate* dir, cudaStream_t ss) {
-            return ax_impl == NEK_AX_FF ? launch_ax_ff(nelt, nx, D, Gff, p, w, ss, nullptr, nullptr, nullptr, ed, dir)
-                                        : launch_ax_fp64(nelt, nx, D, G, p, w, ss);
+            return ax_impl == NEK_AX_FF   ? launch_ax_ff(nelt, nx, D, Gff, p, w, ss, nullptr, nullptr, nullptr, ed, dir)
+                   : ax_impl == NEK_AX_OZ ? launch_ax_oz(nelt, nx, D, Gff, p, w, ss, ed, dir)
+                                          : launch_ax_fp64(nelt, nx, D, G, p, w, ss);
         };
         st = pcg::run<double>(gs, n, gs->d_c, mask, mv, f, x, b, tol_rel, max_iter, check_every, time_ax, ax, s,
                               &res, flags, energies ? &ee : nullptr);

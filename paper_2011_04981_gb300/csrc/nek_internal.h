@@ -119,6 +119,15 @@ struct DirUpdate {
 // True where launch_ax_ff supports dir (every nx of the float-float kernels).
 bool ax_ff_dir_supported(int nx);
 
+// The tensor-core FP64-accurate operator (nek_ax_oz): even nx up to 10.  Goz from nek_geom_oz; u, w
+// 16-byte aligned.  edot (optional): element energies, as for launch_ax_ff; dir (optional, with edot):
+// the direction update, input dir->p (u ignored), every array 16-byte aligned.
+bool ax_oz_supported(int nx);
+nek_status launch_ax_oz(int64_t nelt, int nx, const double* D, const float* Goz, const double* u, double* w,
+                        cudaStream_t s, double* edot = nullptr, const DirUpdate* dir = nullptr);
+nek_status launch_ax_oz_ex(int64_t nelt, int nx, const double* D, const float* Goz, const double* u, double* w,
+                           cudaStream_t s, long long wait_ns, int arrivals, double* edot, const DirUpdate* dir);
+
 // Deterministic block-partial reductions use this fixed grid for a given length.
 int reduce_blocks(int64_t n);
 constexpr int kReduceThreads = 256;

@@ -43,6 +43,7 @@ class NekError(RuntimeError):
 AX_FP64 = 0
 AX_FF = 1
 AX_FF_ENERGY = 2  # the element-energy form, for nek_set_ax_epb / nek_get_ax_epb
+AX_OZ = 3  # FP64-accurate with the contractions on the tensor cores (Gff: the split of nek_geom_oz)
 
 
 class NekCgOpts(ctypes.Structure):

@@ -45,6 +45,14 @@ class DeviceProblem:
             nekax.geom_ff(self.nelt, self.nx, self.G, self.Gff)
         return self.Gff
 
+    def _g_split(self, ax_impl):
+        """The float-pair split of G that an operator kind reads (None for the native FP64 operator)."""
+        if ax_impl == nekax.AX_FF:
+            return self.prepare_ff()
+        if ax_impl == nekax.AX_OZ:
+            return self.prepare_oz()
+        return None
+
     def ax(self, u, w, stream=None):
         nekax.ax(self.nelt, self.nx, self.D, self.G, u, w, stream)
 
@@ -65,14 +73,14 @@ class DeviceProblem:
 
     def cg(self, f, x, tol=1e-8, max_iter=1000, workspace=None, check_every=1, time_ax=False, stream=None,
            ax_impl=nekax.AX_FP64):
-        Gff = self.prepare_ff() if ax_impl == nekax.AX_FF else None
+        Gff = self._g_split(ax_impl)
         return nekax.cg_solve(self.gs, self.nelt, self.nx, self.D, self.G, self.mask, self.minv, f, x, tol,
                               max_iter, workspace, check_every, time_ax, stream, ax_impl=ax_impl, Gff=Gff)
 
     def cg_host(self, f_host, x_host, tol=1e-8, max_iter=1000, workspace=None, staging=None, check_every=1,
                 time_ax=False, stream=None, ax_impl=nekax.AX_FP64):
         """The same solve with f and x in host memory (the library copies them)."""
-        Gff = self.prepare_ff() if ax_impl == nekax.AX_FF else None
+        Gff = self._g_split(ax_impl)
         return nekax.cg_solve_host(self.gs, self.nelt, self.nx, self.D, self.G, self.mask, self.minv, f_host,
                                    x_host, tol, max_iter, workspace, staging, check_every, time_ax, stream,
                                    ax_impl=ax_impl, Gff=Gff)

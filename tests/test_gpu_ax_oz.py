@@ -150,3 +150,65 @@ def test_ax_oz_bounded_wait_runs_out_and_reports():
     assert st == nekax.OK and to == 0
     D, G, u = _case(6, 40, 3)
     assert _rel(_run(6, D, G, u), ref.ax(D, G, u)) <= TOL_AX
+
+
+# ------------------------------------------------------------------ in the Jacobi-PCG solve
+@pytest.mark.parametrize("dims,nx", [((3, 3, 3), 6), ((2, 2, 2), 10), ((3, 2, 2), 8), ((3, 3, 3), 2)])
+def test_cg_with_oz_operator(dims, nx):
+    """The solve with the tensor-core operator (element energies and the fused x / direction update):
+    converges to 1e-8 by the oracle's own residual, within 2 iterations of the oracle's count."""
+    from paper_2011_04981_gb300.problem import DeviceProblem
+
+    mesh = inputs.box_mesh(*dims, nx, perturb=0.1, seed=3)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=4)
+    x = torch.empty((mesh.nelt, nx ** 3), dtype=torch.float64, device=DEV)
+    res = P.cg(_t(f), x, tol=1e-8, max_iter=2000, ax_impl=nekax.AX_OZ)
+    assert res["status"] == nekax.OK, res
+    st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 1e-8, 2000)
+    assert abs(res["iters"] - itr) <= 2, (res["iters"], itr)
+    assert Pr.residual(f, x.cpu().numpy()) <= 1e-8 * (1 + 1e-3)
+    assert _rel(x.cpu().numpy(), xr) <= 1e-6
+    assert np.all(x.cpu().numpy()[mesh.mask == 0] == 0.0)
+
+
+@pytest.mark.parametrize("nx", [6, 10])
+def test_cg_oz_fixed_iterations(nx):
+    """After 1, 2 and 23 iterations the iterate matches the oracle's PCG element by element to 1e-9 of
+    its scale, and the reported residual to 1e-8 relative."""
+    from paper_2011_04981_gb300.problem import DeviceProblem
+
+    mesh = inputs.box_mesh(3, 2, 2, nx, perturb=0.1, seed=7)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=8)
+    for its in (1, 2, 23):
+        x = torch.full((mesh.nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+        res = P.cg(_t(f), x, tol=0.0, max_iter=its, ax_impl=nekax.AX_OZ)
+        assert res["status"] == nekax.OK and res["iters"] == its, res
+        st, xr, itr, rr = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, 0.0, its)
+        xg = x.cpu().numpy()
+        err = np.max(np.abs(xg - xr), axis=1)
+        assert np.max(err) <= 1e-9 * np.max(np.abs(xr)), (its, int(np.argmax(err)), float(err.max()))
+        assert abs(res["relres"] - rr) <= 1e-8 * rr, (its, res["relres"], rr)
+
+
+def test_cg_oz_rejects_unsupported_nx_and_missing_split():
+    from paper_2011_04981_gb300.problem import DeviceProblem
+
+    mesh = inputs.box_mesh(2, 1, 1, 5, perturb=0.1, seed=3)
+    P = DeviceProblem(mesh, DEV)
+    f = _t(inputs.random_global_field(mesh, seed=4))
+    x = torch.empty_like(f)
+    with pytest.raises(nekax.NekError) as ex:
+        nekax.cg_solve(P.gs, mesh.nelt, 5, P.D, P.G, P.mask, P.minv, f, x, 1e-8, 10, ax_impl=nekax.AX_OZ,
+                       Gff=P.prepare_ff())
+    assert ex.value.status == nekax.ERR_UNSUPPORTED_NX
+    mesh = inputs.box_mesh(2, 1, 1, 6, perturb=0.1, seed=3)
+    P = DeviceProblem(mesh, DEV)
+    f = _t(inputs.random_global_field(mesh, seed=4))
+    x = torch.empty_like(f)
+    with pytest.raises(nekax.NekError) as ex:
+        nekax.cg_solve(P.gs, mesh.nelt, 6, P.D, P.G, P.mask, P.minv, f, x, 1e-8, 10, ax_impl=nekax.AX_OZ, Gff=None)
+    assert ex.value.status == nekax.ERR_INVALID_ARG

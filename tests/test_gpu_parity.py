@@ -474,7 +474,8 @@ def test_cg_ff_solve_bit_identical_across_elements_per_cta(nx):
 def test_cg_bench_size_fixed_iterations_match_oracle():
     """The solve the benchmark times, at its size: the 32x32x32 box at nx = 10 with the benchmark's
     seeds, the float-float operator in its solve form (element energies, fused x / direction update,
-    one element per CTA, the tuned count) and the native FP64 operator, three fixed iterations each.
+    one element per CTA, the tuned count), the tensor-core operator in its solve form and the native
+    FP64 operator, three fixed iterations each.
     Every element of the iterate is compared with the oracle's PCG; this covers the fused update's
     load and store offsets over all 32.8 M points."""
     nx = 10
@@ -486,7 +487,7 @@ def test_cg_bench_size_fixed_iterations_match_oracle():
     got = {}
     try:
         assert lib.nek_set_ax_epb(int(nekax.AX_FF_ENERGY), nx, 1) == nekax.OK
-        for impl in (nekax.AX_FF, nekax.AX_FP64):
+        for impl in (nekax.AX_FF, nekax.AX_OZ, nekax.AX_FP64):
             x = torch.full((mesh.nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
             res = P.cg(_t(f), x, tol=0.0, max_iter=its, ax_impl=impl)
             assert res["status"] == nekax.OK and res["iters"] == its, res
