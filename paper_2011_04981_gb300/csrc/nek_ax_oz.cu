@@ -663,6 +663,16 @@ __global__ void __launch_bounds__(kNT, 2)
             const int xs = eu_e + ew + 2 * ed - 32;
             double2* we = reinterpret_cast<double2*>(w + e * N3);
             double energy = 0.0;  // this thread's part of the element's input . w, in a fixed order
+            double2 iv[NPR];      // the input at this thread's points (u, or the p written in stage 1), loaded
+                                  // before any store of w, which the compiler cannot order past them
+            if constexpr (MODE != kOzPlain) {
+#pragma unroll
+                for (int q = 0; q < NPR; q++) {
+                    const int pp = tid + kNT * q < NPP ? tid + kNT * q : 0;
+                    iv[q] = MODE == kOzDir ? reinterpret_cast<const double2*>(dir.p + e * N3)[pp]
+                                           : __ldg(reinterpret_cast<const double2*>(u + e * N3) + pp);
+                }
+            }
 #pragma unroll
             for (int q = 0; q < NPR; q++) {
                 const int pp = tid + kNT * q;
@@ -679,11 +689,8 @@ __global__ void __launch_bounds__(kNT, 2)
                                                     __dadd_rn(widen_scaled(S.y, xs), widen_scaled(lo.y, xs)));
                     we[pp] = wv;
                     if constexpr (MODE != kOzPlain) {
-                        // the input at the two points: u, or the p this thread wrote in stage 1
-                        const double2 iv = MODE == kOzDir ? reinterpret_cast<const double2*>(dir.p + e * N3)[pp]
-                                                          : __ldg(reinterpret_cast<const double2*>(u + e * N3) + pp);
-                        energy = fma(iv.x, wv.x, energy);
-                        energy = fma(iv.y, wv.y, energy);
+                        energy = fma(iv[q].x, wv.x, energy);
+                        energy = fma(iv[q].y, wv.y, energy);
                     }
                 }
             }
