@@ -78,8 +78,9 @@ def parse():
                     help="skip the elements-per-CTA tuning (nek_tune_ax) before timing")
     ap.add_argument("--epb", type=int, default=0,
                     help="fix the AX elements per CTA (1, 2 or 4; nek_set_ax_epb) instead of tuning")
-    ap.add_argument("--ax", default="ff", choices=["fp64", "ff"],
-                    help="AX operator inside the solve: native FP64 or FP64-accurate float-float")
+    ap.add_argument("--ax", default="ff", choices=["fp64", "ff", "oz"],
+                    help="AX operator inside the solve: native FP64, FP64-accurate float-float, or FP64-accurate "
+                         "with the contractions on the tensor cores (BF16 digit slices; even nx up to 10)")
     args = ap.parse_args()
     names = {"native", "sweep", "solve", "mixed", "learned", "batch", "lvec", "net"}
     ex = args.extras.strip().lower()
@@ -164,7 +165,8 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
-AX_SOURCES = {"fp64": ("nek_ax.cu", "ax_fp64_traffic.json"), "ff": ("nek_ax_ff_kernels.cuh", "ax_ff_traffic.json")}
+AX_SOURCES = {"fp64": ("nek_ax.cu", "ax_fp64_traffic.json"), "ff": ("nek_ax_ff_kernels.cuh", "ax_ff_traffic.json"),
+              "oz": ("nek_ax_oz.cu", "ax_oz_traffic.json")}
 
 
 def kernel_source_sha(which="fp64"):
@@ -334,13 +336,17 @@ def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=20, tune=False):
         mesh = inputs.box_mesh(32, 32, 32, nx, perturb=0.1, seed=1)
         P = DeviceProblem(mesh, "cuda", build_minv=False)
         P.prepare_ff()
+        ops = [("fp64", P.ax), ("ff", P.ax_ff)]
+        if nx % 2 == 0 and nx <= 10:
+            P.prepare_oz()
+            ops.append(("oz", P.ax_oz))
         u = torch.rand((mesh.nelt, nx ** 3), dtype=torch.float64, device="cuda") * 2 - 1
         w = torch.empty_like(u)
         s = torch.cuda.current_stream()
         res = {}
-        for name, fn in (("fp64", P.ax), ("ff", P.ax_ff)):
+        for name, fn in ops:
             epb = None
-            if tune:
+            if tune and name != "oz":
                 impl = nekax.AX_FF if name == "ff" else nekax.AX_FP64
                 epb, _ = nekax.tune_ax(impl, mesh.nelt, nx, P.D, P.Gff if name == "ff" else P.G, u, w)
             for _ in range(3):
@@ -358,8 +364,8 @@ def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=20, tune=False):
             res[name] = {"gdofs": g, "ms": t * 1e3, "gflops": g * perfmodel.ax_flops_per_point(nx),
                          "hbm_frac": g * 64 / hbm,
                          "fp64_frac": g * perfmodel.ax_flops_per_point(nx) / 1e3 / FP64_PEAK_TFLOPS,
-                         "epb": epb if epb is not None else nekax.get_ax_epb(
-                             nekax.AX_FF if name == "ff" else nekax.AX_FP64, nx)}
+                         "epb": "2 persistent CTAs per SM" if name == "oz" else epb if epb is not None else
+                         nekax.get_ax_epb(nekax.AX_FF if name == "ff" else nekax.AX_FP64, nx)}
         out[str(nx)] = res
         del P, u, w
         torch.cuda.empty_cache()
@@ -595,14 +601,31 @@ def native_fp64_block(torch, P, f, x, ws, iters, steps=3, tune=True):
         wt = torch.empty_like(f)
         nekax.tune_ax(nekax.AX_FP64, P.nelt, nx, P.D, P.G, f, wt)
         del wt
-    P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, ax_impl=nekax.AX_FP64)
+    out = solve_block(torch, P, f, x, ws, iters, nekax.AX_FP64, steps)
+    t_ax = out["ax"]["ms_per_launch"] / 1e3
+    hbm, kind = peaks()
+    flops = perfmodel.ax_flops_per_point(nx) * P.npts
+    out["ax"].update({"kernel": "k_ax_fp64<%d>" % nx, "tflops": flops / t_ax / 1e12,
+                      "fp64_pipe_frac": flops / t_ax / 1e12 / FP64_PEAK_TFLOPS,
+                      "hbm_frac_64B": 64 * P.npts / t_ax / 1e9 / hbm,
+                      "elements_per_cta": nekax.get_ax_epb(nekax.AX_FP64, nx)})
+    out["note"] = ("native FP64 (the paper's arithmetic); FP64 peak = 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                   "= %.4f TFLOP/s; HBM %s %.0f GB/s" % (FP64_PEAK_TFLOPS, kind, hbm))
+    return out
+
+
+def solve_block(torch, P, f, x, ws, iters, impl, steps=3):
+    """Fixed-iteration Jacobi-PCG rate with operator `impl`, and its AX launches timed inside the solve."""
+    from paper_2011_04981_gb300 import nekax
+
+    P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, ax_impl=impl)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ax_ms, ax_n = 0.0, 0
     e0.record(s)
     for _ in range(steps):
-        r = P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, time_ax=True, ax_impl=nekax.AX_FP64)
+        r = P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, time_ax=True, ax_impl=impl)
         assert r["status"] == nekax.OK and r["iters"] == iters, r
         ax_ms += r["ax_ms_total"]
         ax_n += r["ax_launches"]
@@ -610,16 +633,29 @@ def native_fp64_block(torch, P, f, x, ws, iters, steps=3, tune=True):
     e1.synchronize()
     t = e0.elapsed_time(e1) / 1e3
     ax_t = ax_ms / max(ax_n, 1) / 1e3
-    hbm, kind = peaks()
-    flops = perfmodel.ax_flops_per_point(nx) * P.npts
     return {"gdofs": P.npts * iters * steps / t / 1e9, "ms_per_step": 1e3 * t / steps, "steps": steps,
             "iters_per_step": iters,
-            "ax": {"kernel": "k_ax_fp64<%d>" % nx, "gdofs": P.npts / ax_t / 1e9, "ms_per_launch": ax_t * 1e3,
-                   "tflops": flops / ax_t / 1e12, "fp64_pipe_frac": flops / ax_t / 1e12 / FP64_PEAK_TFLOPS,
-                   "hbm_frac_64B": 64 * P.npts / ax_t / 1e9 / hbm, "share_of_step": ax_ms / 1e3 / t,
-                   "elements_per_cta": nekax.get_ax_epb(nekax.AX_FP64, nx)},
-            "note": "native FP64 (the paper's arithmetic); FP64 peak = 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz "
-                    "= %.4f TFLOP/s; HBM %s %.0f GB/s" % (FP64_PEAK_TFLOPS, kind, hbm)}
+            "ax": {"gdofs": P.npts / ax_t / 1e9, "ms_per_launch": ax_t * 1e3, "share_of_step": ax_ms / 1e3 / t}}
+
+
+def tensor_core_block(torch, P, f, x, ws, iters, steps=3):
+    """The headline solve with the FP64-accurate operator whose contractions run on the tensor cores
+    (nek_ax_oz: BF16 digit slices, exact FP32 level sums in TMEM, float-pair recombination), in its solve
+    form (element energies and the fused x / direction update, 104 algorithmic B/point)."""
+    from paper_2011_04981_gb300 import nekax
+
+    if not (P.nx % 2 == 0 and P.nx <= 10):
+        return {"skipped": "nek_ax_oz takes even nx up to 10"}
+    P.prepare_oz()
+    out = solve_block(torch, P, f, x, ws, iters, nekax.AX_OZ, steps)
+    hbm, kind = peaks()
+    t_ax = out["ax"]["ms_per_launch"] / 1e3
+    out["ax"].update({"kernel": "k_ax_oz<%d, 2>" % P.nx, "hbm_frac_104B": 104 * P.npts / t_ax / 1e9 / hbm})
+    out["note"] = ("FP64-accurate; HBM %s %.0f GB/s.  Standalone (64 B/point) this operator is faster than the "
+                   "float-float one (ax_sweep), inside the solve its fused update's FP64 operations (x and p "
+                   "updates, energies, the join to FP64: 5 per point on the 2-per-clock FP64 pipe) are not "
+                   "hidden by its two CTAs per SM" % (kind, hbm))
+    return out
 
 
 def solves_to_tol(torch, P, f, x, ws, tol=1e-8):
@@ -628,7 +664,11 @@ def solves_to_tol(torch, P, f, x, ws, tol=1e-8):
     from paper_2011_04981_gb300 import nekax
 
     out = {}
-    for name, impl in (("fp64_native", nekax.AX_FP64), ("fp64_float_float", nekax.AX_FF)):
+    ops = [("fp64_native", nekax.AX_FP64), ("fp64_float_float", nekax.AX_FF)]
+    if P.nx % 2 == 0 and P.nx <= 10:
+        P.prepare_oz()
+        ops.append(("fp64_tensor_core", nekax.AX_OZ))
+    for name, impl in ops:
         P.cg(f, x, tol=tol, max_iter=5, workspace=ws, ax_impl=impl)  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -680,17 +720,22 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     iters = args.iters
 
-    ax_impl = nekax.AX_FF if args.ax == "ff" else nekax.AX_FP64
+    ax_impl = {"ff": nekax.AX_FF, "fp64": nekax.AX_FP64, "oz": nekax.AX_OZ}[args.ax]
     if ax_impl == nekax.AX_FF:
         P.prepare_ff()
-    if args.epb:
+    if ax_impl == nekax.AX_OZ:
+        P.prepare_oz()
+    if ax_impl == nekax.AX_OZ:
+        pass  # fixed launch shape: two persistent CTAs per SM
+    elif args.epb:
         if nekax.load().nek_set_ax_epb(int(ax_impl), nx, args.epb) != nekax.OK:
             raise SystemExit("--epb %d does not fit the AX kernel at nx = %d" % (args.epb, nx))
     elif args.tune:
         wt = torch.empty_like(f)
         nekax.tune_ax(ax_impl, mesh.nelt, nx, P.D, P.Gff if ax_impl == nekax.AX_FF else P.G, f, wt)
         del wt
-    ax_epb = nekax.load().nek_get_ax_epb(int(nekax.AX_FF_ENERGY if ax_impl == nekax.AX_FF else ax_impl), nx)
+    ax_epb = (nekax.load().nek_get_ax_epb(int(nekax.AX_FF_ENERGY if ax_impl == nekax.AX_FF else ax_impl), nx)
+              if ax_impl != nekax.AX_OZ else "2 persistent CTAs per SM")
     for _ in range(args.warmup):
         P.cg(f, x, tol=0.0, max_iter=iters, workspace=ws, ax_impl=ax_impl)
     torch.cuda.synchronize()
@@ -741,18 +786,21 @@ def run_native(args):
     hbm, hbm_kind = peaks()
     traffic = traffic_from_profile(nx, mesh.nelt, args.ax)
     # the float-float operator of the solve also applies the x / direction update
-    fused_dir = args.ax == "ff"
+    fused_dir = args.ax in ("ff", "oz")
     ax_bpp = 104 if fused_dir else 64
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.ax == "fp64" else "f64 (AX in f32-pair float-float, FP64-accurate)",
+        "dtype": {"fp64": "f64", "ff": "f64 (AX in f32-pair float-float, FP64-accurate)",
+                  "oz": "f64 (AX contractions as BF16 digit slices on tcgen05 with exact FP32 level sums, "
+                        "FP64-accurate)"}[args.ax],
         "data": "synthetic",
         "config": {"workload": "Jacobi-PCG, %d PCG iterations per step (AX+dssum+mask+dots+updates), "
                                "%dx%dx%d deformed box (perturbation 0.1 h), nx=%d, FP64-accurate, AX %s"
-                               % (iters, e, e, e, nx, "native FP64 (nek_ax)" if args.ax == "fp64" else
-                                  "float-float on the FP32 pipes (nek_ax_ff)"),
+                               % (iters, e, e, e, nx, {"fp64": "native FP64 (nek_ax)",
+                                                       "ff": "float-float on the FP32 pipes (nek_ax_ff)",
+                                                       "oz": "contractions on the tensor cores (nek_ax_oz)"}[args.ax]),
                    "elements": mesh.nelt, "nx": nx, "points": pts, "iters_per_step": iters,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (G alone %.2f GB), no flush" % (pts * 48 / 1e9)},
@@ -771,9 +819,11 @@ def run_native(args):
                      if args.ax == "fp64" else
                      {"bound": "hbm", "achieved": ax_bpp * pts / ax_t / 1e9, "peak": hbm, "unit": "GB/s",
                       "frac": ax_bpp * pts / ax_t / 1e9 / hbm, "traffic": traffic,
-                      "kernel": ("k_ax_ffi<%d>" if nx in (10, 12) else "k_ax_ff<%d>") % nx,
-                      "note": ("FP64-accurate float-float AX with the fused x / direction update, 104 algorithmic "
-                               "B/point (p in and out 16, r 8, minv 8, x in and out 16, G 48, w 8)" if fused_dir else
+                      "kernel": ("k_ax_oz<%d, 2>" if args.ax == "oz" else
+                                 "k_ax_ffi<%d>" if nx in (10, 12) else "k_ax_ff<%d>") % nx,
+                      "note": ("FP64-accurate AX (%s) with the fused x / direction update, 104 algorithmic "
+                               "B/point (p in and out 16, r 8, minv 8, x in and out 16, G 48, w 8)"
+                               % ("tensor-core digit slices" if args.ax == "oz" else "float-float") if fused_dir else
                                "FP64-accurate float-float AX, 64 algorithmic B/point (u 8 + G 48 + w 8)") +
                               "; peak = %s HBM copy (MEASURED_PEAKS hbm_gbs); its instruction limit is the FP32 "
                               "pipe (see profiles)" % hbm_kind}),
@@ -783,6 +833,7 @@ def run_native(args):
     if "native" in ex and args.ax == "ff":
         line["fp64_native"] = _guard("native", lambda: native_fp64_block(torch, P, f, x, ws, iters,
                                                                          tune=args.tune))
+        line["fp64_tensor_core"] = _guard("native", lambda: tensor_core_block(torch, P, f, x, ws, iters))
     if "solve" in ex:
         line["cg_to_1e-8"] = _guard("solve", lambda: solves_to_tol(torch, P, f, x, ws))
     if "mixed" in ex:
