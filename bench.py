@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--extras", default="native,sweep,solve,mixed,learned,batch",
                     help="comma list of blocks after the timed region (native, sweep, solve, mixed, learned, "
                          "batch, lvec), 'all' or 'none'")
+    ap.add_argument("--sweep-elems", type=int, default=32, help="elements per side of the AX sweep's box")
+    ap.add_argument("--sweep-nx", type=int, nargs="+", default=[8, 10, 12, 16], help="nx values of the AX sweep")
     ap.add_argument("--sweep", action="store_true", help="add the standalone AX sweep to --extras")
     ap.add_argument("--solve", action="store_true", help="add the solves to 1e-8 to --extras")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -324,16 +326,16 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ native arm
-def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=20, tune=False):
-    """Standalone AX at each nx on a 32^3-element box: median over `reps` launches, each timed with its own
-    CUDA events (inputs far above L2, so no flush is needed)."""
+def ax_sweep(torch, nxs=(8, 10, 12, 16), reps=20, tune=False, elems=32):
+    """Standalone AX at each nx on an elems^3-element box (32^3 by default): median over `reps` launches, each
+    timed with its own CUDA events (inputs far above L2 at 32^3, so no flush is needed)."""
     from paper_2011_04981_gb300 import inputs, nekax, perfmodel
     from paper_2011_04981_gb300.problem import DeviceProblem
 
     out = {}
     hbm, _ = peaks()
     for nx in nxs:
-        mesh = inputs.box_mesh(32, 32, 32, nx, perturb=0.1, seed=1)
+        mesh = inputs.box_mesh(elems, elems, elems, nx, perturb=0.1, seed=1)
         P = DeviceProblem(mesh, "cuda", build_minv=False)
         P.prepare_ff()
         ops = [("fp64", P.ax), ("ff", P.ax_ff)]
@@ -841,7 +843,8 @@ def run_native(args):
     if "lvec" in ex:
         line["lvec"] = _guard("lvec", lambda: lvec_block(torch, P, iters))
     if "sweep" in ex:
-        line["ax_sweep"] = _guard("sweep", lambda: ax_sweep(torch, tune=args.tune))
+        line["ax_sweep"] = _guard("sweep", lambda: ax_sweep(torch, nxs=tuple(args.sweep_nx), tune=args.tune,
+                                                            elems=args.sweep_elems))
     if "learned" in ex:
         line["learned"] = _guard("learned", lambda: learned_block(torch, args.learned_meshes, args.learned_epochs))
     if "net" in ex:
