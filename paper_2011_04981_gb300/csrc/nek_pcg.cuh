@@ -35,6 +35,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "nek_ff.cuh"
 #include "nek_internal.h"
 #include "nek_reduce.cuh"
 
@@ -313,6 +314,12 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
         arr = to_f64(frr);
         arz = to_f64(frz);
     } else if (flags) {
+        // r and <r,z> in FP64; <r,r> (used only for the residual test and the reported norm) exactly enough on
+        // the FP32 pipes, so that GB300's 2-per-clock FP64 pipe carries three operations a point, not four:
+        // r = rh + rl split by integer operations (|r - rh - rl| <= 2^-46 |r|), r^2 = rh^2 (exact as the
+        // float pair p + e) + 2 rh rl, the p summed with TwoSum, the rest in plain floats: each thread's sum
+        // is good to ~2^-40 of itself
+        float s_hi = 0.f, s_lo = 0.f, s_c = 0.f;
 #pragma unroll 4
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
             const uint8_t fq = flags[q];
@@ -322,11 +329,24 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
             const V zq = minv[q] * rq;
             r[q] = rq;
             if (fq & kOwner) {
-                const double rd = to_f64(rq);
-                arr += rd * rd;
-                arz += rd * to_f64(zq);
+                arz += to_f64(rq) * to_f64(zq);
+                if constexpr (std::is_same<V, double>::value) {
+                    const float2 h = split_double(rq);
+                    const float pr = __fmul_rn(h.x, h.x);
+                    const float er = __fmaf_rn(h.x, h.x, -pr);
+                    const float t = __fmaf_rn(2.f * h.x, h.y, er);
+                    const float sn = __fadd_rn(s_hi, pr);
+                    const float bb = __fsub_rn(sn, s_hi);
+                    s_lo = __fadd_rn(s_lo, __fadd_rn(__fsub_rn(s_hi, __fsub_rn(sn, bb)), __fsub_rn(pr, bb)));
+                    s_hi = sn;
+                    s_c = __fadd_rn(s_c, t);
+                } else {
+                    const double rd = to_f64(rq);
+                    arr += rd * rd;
+                }
             }
         }
+        if constexpr (std::is_same<V, double>::value) arr = (widen(s_hi) + widen(s_lo)) + widen(s_c);
     } else {
         for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
             V wv = w[q];
