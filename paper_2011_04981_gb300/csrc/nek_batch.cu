@@ -213,6 +213,8 @@ __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_b
     const double alpha = s.alpha;
     const int64_t a = ch_begin[c], b = ch_begin[c + 1];
     double acc[2] = {0.0, 0.0};
+    // <r,r> in float pairs on the FP32 pipes, as the single-problem solve's r update does
+    float s_hi = 0.f, s_lo = 0.f, s_c = 0.f;
     for (int64_t q = a + threadIdx.x; q < b; q += BT) {
         const uint8_t fq = flags[q];
         double wq = w[q];  // loaded whatever the flags say
@@ -221,10 +223,11 @@ __global__ void __launch_bounds__(BT) kb_update(const int64_t* __restrict__ ch_b
         const double zq = minv[q] * rq;
         r[q] = rq;
         if (fq & pcg::kOwner) {
-            acc[0] += rq * rq;
+            pcg::sq_pair_add(rq, s_hi, s_lo, s_c);
             acc[1] += rq * zq;
         }
     }
+    acc[0] = (widen(s_hi) + widen(s_lo)) + widen(s_c);
     chunk_reduce<2>(acc, parts, nchunks, c);
 }
 

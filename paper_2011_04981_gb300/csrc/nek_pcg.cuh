@@ -282,6 +282,21 @@ __global__ void __launch_bounds__(NTA) k_alpha(const double* __restrict__ parts,
 }
 
 // r -= alpha mask.w; partials of <r,r>_c and <r,z>_c with z = minv r (not stored)
+// (s_hi + s_lo) + s_c += r^2 in float pairs: r = rh + rl split by integer operations (|r - rh - rl| <=
+// 2^-46 |r|), r^2 = rh^2 (exact as the float pair p + e) + 2 rh rl; p summed with TwoSum into s_hi + s_lo,
+// e + 2 rh rl into s_c.  For sums of ~100 terms a thread: good to ~2^-40 of the sum.
+__device__ __forceinline__ void sq_pair_add(double r, float& s_hi, float& s_lo, float& s_c)
+{
+    const float2 h = split_double(r);
+    const float pr = __fmul_rn(h.x, h.x);
+    const float t = __fmaf_rn(2.f * h.x, h.y, __fmaf_rn(h.x, h.x, -pr));
+    const float sn = __fadd_rn(s_hi, pr);
+    const float bb = __fsub_rn(sn, s_hi);
+    s_lo = __fadd_rn(s_lo, __fadd_rn(__fsub_rn(s_hi, __fsub_rn(sn, bb)), __fsub_rn(pr, bb)));
+    s_hi = sn;
+    s_c = __fadd_rn(s_c, t);
+}
+
 template <class V>
 __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ c, const V* __restrict__ minv,
                                                 const V* __restrict__ w, V* __restrict__ r, double* __restrict__ parts,
@@ -331,15 +346,7 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
             if (fq & kOwner) {
                 arz += to_f64(rq) * to_f64(zq);
                 if constexpr (std::is_same<V, double>::value) {
-                    const float2 h = split_double(rq);
-                    const float pr = __fmul_rn(h.x, h.x);
-                    const float er = __fmaf_rn(h.x, h.x, -pr);
-                    const float t = __fmaf_rn(2.f * h.x, h.y, er);
-                    const float sn = __fadd_rn(s_hi, pr);
-                    const float bb = __fsub_rn(sn, s_hi);
-                    s_lo = __fadd_rn(s_lo, __fadd_rn(__fsub_rn(s_hi, __fsub_rn(sn, bb)), __fsub_rn(pr, bb)));
-                    s_hi = sn;
-                    s_c = __fadd_rn(s_c, t);
+                    sq_pair_add(rq, s_hi, s_lo, s_c);
                 } else {
                     const double rd = to_f64(rq);
                     arr += rd * rd;
