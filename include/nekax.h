@@ -237,6 +237,18 @@ nek_status nek_ax_lowp(int64_t nelt, int nx, int precision, const double* D, con
 nek_status nek_ax_lowp_tc(int64_t nelt, int nx, int precision, const double* D, const void* Glp,
                           const float* gscale, const float* u, float* w, void* stream);
 
+/* Same operator with the D-contractions on the 5th-generation tensor cores
+ * (tcgen05 BF16 / FP16 MMAs, FP32 accumulators in tensor memory): per element,
+ * each direction's contraction is one 128 x 16 x 16 product of the element's
+ * lines (nx points padded to 16) with rnd(D).  precision NEK_PREC_BF16 or
+ * NEK_PREC_F16 (else NEK_ERR_INVALID_ARG), nx 2..11 (else
+ * NEK_ERR_UNSUPPORTED_NX).  Same rounding points and error bound as
+ * nek_ax_lowp; only the order of the FP32 additions inside a contraction
+ * differs.  Every wait on the tensor cores is bounded (~2 s); one that runs out
+ * leaves NaN in the affected outputs.  Arguments as nek_ax_lowp. */
+nek_status nek_ax_lowp_tc5(int64_t nelt, int nx, int precision, const double* D, const void* Glp,
+                           const float* gscale, const float* u, float* w, void* stream);
+
 /* Defect correction (iterative refinement) to FP64 accuracy: the residual
  * r = mask(f - dssum(AX x)), its norm, inner products and the update x += d are
  * FP64 on the GPU (AX through nek_ax_ff when Gff is given, else nek_ax); each

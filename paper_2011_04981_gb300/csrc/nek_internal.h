@@ -79,6 +79,10 @@ nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                         cudaStream_t s, const int32_t* l2g = nullptr, const int32_t* eprob = nullptr,
                         const uint8_t* pdone = nullptr, double* edot = nullptr, const DirUpdate* dir = nullptr);
+// The tcgen05 form of the reduced-precision operator (BF16 / FP16, nx 2..11).
+bool ax_lowp_tc5_supported(int nx, int precision);
+nek_status launch_ax_lowp_tc5(int precision, int64_t nelt, int nx, const double* D, const void* Glp,
+                              const float* gscale, const float* u, float* w, cudaStream_t s, double* edot = nullptr);
 // edot (optional, nelt doubles): per-element energies u_e . w_e in FP64.
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
                           const float* u, float* w, cudaStream_t s, double* edot = nullptr);

@@ -94,9 +94,11 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, int arrivals)
 
 // Wait for the mbarrier phase with parity `parity`; false if it did not complete
 // within wait_ns of global time.  Each try may suspend the thread (up to the
-// hint, 20 us) until the phase completes, so waiting threads do not take issue
-// slots from the other CTAs on the SM; the clock is read every 64 tries.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long wait_ns)
+// hint, 20 us by default) until the phase completes, so waiting threads do not
+// take issue slots from the other CTAs on the SM; the clock is read every 64
+// tries.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long wait_ns,
+                                                  uint32_t hint_ns = 20000)
 {
     const long long t0 = global_ns();
     for (int tries = 1;; tries++) {
@@ -106,7 +108,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
             "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, %3;\n\t"
             "selp.b32 %0, 1, 0, P1;\n\t}\n"
             : "=r"(done)
-            : "r"(mbar), "r"(parity), "r"(20000)
+            : "r"(mbar), "r"(parity), "r"(hint_ns)
             : "memory");
         if (done) return true;
         if ((tries & 63) == 0 && global_ns() - t0 > wait_ns) return false;

@@ -136,6 +136,7 @@ _SIGS = {
     "nek_geom_lowp": ([_I64, _I, _I, _P, _P, _P, _P], _I),
     "nek_ax_lowp": ([_I64, _I, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_ax_lowp_tc": ([_I64, _I, _I, _P, _P, _P, _P, _P, _P], _I),
+    "nek_ax_lowp_tc5": ([_I64, _I, _I, _P, _P, _P, _P, _P, _P], _I),
     "nek_cg_mixed_workspace_bytes": ([_I64, _I, _I], ctypes.c_size_t),
     "nek_cg_solve_mixed": ([_P, _I64, _I, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _D, _D, _I, _I, _P,
                             ctypes.POINTER(NekMixedInfo), _P], _I),
@@ -356,6 +357,12 @@ def ax_lowp(nelt, nx, precision, D, Glp, gscale, u, w, stream=None):
 def ax_lowp_tc(nelt, nx, precision, D, Glp, gscale, u, w, stream=None):
     _check("nek_ax_lowp_tc", load().nek_ax_lowp_tc(nelt, nx, int(precision), _ptr(D), _ptr(Glp), _ptr(gscale),
                                                    _ptr(u), _ptr(w), _stream(stream)))
+
+
+def ax_lowp_tc5(nelt, nx, precision, D, Glp, gscale, u, w, stream=None):
+    """The reduced-precision operator with its contractions as tcgen05 MMAs (BF16 / FP16, nx 2..11)."""
+    _check("nek_ax_lowp_tc5", load().nek_ax_lowp_tc5(nelt, nx, int(precision), _ptr(D), _ptr(Glp), _ptr(gscale),
+                                                     _ptr(u), _ptr(w), _stream(stream)))
 
 
 def cg_solve_mixed(gs, nelt, nx, D, G, Gff, precision, Glp, gscale, m, minv, f, x, tol=1e-8, inner_tol=1e-2,

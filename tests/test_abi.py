@@ -94,6 +94,20 @@ def test_ax_oz_rejects_bad_arguments_before_launch(lib):
     assert L.nek_ax_oz_selftest(1, 100, None) == nekax.ERR_INVALID_ARG
 
 
+def test_ax_lowp_tc5_rejects_bad_arguments_before_launch(lib):
+    A16 = 0x10000
+    L = lib
+    for nx in (1, 12, 16):
+        assert L.nek_ax_lowp_tc5(4, nx, 1, A16, A16, A16, A16, A16 * 2, None) == nekax.ERR_UNSUPPORTED_NX
+    assert L.nek_ax_lowp_tc5(4, 8, 0, A16, A16, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # FP32: no MMA form
+    assert L.nek_ax_lowp_tc5(4, 8, 3, A16, A16, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_lowp_tc5(-1, 8, 1, A16, A16, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_lowp_tc5(0, 8, 1, None, None, None, None, None, None) == nekax.OK
+    assert L.nek_ax_lowp_tc5(4, 8, 1, None, A16, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG
+    assert L.nek_ax_lowp_tc5(4, 8, 1, A16, A16 + 2, A16, A16, A16 * 2, None) == nekax.ERR_INVALID_ARG  # Glp
+    assert L.nek_ax_lowp_tc5(4, 8, 1, A16, A16, A16, A16, A16 + 256, None) == nekax.ERR_INVALID_ARG  # overlap
+
+
 def test_other_entry_points_reject_bad_arguments(lib):
     L = lib
     A16 = 0x10000

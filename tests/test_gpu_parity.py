@@ -590,16 +590,26 @@ def test_ax_lowp_componentwise_bound(prec, tc, nx):
     ud = torch.from_numpy(u.astype(np.float32)).to(DEV)
     wd = torch.full_like(ud, float("nan"))
     (nekax.ax_lowp_tc if tc else nekax.ax_lowp)(mesh.nelt, nx, prec, _t(D), Glp, gsc, ud, wd)
+    _check_lowp_bound(prec, nx, D, G, u, wd, "tensor-core %d" % tc)
+    if tc and nx <= 11:
+        # the tcgen05 form (nx up to 11): the same bound; results equal the mma.sync form's up to the order of
+        # the FP32 additions inside a contraction
+        w5 = torch.full_like(ud, float("nan"))
+        nekax.ax_lowp_tc5(mesh.nelt, nx, prec, _t(D), Glp, gsc, ud, w5)
+        _check_lowp_bound(prec, nx, D, G, u, w5, "tcgen05")
+
+
+def _check_lowp_bound(prec, nx, D, G, u, wd, form):
     torch.cuda.synchronize()
     w = wd.cpu().numpy().astype(np.float64)
-    assert np.all(np.isfinite(w))
+    assert np.all(np.isfinite(w)), form
     u32 = u.astype(np.float32).astype(np.float64)
     w_ref = ref.ax(D, G, u32)
     w_abs = ref.ax(np.abs(D), np.abs(G), np.abs(u32))
     bound = 4.0 * (UNIT_IN[prec] + (2 * nx + 3) * 2.0 ** -24) * w_abs
     ratio = np.max(np.abs(w - w_ref) / bound)
-    print("lowp bound ratio: precision %d tensor-core %d nx %d: %.3f" % (prec, tc, nx, ratio))
-    assert ratio <= 1.0, ratio
+    print("lowp bound ratio: precision %d %s nx %d: %.3f" % (prec, form, nx, ratio))
+    assert ratio <= 1.0, (form, ratio)
 
 
 @pytest.mark.parametrize("prec", [nekax.PREC_F32, nekax.PREC_BF16, nekax.PREC_F16])
