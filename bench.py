@@ -457,7 +457,18 @@ def mixed_block(torch, P, f, x, ws_bytes_hint=None):
             e1.record()
             e1.synchronize()
             t_tc = e0.elapsed_time(e1) / 10 / 1e3
-            rec["tensor_core_form"] = {"ax_gdofs": P.npts / t_tc / 1e9,
+            rec["tensor_core_form"] = {"kernel": "mma.sync m16n8k16 (nek_ax_lowp_tc)", "ax_gdofs": P.npts / t_tc / 1e9,
+                                       "ax_rel_err_vs_fp64": float((w2.double() - w64).abs().max() / w64.abs().max())}
+            if nx <= 11:  # the tcgen05 form, which the solves below use as their inner operator
+                nekax.ax_lowp_tc5(nelt, nx, prec, P.D, Glp, gsc, u32, w2)
+                e0.record()
+                for _ in range(10):
+                    nekax.ax_lowp_tc5(nelt, nx, prec, P.D, Glp, gsc, u32, w2)
+                e1.record()
+                e1.synchronize()
+                t5 = e0.elapsed_time(e1) / 10 / 1e3
+                rec["tcgen05_form"] = {"kernel": "k_ax_lowp_tc5 (nek_ax_lowp_tc5), the solve's inner operator",
+                                       "ax_gdofs": P.npts / t5 / 1e9, "ax_hbm_frac": P.npts * bpp / t5 / 1e9 / hbm,
                                        "ax_rel_err_vs_fp64": float((w2.double() - w64).abs().max() / w64.abs().max())}
         for tol in (1e-8, 1e-10):
             torch.cuda.synchronize()

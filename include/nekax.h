@@ -252,8 +252,9 @@ nek_status nek_ax_lowp_tc5(int64_t nelt, int nx, int precision, const double* D,
 /* Defect correction (iterative refinement) to FP64 accuracy: the residual
  * r = mask(f - dssum(AX x)), its norm, inner products and the update x += d are
  * FP64 on the GPU (AX through nek_ax_ff when Gff is given, else nek_ax); each
- * correction solves A d = r/||r|| by Jacobi-PCG with FP32 vectors and
- * nek_ax_lowp until its relative residual is <= inner_tol (or max_inner
+ * correction solves A d = r/||r|| by Jacobi-PCG with FP32 vectors and the
+ * reduced-precision operator (nek_ax_lowp_tc5 for BF16 / FP16 at nx up to 11,
+ * else nek_ax_lowp) until its relative residual is <= inner_tol (or max_inner
  * iterations).  Stops when ||r||_c/||b||_c <= tol_rel (NEK_OK) or after max_outer
  * corrections (NEK_ERR_NOT_CONVERGED).  workspace: device, >=
  * nek_cg_mixed_workspace_bytes(...) bytes, 256-aligned, or NULL.  Synchronous.

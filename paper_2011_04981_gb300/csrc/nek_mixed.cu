@@ -609,8 +609,11 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
     auto ax64 = [&](const double* p, double* w) {
         return Gff ? launch_ax_ff(nelt, nx, D, Gff, p, w, s) : launch_ax_fp64(nelt, nx, D, G, p, w, s);
     };
+    // the inner operator: the tcgen05 form where it applies (BF16 / FP16, nx up to 11), else the CUDA-core one
+    const bool tc5 = ax_lowp_tc5_supported(nx, precision);
     auto ax_lo = [&](const float* p, float* w, double* ed, const DirUpdate*, cudaStream_t ss) {
-        return launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed);
+        return tc5 ? launch_ax_lowp_tc5(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed)
+                   : launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed);
     };
 
     if (!minv) {
