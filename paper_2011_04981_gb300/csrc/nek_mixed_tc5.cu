@@ -188,6 +188,14 @@ __global__ void __launch_bounds__(kT5, 4)
     uint32_t parity = 0;
 
     for (int64_t e = blockIdx.x; e < nelt; e += gridDim.x) {
+        // the next element's u and G into L2 while this one is processed
+        if (e + gridDim.x < nelt) {
+            const unsigned char* un = reinterpret_cast<const unsigned char*>(u + (e + gridDim.x) * N3);
+            const unsigned char* gn = reinterpret_cast<const unsigned char*>(Glp + (e + gridDim.x) * (int64_t)N3 * 6);
+            for (int q = tid; q < (4 * N3 + 127) / 128; q += kT5) asm volatile("prefetch.global.L2 [%0];" ::"l"(un + 128 * q));
+            for (int q = tid; q < (12 * N3 + 127) / 128; q += kT5)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(gn + 128 * q));
+        }
         // ---- u into shared memory, the element's scale s_u
         const float* ue = u + e * N3;
         float mx = 0.f;
