@@ -12,7 +12,8 @@ namespace nek {
 constexpr int kMinNx = 2;
 constexpr int kMaxNx = 16;
 
-struct DirUpdate;  // below
+struct DirUpdate;   // below
+struct DirUpdateF;  // below
 
 // Record a CUDA error in the calling thread's last-error slot and map it to NEK_ERR_CUDA.
 nek_status cuda_fail(cudaError_t e);
@@ -79,10 +80,12 @@ nek_status launch_ax_fp64(int64_t nelt, int nx, const double* D, const double* G
 nek_status launch_ax_ff(int64_t nelt, int nx, const double* D, const float* Gff, const double* u, double* w,
                         cudaStream_t s, const int32_t* l2g = nullptr, const int32_t* eprob = nullptr,
                         const uint8_t* pdone = nullptr, double* edot = nullptr, const DirUpdate* dir = nullptr);
-// The tcgen05 form of the reduced-precision operator (BF16 / FP16, nx 2..11).
+// The tcgen05 form of the reduced-precision operator (BF16 / FP16, nx 2..11).  edot (optional): element
+// energies; dir (optional, with edot): the FP32 direction update below, input dir->p (u ignored).
 bool ax_lowp_tc5_supported(int nx, int precision);
 nek_status launch_ax_lowp_tc5(int precision, int64_t nelt, int nx, const double* D, const void* Glp,
-                              const float* gscale, const float* u, float* w, cudaStream_t s, double* edot = nullptr);
+                              const float* gscale, const float* u, float* w, cudaStream_t s, double* edot = nullptr,
+                              const DirUpdateF* dir = nullptr);
 // edot (optional, nelt doubles): per-element energies u_e . w_e in FP64.
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
                           const float* u, float* w, cudaStream_t s, double* edot = nullptr);
@@ -118,6 +121,15 @@ struct DirUpdate {
     const double* r;
     const double* minv;
     double* x;
+    const PcgScalars* sc;
+};
+// The same update on FP32 vectors (the inner solve of defect correction), with alpha and beta rounded to
+// float and the operations of that solve's own update, x = fma(alpha, p, x) and p = fma(beta, p, minv r).
+struct DirUpdateF {
+    float* p;
+    const float* r;
+    const float* minv;
+    float* x;
     const PcgScalars* sc;
 };
 // True where launch_ax_ff supports dir (every nx of the float-float kernels).

@@ -611,8 +611,9 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
     };
     // the inner operator: the tcgen05 form where it applies (BF16 / FP16, nx up to 11), else the CUDA-core one
     const bool tc5 = ax_lowp_tc5_supported(nx, precision);
-    auto ax_lo = [&](const float* p, float* w, double* ed, const DirUpdate*, cudaStream_t ss) {
-        return tc5 ? launch_ax_lowp_tc5(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed)
+    // (the tcgen05 form also takes the inner solve's x / direction update)
+    auto ax_lo = [&](const float* p, float* w, double* ed, const DirUpdateF* dir, cudaStream_t ss) {
+        return tc5 ? launch_ax_lowp_tc5(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed, dir)
                    : launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed);
     };
 
@@ -647,7 +648,7 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
         launches += 1;
         {
             pcg::Result res;
-            const pcg::ElementEnergies ee{L.edot, nelt};  // the operator's energies give <p,w>
+            const pcg::ElementEnergies ee{L.edot, nelt, tc5};  // the operator's energies give <p,w>
             nek_status si = pcg::run<float>(gs, n, L.c, mask, L.minv, L.b.w, L.d, L.b, inner_tol, max_inner, 10,
                                            false, ax_lo, s, &res, L.flags, &ee);
             inner_total += res.iters;

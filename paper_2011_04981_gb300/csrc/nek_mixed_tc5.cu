@@ -18,6 +18,12 @@
 // line of each direction) into FP32 point arrays in shared memory, and the
 // pointwise stages (G product, the final sum and scaling) run point-strided.
 //
+// Three forms: the plain operator; with element energies u_e . w_e (the inner
+// solve's <p,w>); and with energies and the PCG direction update of the inner
+// solve done as the element's input is loaded (x += alpha p, p = minv r + beta p
+// with that solve's own FP32 operations; the operator is applied to the new p),
+// which takes the solve's separate x / direction pass over the vectors away.
+//
 // Every wait on the mbarrier is bounded (~2 s of global time); a wait that
 // runs out writes NaN into the CTA's remaining outputs, waits once more for its
 // MMAs, frees its tensor memory and returns.
@@ -38,6 +44,7 @@ constexpr int kT5 = 128;
 constexpr uint32_t kCols5 = 64;
 constexpr long long kWait5 = 2000000000LL;
 constexpr uint32_t kHint5 = 200;  // ns a try may suspend the waiting thread: the MMAs take well under 1 us
+constexpr int kLpPlain = 0, kLpEnergy = 1, kLpDir = 2;  // operator forms (MODE)
 
 template <class S>
 struct Lp5;
@@ -141,11 +148,11 @@ __device__ __forceinline__ void issue3(uint32_t tmem, uint32_t a_base, uint32_t 
     tc5::mma_commit_lane0(mbar);
 }
 
-template <class S, int NX, bool ENERGY>
-__global__ void __launch_bounds__(kT5, 4)
+template <class S, int NX, int MODE>
+__global__ void __launch_bounds__(kT5, MODE == kLpDir ? 6 : 4)
     k_ax_lowp_tc5(int64_t nelt, const double* __restrict__ D, const S* __restrict__ Glp,
                   const float* __restrict__ gscale, const float* __restrict__ u, float* __restrict__ w,
-                  double* __restrict__ edot, long long wait_ns)
+                  double* __restrict__ edot, DirUpdateF dir, long long wait_ns)
 {
     constexpr int N2 = NX * NX, N3 = N2 * NX;
     constexpr uint32_t IDESC = idesc_lowp(Lp5<S>::kFmt);
@@ -186,23 +193,75 @@ __global__ void __launch_bounds__(kT5, 4)
     const bool line = m < N2;
     const int la = m % NX, lb = m / NX;  // r-line (j,k) = (la, lb); s-line (i,k) = (la, lb); t-line (i,j) = (la, lb)
     uint32_t parity = 0;
+    // the direction update: x += alpha p while an x update is pending, p = minv r + beta p while the solve goes on
+    bool dx = false, dp = false;
+    float alpha = 0.f, beta = 0.f;
+    if constexpr (MODE == kLpDir) {
+        dx = dir.sc->xpend != 0;
+        dp = !(dir.sc->done || dir.sc->status != NEK_OK);
+        alpha = (float)dir.sc->alpha;
+        beta = (float)dir.sc->beta;
+    }
 
     for (int64_t e = blockIdx.x; e < nelt; e += gridDim.x) {
-        // the next element's u and G into L2 while this one is processed
+        // the next element's inputs and G into L2 while this one is processed
         if (e + gridDim.x < nelt) {
-            const unsigned char* un = reinterpret_cast<const unsigned char*>(u + (e + gridDim.x) * N3);
-            const unsigned char* gn = reinterpret_cast<const unsigned char*>(Glp + (e + gridDim.x) * (int64_t)N3 * 6);
-            for (int q = tid; q < (4 * N3 + 127) / 128; q += kT5) asm volatile("prefetch.global.L2 [%0];" ::"l"(un + 128 * q));
+            const int64_t o = (e + gridDim.x) * N3;
+            const unsigned char* gn = reinterpret_cast<const unsigned char*>(Glp + o * 6);
+            for (int q = tid; q < (4 * N3 + 127) / 128; q += kT5) {
+                if constexpr (MODE == kLpDir) {
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const unsigned char*>(dir.p + o) + 128 * q));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const unsigned char*>(dir.r + o) + 128 * q));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const unsigned char*>(dir.minv + o) + 128 * q));
+                    if (dx)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const unsigned char*>(dir.x + o) + 128 * q));
+                } else {
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const unsigned char*>(u + o) + 128 * q));
+                }
+            }
             for (int q = tid; q < (12 * N3 + 127) / 128; q += kT5)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(gn + 128 * q));
         }
-        // ---- u into shared memory, the element's scale s_u
-        const float* ue = u + e * N3;
+        // ---- u (with the direction update: the new p) into shared memory, the element's scale s_u
         float mx = 0.f;
-        for (int q = tid; q < N3; q += kT5) {
-            const float v = __ldg(ue + q);
-            sU[q] = v;
-            mx = fmaxf(mx, fabsf(v));
+        if constexpr (MODE == kLpDir) {
+            float* pe = dir.p + e * N3;
+            float* xe = dir.x + e * N3;
+            const float* re = dir.r + e * N3;
+            const float* me = dir.minv + e * N3;
+            constexpr int KB = 4;  // points per batch: a batch's loads are issued before its stores
+            for (int q0 = tid; q0 < N3; q0 += KB * kT5) {
+                float po[KB], rv[KB], mv[KB], xv[KB];
+#pragma unroll
+                for (int k = 0; k < KB; k++) {
+                    const int q = q0 + k * kT5 < N3 ? q0 + k * kT5 : q0;
+                    po[k] = pe[q];
+                    rv[k] = __ldg(re + q);
+                    mv[k] = __ldg(me + q);
+                    xv[k] = dx ? xe[q] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < KB; k++) {
+                    const int q = q0 + k * kT5;
+                    if (q < N3) {
+                        if (dx) xe[q] = fmaf(alpha, po[k], xv[k]);
+                        float v = po[k];
+                        if (dp) {
+                            v = fmaf(beta, po[k], mv[k] * rv[k]);
+                            pe[q] = v;
+                        }
+                        sU[q] = v;
+                        mx = fmaxf(mx, fabsf(v));
+                    }
+                }
+            }
+        } else {
+            const float* ue = u + e * N3;
+            for (int q = tid; q < N3; q += kT5) {
+                const float v = __ldg(ue + q);
+                sU[q] = v;
+                mx = fmaxf(mx, fabsf(v));
+            }
         }
         const float su = pow2_up(cta_max(mx, red));
         const float inv = 1.f / su;  // a power of two: exact
@@ -313,9 +372,11 @@ __global__ void __launch_bounds__(kT5, 4)
             for (int p = tid; p < N3; p += kT5) {
                 const float wv = ((X[p] + X[N3 + p]) + X[2 * N3 + p]) * scale;
                 we[p] = wv;
-                if constexpr (ENERGY) energy = fmaf(__ldg(u + e * N3 + p), wv, energy);
+                // the input at p: with the direction update the p this thread wrote above (a plain load)
+                if constexpr (MODE == kLpDir) energy = fmaf(dir.p[e * N3 + p], wv, energy);
+                if constexpr (MODE == kLpEnergy) energy = fmaf(__ldg(u + e * N3 + p), wv, energy);
             }
-            if constexpr (ENERGY) {
+            if constexpr (MODE != kLpPlain) {
                 double t = (double)energy;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
@@ -323,7 +384,7 @@ __global__ void __launch_bounds__(kT5, 4)
             }
         }
         __syncthreads();  // u and the point arrays are read before the next element overwrites them
-        if constexpr (ENERGY) {
+        if constexpr (MODE != kLpPlain) {
             if (tid == 0) edot[e] = (esum[0] + esum[1]) + (esum[2] + esum[3]);
         }
         continue;
@@ -377,20 +438,20 @@ int tc5_sm_count()
     return n;
 }
 
-template <class S, int NX, bool ENERGY>
+template <class S, int NX, int MODE>
 nek_status launch_tc5_kernel(int64_t nelt, const double* D, const void* Glp, const float* gscale, const float* u,
-                             float* w, double* edot, cudaStream_t s)
+                             float* w, double* edot, const DirUpdateF& dir, cudaStream_t s)
 {
     static std::atomic<uint64_t> configured{0};
     constexpr size_t smem = tc5_smem_bytes<NX>();
-    nek_status st = ensure_dyn_smem(k_ax_lowp_tc5<S, NX, ENERGY>, smem, configured);
+    nek_status st = ensure_dyn_smem(k_ax_lowp_tc5<S, NX, MODE>, smem, configured);
     if (st != NEK_OK) return st;
     // shared memory over L1, so that the CTAs the grid is sized for all fit
     static std::atomic<uint64_t> carved{0};
     {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !(carved.load() & (uint64_t(1) << dev))) {
-            st = check_cuda(cudaFuncSetAttribute(k_ax_lowp_tc5<S, NX, ENERGY>,
+            st = check_cuda(cudaFuncSetAttribute(k_ax_lowp_tc5<S, NX, MODE>,
                                                  cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             if (st != NEK_OK) return st;
             carved.fetch_or(uint64_t(1) << dev);
@@ -399,37 +460,39 @@ nek_status launch_tc5_kernel(int64_t nelt, const double* D, const void* Glp, con
     // persistent CTAs: as many as are resident on an SM at once, from the kernel's registers and shared
     // memory and the device's limits (at most 8, whose 64 TMEM columns fill the 512)
     static int per_sm = 0;
-    if (!per_sm) per_sm = resident_ctas(reinterpret_cast<const void*>(k_ax_lowp_tc5<S, NX, ENERGY>), kT5, smem, 8);
+    if (!per_sm) per_sm = resident_ctas(reinterpret_cast<const void*>(k_ax_lowp_tc5<S, NX, MODE>), kT5, smem, 8);
     const int64_t cap = (int64_t)per_sm * tc5_sm_count();
     const int grid = static_cast<int>(nelt < cap ? nelt : cap);
-    k_ax_lowp_tc5<S, NX, ENERGY><<<grid, kT5, smem, s>>>(nelt, D, static_cast<const S*>(Glp), gscale, u, w, edot,
-                                                          kWait5);
+    k_ax_lowp_tc5<S, NX, MODE><<<grid, kT5, smem, s>>>(nelt, D, static_cast<const S*>(Glp), gscale, u, w, edot, dir,
+                                                        kWait5);
     return check_launch();
 }
 
 template <class S, int NX>
 nek_status launch_tc5_nx(int64_t nelt, const double* D, const void* Glp, const float* gscale, const float* u,
-                         float* w, double* edot, cudaStream_t s)
+                         float* w, double* edot, const DirUpdateF* dir, cudaStream_t s)
 {
-    return edot ? launch_tc5_kernel<S, NX, true>(nelt, D, Glp, gscale, u, w, edot, s)
-                : launch_tc5_kernel<S, NX, false>(nelt, D, Glp, gscale, u, w, nullptr, s);
+    const DirUpdateF none{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (edot && dir) return launch_tc5_kernel<S, NX, kLpDir>(nelt, D, Glp, gscale, u, w, edot, *dir, s);
+    return edot ? launch_tc5_kernel<S, NX, kLpEnergy>(nelt, D, Glp, gscale, u, w, edot, none, s)
+                : launch_tc5_kernel<S, NX, kLpPlain>(nelt, D, Glp, gscale, u, w, nullptr, none, s);
 }
 
 template <class S>
 nek_status launch_tc5_t(int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale, const float* u,
-                        float* w, double* edot, cudaStream_t s)
+                        float* w, double* edot, const DirUpdateF* dir, cudaStream_t s)
 {
     switch (nx) {
-        case 2: return launch_tc5_nx<S, 2>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 3: return launch_tc5_nx<S, 3>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 4: return launch_tc5_nx<S, 4>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 5: return launch_tc5_nx<S, 5>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 6: return launch_tc5_nx<S, 6>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 7: return launch_tc5_nx<S, 7>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 8: return launch_tc5_nx<S, 8>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 9: return launch_tc5_nx<S, 9>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 10: return launch_tc5_nx<S, 10>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 11: return launch_tc5_nx<S, 11>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 2: return launch_tc5_nx<S, 2>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 3: return launch_tc5_nx<S, 3>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 4: return launch_tc5_nx<S, 4>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 5: return launch_tc5_nx<S, 5>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 6: return launch_tc5_nx<S, 6>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 7: return launch_tc5_nx<S, 7>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 8: return launch_tc5_nx<S, 8>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 9: return launch_tc5_nx<S, 9>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 10: return launch_tc5_nx<S, 10>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 11: return launch_tc5_nx<S, 11>(nelt, D, Glp, gscale, u, w, edot, dir, s);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
 }
@@ -442,10 +505,11 @@ bool ax_lowp_tc5_supported(int nx, int precision)
 }
 
 nek_status launch_ax_lowp_tc5(int precision, int64_t nelt, int nx, const double* D, const void* Glp,
-                              const float* gscale, const float* u, float* w, cudaStream_t s, double* edot)
+                              const float* gscale, const float* u, float* w, cudaStream_t s, double* edot,
+                              const DirUpdateF* dir)
 {
-    if (precision == NEK_PREC_BF16) return launch_tc5_t<__nv_bfloat16>(nelt, nx, D, Glp, gscale, u, w, edot, s);
-    if (precision == NEK_PREC_F16) return launch_tc5_t<__half>(nelt, nx, D, Glp, gscale, u, w, edot, s);
+    if (precision == NEK_PREC_BF16) return launch_tc5_t<__nv_bfloat16>(nelt, nx, D, Glp, gscale, u, w, edot, dir, s);
+    if (precision == NEK_PREC_F16) return launch_tc5_t<__half>(nelt, nx, D, Glp, gscale, u, w, edot, dir, s);
     return NEK_ERR_INVALID_ARG;
 }
 

@@ -22,8 +22,8 @@
 // because p holds the same value in every copy of a node and is zero on masked
 // nodes (z = minv r and r vanish there).  The operator writes those energies
 // and k_alpha sums them.  An operator that can also apply k_p's x / direction
-// update as it loads p (ElementEnergies::fused_dir, DirUpdate) takes over that
-// pass: the loop then runs operator, dssum, k_alpha, k_update, k_beta, and k_p
+// update as it loads p (ElementEnergies::fused_dir; DirUpdate, or DirUpdateF for
+// FP32 vectors) takes over that pass: the loop then runs operator, dssum, k_alpha, k_update, k_beta, and k_p
 // runs once after it for the last x update.
 // Reductions use a fixed grid per length and a fixed shuffle tree, so results
 // are deterministic.  Once the residual test passes, or a breakdown is seen, a
@@ -441,9 +441,9 @@ struct Result {
 
 // The element-energy path (see the top of this file): the operator writes
 // edot[e] = p_e . (A_e p_e) for its nelt elements (k_update applies the mask,
-// from the point flags or the mask array).  fused_dir (FP64 vectors only): the
-// operator also applies the x / direction update as it loads p (DirUpdate), so
-// k_p runs once, after the loop, for the last x update.
+// from the point flags or the mask array).  fused_dir: the operator also
+// applies the x / direction update as it loads p (DirUpdate for FP64 vectors,
+// DirUpdateF for FP32), so k_p runs once, after the loop, for the last x update.
 struct ElementEnergies {
     double* edot;
     int64_t nelt;
@@ -493,9 +493,9 @@ nek_status run(const nek_gs* gs, int64_t n, const V* c, const uint8_t* mask, con
     const int nb = reduce_blocks(n);
     const int sb = stream_blocks(n);
     int launches = 0;
-    const bool fused = ee && ee->fused_dir && std::is_same<V, double>::value;
-    DirUpdate dir{};
-    if constexpr (std::is_same<V, double>::value) dir = DirUpdate{b.p, b.r, minv, x, b.sc};
+    const bool fused = ee && ee->fused_dir;
+    using Dir = typename std::conditional<std::is_same<V, double>::value, DirUpdate, DirUpdateF>::type;
+    const Dir dir{b.p, b.r, minv, x, b.sc};
     std::vector<cudaEvent_t> ev;
     Scalars h{};
     nek_status st = NEK_OK;

@@ -634,6 +634,38 @@ def test_cg_mixed_defect_correction(prec, outer_ff):
     assert res["outer"] >= 2 and res["inner"] > res["outer"]
 
 
+@pytest.mark.parametrize("prec", [nekax.PREC_F32, nekax.PREC_BF16, nekax.PREC_F16])
+def test_cg_mixed_inner_direction_update_fused(prec):
+    """The tcgen05 inner operator (BF16 / FP16) applies the inner solve's x / direction update itself, so an
+    inner iteration is five launches (operator, dssum, alpha, r update, beta) instead of six; one outer step
+    of K inner iterations (an unreachable inner tolerance) then launches 15 + 5K kernels (14 + 6K with the
+    separate update pass of the FP32 operator)."""
+    nx, K = 6, 7
+    mesh = inputs.box_mesh(3, 3, 2, nx, perturb=0.1, seed=8)
+    P = DeviceProblem(mesh, DEV)
+    f = inputs.random_global_field(mesh, seed=9)
+    nb = nekax.load().nek_lowp_bytes_per_value(prec)
+    Glp = torch.empty((mesh.nelt, nx ** 3, 6), dtype={4: torch.float32, 2: torch.float16}[nb], device=DEV)
+    gsc = torch.empty(mesh.nelt, dtype=torch.float32, device=DEV)
+    nekax.geom_lowp(mesh.nelt, nx, prec, P.G, Glp, gsc)
+    x = torch.full((mesh.nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+    res = nekax.cg_solve_mixed(P.gs, mesh.nelt, nx, P.D, P.G, P.prepare_ff(), prec, Glp, gsc, P.mask, P.minv,
+                               _t(f), x, tol=1e-30, inner_tol=1e-30, max_outer=1, max_inner=K)
+    assert res["status"] == nekax.ERR_NOT_CONVERGED and res["outer"] == 1 and res["inner"] == K, res
+    fused = prec != nekax.PREC_F32
+    assert res["kernel_launches"] == (15 + 5 * K if fused else 14 + 6 * K), res
+    # the outer step's x: finite, zero on masked nodes, its residual the one the oracle computes, and close
+    # to that of K exact Jacobi-PCG iterations (0.119 on this mesh)
+    xs = x.cpu().numpy()
+    assert np.all(np.isfinite(xs))
+    assert np.all(xs.reshape(-1)[mesh.mask.reshape(-1) == 0] == 0.0)
+    Pr = ref.Problem(mesh)
+    rel = Pr.residual(f, xs)
+    assert abs(res["relres"] - rel) <= 1e-9 * rel, (res, rel)
+    _, xk, _, _ = ref.pcg(Pr.D, Pr.G, Pr.offsets, Pr.idx, mesh.mask, Pr.minv, f, tol=0.0, max_iter=K)
+    assert 0.0 < rel < 2.0 * Pr.residual(f, xk), (rel, Pr.residual(f, xk))
+
+
 # ------------------------------------------------------------------ batched solves
 def _batch_case(seed=0):
     specs = [dict(ex=2, ey=2, ez=2, nx=8), dict(ex=3, ey=2, ez=1, nx=6), dict(ex=2, ey=1, ez=1, nx=10),
