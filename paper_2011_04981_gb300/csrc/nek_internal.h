@@ -86,9 +86,11 @@ bool ax_lowp_tc5_supported(int nx, int precision);
 nek_status launch_ax_lowp_tc5(int precision, int64_t nelt, int nx, const double* D, const void* Glp,
                               const float* gscale, const float* u, float* w, cudaStream_t s, double* edot = nullptr,
                               const DirUpdateF* dir = nullptr);
-// edot (optional, nelt doubles): per-element energies u_e . w_e in FP64.
+// edot (optional, nelt doubles): per-element energies u_e . w_e in FP64; dir (optional, with edot): the
+// FP32 direction update (DirUpdateF), input dir->p (u ignored).
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
-                          const float* u, float* w, cudaStream_t s, double* edot = nullptr);
+                          const float* u, float* w, cudaStream_t s, double* edot = nullptr,
+                          const DirUpdateF* dir = nullptr);
 nek_status launch_mask(int64_t n, const uint8_t* mask, double* v, cudaStream_t s);
 // Diagonal of the element operators (before summation over shared nodes).
 nek_status launch_diag_local(int64_t nelt, int nx, const double* D, const double* G, double* d, cudaStream_t s);

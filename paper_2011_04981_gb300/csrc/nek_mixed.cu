@@ -160,15 +160,19 @@ __device__ __forceinline__ void line_apply(const float* __restrict__ M, const fl
 // registers; the pointwise G product runs on the t-lines; phase 2 sums the
 // r- and s-contributions through shared memory and adds the t-contribution in
 // registers before the store.
-// ENERGY: edot[e] = sum over the element's points of u w (each thread's nx
-// terms summed in FP32, the element's threads in FP64), which the inner solve
-// uses for <p,w> (see nek_pcg.cuh).
-template <class S, int NX, int EPB, bool ENERGY>
+// MODE kLowpEnergy: edot[e] = sum over the element's points of u w (each
+// thread's nx terms summed in FP32, the element's threads in FP64), which the
+// inner solve uses for <p,w> (see nek_pcg.cuh).  MODE kLowpDir: the same, and
+// the inner solve's x / direction update (DirUpdateF) is applied as the
+// element's input is loaded: x += alpha p, p = minv r + beta p with that
+// solve's own FP32 operations, and the operator is applied to the new p.
+constexpr int kLowpPlain = 0, kLowpEnergy = 1, kLowpDir = 2;
+template <class S, int NX, int EPB, int MODE>
 __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const double* __restrict__ D,
                                                           const S* __restrict__ Glp,
                                                           const float* __restrict__ gscale,
                                                           const float* __restrict__ u, float* __restrict__ w,
-                                                          double* __restrict__ edot)
+                                                          double* __restrict__ edot, DirUpdateF dir)
 {
     using L = Lp<S>;
     constexpr int N2 = NX * NX, N3 = NX * NX * NX, NT = N2 * EPB, R = lp_row(NX);
@@ -190,7 +194,40 @@ __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const dou
         sDT[q] = l < NX ? L::rnd((float)D[l * NX + o]) : 0.f;
     }
     for (int q = tid; q < EPB; q += NT) sMax[q] = 0.f;
-    {
+    if constexpr (MODE == kLowpDir) {
+        const bool dx = dir.sc->xpend != 0, dp = !(dir.sc->done || dir.sc->status != NEK_OK);
+        const float alpha = (float)dir.sc->alpha, beta = (float)dir.sc->beta;
+        float* pb = dir.p + e0 * N3;
+        float* xb = dir.x + e0 * N3;
+        const float* rb = dir.r + e0 * N3;
+        const float* mb = dir.minv + e0 * N3;
+        const int nq = ne * N3;
+        constexpr int KB = 4;  // points per batch: a batch's loads are issued before its stores
+        for (int q0 = tid; q0 < nq; q0 += KB * NT) {
+            float po[KB], rv[KB], mv[KB], xv[KB];
+#pragma unroll
+            for (int k = 0; k < KB; k++) {
+                const int q = q0 + k * NT < nq ? q0 + k * NT : q0;
+                po[k] = pb[q];
+                rv[k] = __ldg(rb + q);
+                mv[k] = __ldg(mb + q);
+                xv[k] = dx ? xb[q] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < KB; k++) {
+                const int q = q0 + k * NT;
+                if (q < nq) {
+                    if (dx) xb[q] = fmaf(alpha, po[k], xv[k]);
+                    float v = po[k];
+                    if (dp) {
+                        v = fmaf(beta, po[k], mv[k] * rv[k]);
+                        pb[q] = v;
+                    }
+                    sU[q] = v;
+                }
+            }
+        }
+    } else {
         const float* src = u + e0 * N3;
         for (int q = tid; q < ne * N3; q += NT) sU[q] = __ldg(src + q);
     }
@@ -289,62 +326,68 @@ __global__ void __launch_bounds__(NX* NX* EPB) k_ax_lowp(int64_t nelt, const dou
         const float scale = su * gscale[e0 + el];
         float* we = w + (e0 + el) * (int64_t)N3;
         const float* ug = u + (e0 + el) * (int64_t)N3;
+        // with the direction update: the p written above
+        const float* pg = MODE == kLowpDir ? dir.p + (e0 + el) * (int64_t)N3 : nullptr;
 #pragma unroll
         for (int k = 0; k < NX; k++) {
             const int p = k * N2 + b * NX + a;
             const float wv = (ue[p] + ot[k]) * scale;
             we[p] = wv;
-            if constexpr (ENERGY) energy = fmaf(__ldg(ug + p), wv, energy);
+            // (written by another thread of the block before the barriers above: a plain load)
+            if constexpr (MODE == kLowpDir) energy = fmaf(pg[p], wv, energy);
+            if constexpr (MODE == kLowpEnergy) energy = fmaf(__ldg(ug + p), wv, energy);
         }
     }
-    if constexpr (ENERGY)
+    if constexpr (MODE != kLowpPlain)
         element_sums<N2, EPB>(pcg::to_f64(energy), reinterpret_cast<double*>(sR), edot + e0, ne);
 }
 
-template <class S, int NX, bool ENERGY>
+template <class S, int NX, int MODE>
 nek_status launch_lowp_kernel(int64_t nelt, const double* D, const void* Glp, const float* gscale, const float* u,
-                              float* w, double* edot, cudaStream_t s)
+                              float* w, double* edot, const DirUpdateF& dir, cudaStream_t s)
 {
     constexpr int EPB = lp_epb(NX);
     constexpr size_t smem = lp_smem_bytes<NX, EPB>();
     static std::atomic<uint64_t> configured{0};
-    nek_status st = ensure_dyn_smem(k_ax_lowp<S, NX, EPB, ENERGY>, smem, configured);
+    nek_status st = ensure_dyn_smem(k_ax_lowp<S, NX, EPB, MODE>, smem, configured);
     if (st != NEK_OK) return st;
     const int64_t blocks = (nelt + EPB - 1) / EPB;
     if (blocks > 0x7fffffff) return NEK_ERR_TOO_LARGE;
-    k_ax_lowp<S, NX, EPB, ENERGY><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
-        nelt, D, static_cast<const S*>(Glp), gscale, u, w, edot);
+    k_ax_lowp<S, NX, EPB, MODE><<<(unsigned)blocks, NX * NX * EPB, smem, s>>>(
+        nelt, D, static_cast<const S*>(Glp), gscale, u, w, edot, dir);
     return check_launch();
 }
 
 template <class S, int NX>
 nek_status launch_lowp_nx(int64_t nelt, const double* D, const void* Glp, const float* gscale, const float* u,
-                          float* w, double* edot, cudaStream_t s)
+                          float* w, double* edot, const DirUpdateF* dir, cudaStream_t s)
 {
-    return edot ? launch_lowp_kernel<S, NX, true>(nelt, D, Glp, gscale, u, w, edot, s)
-                : launch_lowp_kernel<S, NX, false>(nelt, D, Glp, gscale, u, w, nullptr, s);
+    const DirUpdateF none{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (edot && dir) return launch_lowp_kernel<S, NX, kLowpDir>(nelt, D, Glp, gscale, u, w, edot, *dir, s);
+    return edot ? launch_lowp_kernel<S, NX, kLowpEnergy>(nelt, D, Glp, gscale, u, w, edot, none, s)
+                : launch_lowp_kernel<S, NX, kLowpPlain>(nelt, D, Glp, gscale, u, w, nullptr, none, s);
 }
 
 template <class S>
 nek_status launch_lowp_t(int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
-                         const float* u, float* w, double* edot, cudaStream_t s)
+                         const float* u, float* w, double* edot, const DirUpdateF* dir, cudaStream_t s)
 {
     switch (nx) {
-        case 2: return launch_lowp_nx<S, 2>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 3: return launch_lowp_nx<S, 3>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 4: return launch_lowp_nx<S, 4>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 5: return launch_lowp_nx<S, 5>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 6: return launch_lowp_nx<S, 6>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 7: return launch_lowp_nx<S, 7>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 8: return launch_lowp_nx<S, 8>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 9: return launch_lowp_nx<S, 9>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 10: return launch_lowp_nx<S, 10>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 11: return launch_lowp_nx<S, 11>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 12: return launch_lowp_nx<S, 12>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 13: return launch_lowp_nx<S, 13>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 14: return launch_lowp_nx<S, 14>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 15: return launch_lowp_nx<S, 15>(nelt, D, Glp, gscale, u, w, edot, s);
-        case 16: return launch_lowp_nx<S, 16>(nelt, D, Glp, gscale, u, w, edot, s);
+        case 2: return launch_lowp_nx<S, 2>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 3: return launch_lowp_nx<S, 3>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 4: return launch_lowp_nx<S, 4>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 5: return launch_lowp_nx<S, 5>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 6: return launch_lowp_nx<S, 6>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 7: return launch_lowp_nx<S, 7>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 8: return launch_lowp_nx<S, 8>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 9: return launch_lowp_nx<S, 9>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 10: return launch_lowp_nx<S, 10>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 11: return launch_lowp_nx<S, 11>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 12: return launch_lowp_nx<S, 12>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 13: return launch_lowp_nx<S, 13>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 14: return launch_lowp_nx<S, 14>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 15: return launch_lowp_nx<S, 15>(nelt, D, Glp, gscale, u, w, edot, dir, s);
+        case 16: return launch_lowp_nx<S, 16>(nelt, D, Glp, gscale, u, w, edot, dir, s);
         default: return NEK_ERR_UNSUPPORTED_NX;
     }
 }
@@ -355,12 +398,12 @@ nek_status launch_ax_lowp_tc(int prec, int64_t nelt, int nx, const double* D, co
                              const float* u, float* w, cudaStream_t s);
 
 nek_status launch_ax_lowp(int prec, int64_t nelt, int nx, const double* D, const void* Glp, const float* gscale,
-                          const float* u, float* w, cudaStream_t s, double* edot)
+                          const float* u, float* w, cudaStream_t s, double* edot, const DirUpdateF* dir)
 {
     switch (prec) {
-        case NEK_PREC_F32: return launch_lowp_t<float>(nelt, nx, D, Glp, gscale, u, w, edot, s);
-        case NEK_PREC_BF16: return launch_lowp_t<__nv_bfloat16>(nelt, nx, D, Glp, gscale, u, w, edot, s);
-        case NEK_PREC_F16: return launch_lowp_t<__half>(nelt, nx, D, Glp, gscale, u, w, edot, s);
+        case NEK_PREC_F32: return launch_lowp_t<float>(nelt, nx, D, Glp, gscale, u, w, edot, dir, s);
+        case NEK_PREC_BF16: return launch_lowp_t<__nv_bfloat16>(nelt, nx, D, Glp, gscale, u, w, edot, dir, s);
+        case NEK_PREC_F16: return launch_lowp_t<__half>(nelt, nx, D, Glp, gscale, u, w, edot, dir, s);
         default: return NEK_ERR_INVALID_ARG;
     }
 }
@@ -611,10 +654,10 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
     };
     // the inner operator: the tcgen05 form where it applies (BF16 / FP16, nx up to 11), else the CUDA-core one
     const bool tc5 = ax_lowp_tc5_supported(nx, precision);
-    // (the tcgen05 form also takes the inner solve's x / direction update)
+    // (both take the inner solve's x / direction update)
     auto ax_lo = [&](const float* p, float* w, double* ed, const DirUpdateF* dir, cudaStream_t ss) {
         return tc5 ? launch_ax_lowp_tc5(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed, dir)
-                   : launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed);
+                   : launch_ax_lowp(precision, nelt, nx, D, Glp, gscale, p, w, ss, ed, dir);
     };
 
     if (!minv) {
@@ -648,7 +691,7 @@ nek_status nek_cg_solve_mixed(const nek_gs* gs, int64_t nelt, int nx, const doub
         launches += 1;
         {
             pcg::Result res;
-            const pcg::ElementEnergies ee{L.edot, nelt, tc5};  // the operator's energies give <p,w>
+            const pcg::ElementEnergies ee{L.edot, nelt, true};  // the operator's energies give <p,w>
             nek_status si = pcg::run<float>(gs, n, L.c, mask, L.minv, L.b.w, L.d, L.b, inner_tol, max_inner, 10,
                                            false, ax_lo, s, &res, L.flags, &ee);
             inner_total += res.iters;

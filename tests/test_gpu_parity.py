@@ -636,10 +636,10 @@ def test_cg_mixed_defect_correction(prec, outer_ff):
 
 @pytest.mark.parametrize("prec", [nekax.PREC_F32, nekax.PREC_BF16, nekax.PREC_F16])
 def test_cg_mixed_inner_direction_update_fused(prec):
-    """The tcgen05 inner operator (BF16 / FP16) applies the inner solve's x / direction update itself, so an
-    inner iteration is five launches (operator, dssum, alpha, r update, beta) instead of six; one outer step
-    of K inner iterations (an unreachable inner tolerance) then launches 15 + 5K kernels (14 + 6K with the
-    separate update pass of the FP32 operator)."""
+    """The inner operator (the CUDA-core form for FP32, the tcgen05 form for BF16 / FP16) applies the inner
+    solve's x / direction update itself, so an inner iteration is five launches (operator, dssum, alpha,
+    r update, beta) instead of six with a separate update pass: one outer step of K inner iterations (an
+    unreachable inner tolerance) launches 15 + 5K kernels (it would be 14 + 6K)."""
     nx, K = 6, 7
     mesh = inputs.box_mesh(3, 3, 2, nx, perturb=0.1, seed=8)
     P = DeviceProblem(mesh, DEV)
@@ -652,8 +652,7 @@ def test_cg_mixed_inner_direction_update_fused(prec):
     res = nekax.cg_solve_mixed(P.gs, mesh.nelt, nx, P.D, P.G, P.prepare_ff(), prec, Glp, gsc, P.mask, P.minv,
                                _t(f), x, tol=1e-30, inner_tol=1e-30, max_outer=1, max_inner=K)
     assert res["status"] == nekax.ERR_NOT_CONVERGED and res["outer"] == 1 and res["inner"] == K, res
-    fused = prec != nekax.PREC_F32
-    assert res["kernel_launches"] == (15 + 5 * K if fused else 14 + 6 * K), res
+    assert res["kernel_launches"] == 15 + 5 * K, res
     # the outer step's x: finite, zero on masked nodes, its residual the one the oracle computes, and close
     # to that of K exact Jacobi-PCG iterations (0.119 on this mesh)
     xs = x.cpu().numpy()
