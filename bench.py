@@ -68,6 +68,8 @@ def parse():
                     help="bound on the oracle's CPU time per sample (default: about 10-15 s for cpu_baseline, "
                          "120 s spread over the steps of --impl reference)")
     ap.add_argument("--mixed", action="store_true", help="add defect correction (FP32/BF16/FP16) to --extras")
+    ap.add_argument("--mixed-precisions", default="f32,bf16,f16",
+                    help="comma list of the defect-correction block's inner precisions (f32, bf16, f16)")
     ap.add_argument("--batch", type=int, default=256,
                     help="problems of the batched block (nelt log-uniform in [8,4096])")
     ap.add_argument("--learned", action="store_true", help="add the learned-preconditioner block to --extras")
@@ -416,7 +418,7 @@ def lvec_block(torch, P, iters, reps=3):
     return out
 
 
-def mixed_block(torch, P, f, x, ws_bytes_hint=None):
+def mixed_block(torch, P, f, x, precisions=("f32", "bf16", "f16")):
     """FP64 defect correction with reduced-precision inner PCG on the bench mesh."""
     from paper_2011_04981_gb300 import nekax
 
@@ -431,6 +433,8 @@ def mixed_block(torch, P, f, x, ws_bytes_hint=None):
     hbm, _ = peaks()
     for name, prec, dt in (("f32", nekax.PREC_F32, torch.float32), ("bf16", nekax.PREC_BF16, torch.float16),
                            ("f16", nekax.PREC_F16, torch.float16)):
+        if name not in precisions:
+            continue
         Glp = torch.empty((nelt, nx ** 3, 6), dtype=dt, device="cuda")
         gsc = torch.empty(nelt, dtype=torch.float32, device="cuda")
         nekax.geom_lowp(nelt, nx, prec, P.G, Glp, gsc)
@@ -850,7 +854,8 @@ def run_native(args):
     if "solve" in ex:
         line["cg_to_1e-8"] = _guard("solve", lambda: solves_to_tol(torch, P, f, x, ws))
     if "mixed" in ex:
-        line["mixed"] = _guard("mixed", lambda: mixed_block(torch, P, f, x))
+        precs = tuple(q.strip() for q in args.mixed_precisions.split(","))
+        line["mixed"] = _guard("mixed", lambda: mixed_block(torch, P, f, x, precs))
     if "lvec" in ex:
         line["lvec"] = _guard("lvec", lambda: lvec_block(torch, P, iters))
     if "sweep" in ex:

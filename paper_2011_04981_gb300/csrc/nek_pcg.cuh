@@ -23,8 +23,8 @@
 // nodes (z = minv r and r vanish there).  The operator writes those energies
 // and k_alpha sums them.  An operator that can also apply k_p's x / direction
 // update as it loads p (ElementEnergies::fused_dir; DirUpdate, or DirUpdateF for
-// FP32 vectors) takes over that pass: the loop then runs operator, dssum, k_alpha, k_update, k_beta, and k_p
-// runs once after it for the last x update.
+// FP32 vectors) takes over that pass: the loop then runs operator, dssum,
+// k_alpha, k_update, k_beta, and k_p runs once after it for the last x update.
 // Reductions use a fixed grid per length and a fixed shuffle tree, so results
 // are deterministic.  Once the residual test passes, or a breakdown is seen, a
 // device flag makes every later update kernel of the call return at once.
@@ -309,25 +309,53 @@ __global__ void __launch_bounds__(NT) k_update(int64_t n, const V* __restrict__ 
     double arr = 0.0, arz = 0.0;
     const int64_t stride = (int64_t)gridDim.x * NT;
     if (flags && std::is_same<V, float>::value) {
-        // FP32 vectors (the inner solve of defect correction, run to a relative
-        // residual of about 1e-2): each thread sums its ~100 positive terms in
-        // FP32 with FMAs and hands one double to the block's FP64 reduction
-        float frr = 0.f, frz = 0.f;
+        if constexpr (std::is_same<V, float>::value) {  // (instantiated for FP32 vectors only)
+            // FP32 vectors (the inner solve of defect correction, run to a relative
+            // residual of about 1e-2): each thread sums its ~100 positive terms in
+            // FP32 with FMAs and hands one double to the block's FP64 reduction
+            float frr = 0.f, frz = 0.f;
+            auto point = [&](uint32_t fq, float wq, float ro, float mq) {
+                if (!(fq & kFree)) wq = 0.f;  // the mask
+                const float rq = fmaf(-(float)alpha, wq, ro);
+                const float zq = mq * rq;
+                if (fq & kOwner) {
+                    frr = fmaf(rq, rq, frr);
+                    frz = fmaf(rq, zq, frz);
+                }
+                return rq;
+            };
+            const uintptr_t al = reinterpret_cast<uintptr_t>(w) | reinterpret_cast<uintptr_t>(r) |
+                                 reinterpret_cast<uintptr_t>(minv);
+            if ((al & 15) == 0 && (reinterpret_cast<uintptr_t>(flags) & 3) == 0) {
+                // four consecutive points per access (16-byte vectors, one 32-bit word of flags); the last n % 4
+                // points by block 0
+                const int64_t n4 = n >> 2;
+                const float4* w4 = reinterpret_cast<const float4*>(w);
+                const float4* m4 = reinterpret_cast<const float4*>(minv);
+                float4* r4 = reinterpret_cast<float4*>(r);
+                const uint32_t* f4 = reinterpret_cast<const uint32_t*>(flags);
+                for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n4; q += stride) {
+                    const uint32_t fq = f4[q];
+                    const float4 wv = w4[q], mv = m4[q], ro = r4[q];
+                    float4 rn;
+                    rn.x = point(fq & 0xffu, wv.x, ro.x, mv.x);
+                    rn.y = point((fq >> 8) & 0xffu, wv.y, ro.y, mv.y);
+                    rn.z = point((fq >> 16) & 0xffu, wv.z, ro.z, mv.z);
+                    rn.w = point(fq >> 24, wv.w, ro.w, mv.w);
+                    r4[q] = rn;
+                }
+                if (blockIdx.x == 0 && threadIdx.x < (n & 3)) {
+                    const int64_t q = 4 * n4 + threadIdx.x;
+                    r[q] = point(flags[q], w[q], r[q], minv[q]);
+                }
+            } else {
 #pragma unroll 4
-        for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride) {
-            const uint8_t fq = flags[q];
-            V wq = w[q];
-            if (!(fq & kFree)) wq = V(0);  // the mask
-            const V rq = fma(-alpha, wq, r[q]);
-            const V zq = minv[q] * rq;
-            r[q] = rq;
-            if (fq & kOwner) {
-                frr = fmaf((float)rq, (float)rq, frr);
-                frz = fmaf((float)rq, (float)zq, frz);
+                for (int64_t q = blockIdx.x * (int64_t)NT + threadIdx.x; q < n; q += stride)
+                    r[q] = point(flags[q], w[q], r[q], minv[q]);
             }
+            arr = to_f64(frr);
+            arz = to_f64(frz);
         }
-        arr = to_f64(frr);
-        arz = to_f64(frz);
     } else if (flags) {
         // r and <r,z> in FP64; <r,r> (used only for the residual test and the reported norm) exactly enough on
         // the FP32 pipes, so that GB300's 2-per-clock FP64 pipe carries three operations a point, not four:
