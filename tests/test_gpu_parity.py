@@ -634,6 +634,33 @@ def test_cg_mixed_defect_correction(prec, outer_ff):
     assert res["outer"] >= 2 and res["inner"] > res["outer"]
 
 
+@pytest.mark.parametrize("dims,nx,prec", [
+    ((3, 1, 1), 3, nekax.PREC_F32),    # 81 points: the vector r update's n % 4 tail
+    ((3, 1, 1), 3, nekax.PREC_F16),    # the tcgen05 form with the direction update at its smallest nx
+    ((2, 2, 1), 11, nekax.PREC_F16),   # ... and at its largest
+    ((2, 1, 2), 12, nekax.PREC_BF16),  # the CUDA-core form with the update for BF16 (beyond the tcgen05 form)
+    ((1, 3, 1), 13, nekax.PREC_F32),   # two elements per CTA over three elements: a ragged last CTA
+])
+def test_cg_mixed_direction_update_forms(dims, nx, prec):
+    """Defect correction to 1e-10 through each operator form that applies the inner direction update, checked
+    with the oracle's residual of the returned x."""
+    mesh = inputs.box_mesh(*dims, nx, perturb=0.1, seed=nx)
+    P = DeviceProblem(mesh, DEV)
+    Pr = ref.Problem(mesh)
+    f = inputs.random_global_field(mesh, seed=nx + 1)
+    nb = nekax.load().nek_lowp_bytes_per_value(prec)
+    Glp = torch.empty((mesh.nelt, nx ** 3, 6), dtype={4: torch.float32, 2: torch.float16}[nb], device=DEV)
+    gsc = torch.empty(mesh.nelt, dtype=torch.float32, device=DEV)
+    nekax.geom_lowp(mesh.nelt, nx, prec, P.G, Glp, gsc)
+    x = torch.full((mesh.nelt, nx ** 3), float("nan"), dtype=torch.float64, device=DEV)
+    res = nekax.cg_solve_mixed(P.gs, mesh.nelt, nx, P.D, P.G, P.prepare_ff(), prec, Glp, gsc, P.mask, P.minv,
+                               _t(f), x, tol=1e-10, inner_tol=1e-2, max_outer=60, max_inner=4000)
+    assert res["status"] == nekax.OK, res
+    assert Pr.residual(f, x.cpu().numpy()) <= 1e-10 * 1.01
+    # five launches per inner iteration at most, plus a bounded count per outer step
+    assert res["kernel_launches"] <= 5 * res["inner"] + 60 * res["outer"] + 10, res
+
+
 @pytest.mark.parametrize("prec", [nekax.PREC_F32, nekax.PREC_BF16, nekax.PREC_F16])
 def test_cg_mixed_inner_direction_update_fused(prec):
     """The inner operator (the CUDA-core form for FP32, the tcgen05 form for BF16 / FP16) applies the inner
