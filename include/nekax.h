@@ -255,7 +255,9 @@ nek_status nek_ax_lowp_tc5(int64_t nelt, int nx, int precision, const double* D,
  * correction solves A d = r/||r|| by Jacobi-PCG with FP32 vectors and the
  * reduced-precision operator (nek_ax_lowp_tc5 for BF16 / FP16 at nx up to 11,
  * else nek_ax_lowp) until its relative residual is <= inner_tol (or max_inner
- * iterations).  Stops when ||r||_c/||b||_c <= tol_rel (NEK_OK) or after max_outer
+ * iterations); that operator also applies the inner solve's x / direction update
+ * as it loads p, with the FP32 operations of the update (five kernels an inner
+ * iteration).  Stops when ||r||_c/||b||_c <= tol_rel (NEK_OK) or after max_outer
  * corrections (NEK_ERR_NOT_CONVERGED).  workspace: device, >=
  * nek_cg_mixed_workspace_bytes(...) bytes, 256-aligned, or NULL.  Synchronous.
  */
