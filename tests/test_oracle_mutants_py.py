@@ -1,4 +1,5 @@
-"""The pins of the oracle's Python modules (GLL rule, network, unique-node vectors) catch plausible mistakes.
+"""The pins of the oracle's Python code (GLL rule, network, unique-node vectors, the dense brute-force
+operator) catch plausible mistakes.
 
 Each case plants one mistake (a wrong power, a flipped sign, swapped indices, a dropped term, a shift the wrong
 way, an overwrite in place of a sum) in a copy of a module's source, executes the copy, puts its functions in
@@ -8,13 +9,15 @@ oracle is never modified.
 import numpy as np
 import pytest
 
-from oracle import gll, lvec, net
+from oracle import gll, lvec, net, ref
+from tests import test_oracle_ax as tax
 from tests import test_oracle_gll as tg
 from tests import test_oracle_lvec as tl
 from tests import test_oracle_net as tn
 
 MUTANTS = [
-    # GLL rule: weights 2 / (N (N+1) L_N(x)^2), corner entries of D -+N(N+1)/4, off-diagonal L_N(x_i) / (L_N(x_l) (x_i - x_l))
+    # GLL rule: weights 2 / (N (N+1) L_N(x)^2), corner entries of D -+N(N+1)/4,
+    # off-diagonal entries L_N(x_i) / (L_N(x_l) (x_i - x_l))
     ("gll_weight_power", gll, "rho = 2.0 / (N * (N + 1) * LN ** 2)", "rho = 2.0 / (N * (N + 1) * LN)",
      lambda: tg.test_quadrature_exact_to_degree_2N_minus_1(5)),
     ("gll_corner_sign", gll, "D[0, 0] = -N * (N + 1) / 4.0", "D[0, 0] = N * (N + 1) / 4.0",
@@ -42,6 +45,11 @@ MUTANTS = [
      "    return out", lambda: tl.test_apply_equals_dense_assembled_matrix((2, 2, 1), 3)),
     ("lvec_cg_beta_inverted", lvec, "beta = rz_new / rz", "beta = rz / rz_new",
      lambda: tl.test_same_iterates_as_the_element_vector_solve((3, 2, 2), 4)),
+    # the dense brute-force operator (itself a pin of the C operator): Kronecker factor order, G components
+    ("dense_s_gradient_kron_order", ref, "Bs = np.kron(I, np.kron(D, I))", "Bs = np.kron(D, np.kron(I, I))",
+     lambda: tax.test_dense_brute_force(3)),
+    ("dense_offdiagonal_components_swapped", ref, "(0, 1): 1, (0, 2): 2", "(0, 1): 2, (0, 2): 1",
+     lambda: tax.test_dense_brute_force(3)),
 ]
 
 
